@@ -1,0 +1,235 @@
+/*
+ * pdeshep.h -- C ABI of the GB300 (sm_103a) banded FEAST spectrum-slicing
+ * library: the data-parallel core of step (II) of PDESHEP (arXiv 2012.00506,
+ * "A Parallel Direct Eigensolver for Sequences of Hermitian Eigenvalue
+ * Problems with No Tridiagonalization").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Band storage.  The Hermitian (or real symmetric) band matrix B of order n
+ *    and semi-bandwidth b is given in LAPACK lower compact band form,
+ *    column-major: B(i,j) for j <= i <= min(n-1, j+b) at band[(i-j) + j*ldab],
+ *    ldab >= b+1.  Real input is double; complex input is interleaved
+ *    pdeshep_c128.  The diagonal of a complex band must have zero imaginary
+ *    part (it is ignored).  This is the compact storage the paper keeps on
+ *    every process (Section 3, "stored compactly as in LAPACK").
+ *  * Dense blocks (start vectors, eigenvectors) are column-major n x m with
+ *    leading dimension n, of the same scalar type as the band.
+ *  * Pointers prefixed d_ are device pointers, h_ host pointers.  The caller
+ *    owns every buffer; the library never allocates device memory.  Scratch
+ *    memory is a caller-provided device workspace whose size is returned by
+ *    the matching *_workspace_size query (256-byte aligned base required).
+ *  * Work is issued on the CUDA stream passed as `stream` (a cudaStream_t;
+ *    NULL = legacy default stream).  Entry points that return host outputs
+ *    synchronise that stream before returning.
+ *  * Status: 0 = success; -i = the i-th argument (1-based) is invalid
+ *    (LAPACK `info` convention); positive = a PDESHEP_* outcome below.
+ *    CUDA runtime failures return PDESHEP_CUDA_ERROR and leave the message
+ *    in pdeshep_last_error().
+ */
+#ifndef PDESHEP_H
+#define PDESHEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double re, im;
+} pdeshep_c128;
+
+/* ---- status codes --------------------------------------------------------- */
+#define PDESHEP_OK 0
+#define PDESHEP_NOT_CONVERGED 1      /* max_iter reached before every slice converged */
+#define PDESHEP_COUNT_MISMATCH 2     /* m0 of a slice is below its exact count (Section 3.2) */
+#define PDESHEP_CHOLQR_BREAKDOWN 3   /* Gram matrix not numerically positive definite */
+#define PDESHEP_NONFINITE_INPUT 4    /* NaN/Inf in the band or start vectors */
+#define PDESHEP_WORKSPACE_TOO_SMALL 5
+#define PDESHEP_DEVICE_TIMEOUT 6     /* a bounded device-side wait gave up */
+#define PDESHEP_SINGULAR 7           /* exactly zero pivot in a shifted factorization */
+#define PDESHEP_CUDA_ERROR 8
+#define PDESHEP_EIG_NOT_CONVERGED 9  /* small dense eigensolver did not converge */
+
+/* ---- precision of the shifted factorizations and solves ----------------- */
+#define PDESHEP_FP64 0   /* complex128 LU and solves (plain FEAST, Algorithm 1) */
+#define PDESHEP_MIXED 1  /* complex64 LU and solves with FP32 accumulation + FP64 refinement */
+
+/* ---- refinement policy for PDESHEP_MIXED --------------------------------- */
+#define PDESHEP_REFINE_NONE 0      /* plain filter in complex64 (FP32-class accuracy) */
+#define PDESHEP_REFINE_RESIDUAL 1  /* filter applied to FP64 Ritz residuals (default):
+                                      r(B) x = r(lambda) x + sum_j w_j/(z_j-lambda) (z_j I-B)^{-1} (Bx - lambda x) */
+
+typedef struct {
+  double tol;              /* relative residual ||Bx - lambda x|| / (bnorm ||x||); default 1e-10 */
+  int32_t max_iter;        /* FEAST iterations per slice; default 20 */
+  int32_t precision;       /* PDESHEP_FP64 or PDESHEP_MIXED; default PDESHEP_MIXED */
+  int32_t refine_policy;   /* PDESHEP_REFINE_*; default PDESHEP_REFINE_RESIDUAL */
+  int32_t rhs_chunk;       /* right-hand sides per solve block (0 = autotuned) */
+  double ellipse_ratio;    /* vertical / horizontal semi-axis of the contour; default 0.3 */
+  double bnorm;            /* ||B||_2 for the residual; <= 0: computed by the library */
+  uint64_t seed;           /* reserved for library-drawn start vectors */
+  size_t hbm_cap_bytes;    /* cap on factor storage per wave; 0 = whole workspace */
+  int32_t autotune;        /* 0 off, 1 on (tile/chunk choice from measured timings) */
+  int32_t verbose;         /* 0 quiet */
+  void* stream;            /* cudaStream_t */
+} pdeshep_opts;
+
+typedef struct {
+  int32_t iterations;      /* FEAST iterations of the slowest slice */
+  int32_t waves;           /* factorization waves issued */
+  int64_t factorizations;  /* shifted band LU factorizations */
+  int64_t rhs_sweeps;      /* (system, column-block) forward+backward solve sweeps */
+  double ms_inertia;       /* wall time per phase (CUDA events on the stream) */
+  double ms_factor;
+  double ms_solve;
+  double ms_rr;
+  double ms_total;
+  double max_residual;     /* over the converged in-slice pairs */
+  double min_rel_error_est;/* reserved */
+} pdeshep_stats;
+
+/* Fill *o with the defaults listed above. */
+void pdeshep_opts_default(pdeshep_opts* o);
+
+/* Human-readable name of a status code (static string). */
+const char* pdeshep_status_string(int status);
+
+/* Last CUDA error message recorded by this thread (static per-thread buffer). */
+const char* pdeshep_last_error(void);
+
+/* Library version string. */
+const char* pdeshep_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Sylvester inertia (Section 3.2; Section 3.1): for every sigma_s counts the  */
+/* eigenvalues of B below sigma_s as the number of negative pivots of the     */
+/* pivot-free LDL^T (real) / LDL^H (complex) factorization of B - sigma_s I,  */
+/* computed in FP64 without fused multiply-add, in a fixed operation order.   */
+/* An exactly zero pivot is replaced by -pivmin, pivmin = DBL_MIN *           */
+/* max(1, amax^2), amax = max over stored band entries of max(|Re|,|Im|).     */
+/*  h_sigma[nsigma] (host) -> h_neg[nsigma] (host, synchronous).              */
+/*  d_pivots: optional device output (NULL to skip) of the nsigma x n pivots  */
+/*  D (row s holds the pivots for sigma_s).                                   */
+/* Workspace: pdeshep_inertia_workspace_size(n, b, is_complex, nsigma).      */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_inertia_workspace_size(int64_t n, int32_t b, int32_t is_complex, int32_t nsigma);
+int pdeshep_inertia(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                    int32_t nsigma, const double* h_sigma, int64_t* h_neg, double* d_pivots,
+                    void* d_work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Eigenvalue enclosures by bisection on inertia (slice boundaries with exact */
+/* counts; the fall-back of the slice proposer).  For each requested index   */
+/* k_t (0-based, ascending order of eigenvalues) returns h_lo[t] < h_hi[t]    */
+/* with count(h_lo[t]) <= k_t < count(h_hi[t]), i.e. lambda_{k_t} in          */
+/* [h_lo, h_hi), and h_hi - h_lo <= rtol * max(1, |h_lo|, |h_hi|).  All       */
+/* enclosures are refined together: each round evaluates `fanout` points per  */
+/* enclosure in one batched inertia launch.                                  */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_bisect_workspace_size(int64_t n, int32_t b, int32_t is_complex, int32_t nidx,
+                                     int32_t fanout);
+int pdeshep_bisect(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                   int32_t nidx, const int64_t* h_idx, double rtol, int32_t fanout,
+                   double* h_lo, double* h_hi, void* d_work, size_t work_bytes, void* stream);
+
+/* Gershgorin interval [lo, hi] of the band (device reduction, synchronous). */
+int pdeshep_gershgorin(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                       double* h_lo, double* h_hi, void* d_work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Quadrature rule (Section 2.2, eqs. (8)-(9)): ne Gauss-Legendre nodes on the */
+/* upper half of the ellipse around [lo, hi] with vertical/horizontal ratio  */
+/* rho: z_k = c + r(cos t_k + i rho sin t_k), w_k = (omega_k r/4)(rho cos t_k */
+/* + i sin t_k), t_k = (pi/2)(1 - x_k), c = (lo+hi)/2, r = (hi-lo)/2, so that  */
+/* the filter is r(x) = 2 Re sum_k w_k/(z_k - x) (the lower half follows by   */
+/* conjugate symmetry).  Host only.                                          */
+/* ------------------------------------------------------------------------ */
+int pdeshep_contour_rule(int32_t ne, double lo, double hi, double rho, pdeshep_c128* h_z,
+                         pdeshep_c128* h_w);
+
+/* ------------------------------------------------------------------------ */
+/* Shifted band solves of eq. (10): for each shift z_s, factor z_s I - B by   */
+/* LU with partial pivoting inside the band (fill to 2b superdiagonals) and   */
+/* solve for nrhs right-hand sides:                                          */
+/*   trans = 0: X_s = (z_s I - B)^{-1} Y;  trans = 1: X_s = (z_s I - B)^{-H} Y */
+/* d_rhs: n x nrhs complex128 (device); d_x: nshift blocks of n x nrhs        */
+/* complex128 (device), block s at d_x + s*n*nrhs.                            */
+/* precision: PDESHEP_FP64 (complex128 arithmetic) or PDESHEP_MIXED (complex64 */
+/* factors and solves, FP32 accumulation; inputs/outputs stay complex128).    */
+/* d_ipiv: optional (NULL to skip) nshift x n int32 pivot rows, 0-based,      */
+/* LAPACK gbtrf meaning: at step k rows k and d_ipiv[k] were interchanged.   */
+/* Returns PDESHEP_SINGULAR if some pivot was exactly zero.                   */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_shifted_solve_workspace_size(int64_t n, int32_t b, int32_t nshift, int32_t nrhs,
+                                            int32_t precision);
+int pdeshep_shifted_solve(int64_t n, int32_t b, int32_t is_complex, const void* d_band,
+                          int64_t ldab, int32_t nshift, const pdeshep_c128* h_shifts, int32_t nrhs,
+                          const pdeshep_c128* d_rhs, int32_t trans, int32_t precision,
+                          pdeshep_c128* d_x, int32_t* d_ipiv, void* d_work, size_t work_bytes,
+                          void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Band times dense block: d_y = B d_x for nrhs columns (FP64).               */
+/* ------------------------------------------------------------------------ */
+int pdeshep_band_matmul(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                        int32_t nrhs, const void* d_x, void* d_y, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* CholQR (orthonormal basis for the Rayleigh-Ritz step of Section 2.2) on a  */
+/* batch of column blocks, FP64: for block t (n x m_t, starting at column     */
+/* col_off[t] of d_q), G = Q^H Q = R^H R (R upper, positive diagonal),        */
+/* Q <- Q R^{-1}; `passes` = 1 (CholQR) or 2 (CholQR2).  d_r: optional        */
+/* output of the last pass's R factors, block t at d_r + sum_{u<t} m_u^2,     */
+/* column-major.  Returns PDESHEP_CHOLQR_BREAKDOWN if a Cholesky pivot is not */
+/* positive.                                                                 */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_cholqr_workspace_size(int64_t n, int32_t nblk, const int32_t* h_m, int32_t is_complex);
+int pdeshep_cholqr(int64_t n, int32_t is_complex, int32_t nblk, const int32_t* h_m, void* d_q,
+                   int32_t passes, void* d_r, void* d_work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched small dense Hermitian eigensolver for A_q W_q = W_q Lambda_q       */
+/* (Section 2.2): block t is an m_t x m_t column-major matrix at offset       */
+/* sum_{u<t} m_u^2 of d_a (overwritten), eigenvalues ascending into d_lam     */
+/* (offset sum_{u<t} m_u), eigenvectors into d_v (same layout as d_a), each   */
+/* scaled so its first largest-magnitude component is real positive.         */
+/* FP64 cyclic Jacobi in parallel (round-robin) order, one thread-block      */
+/* cluster per block; sweeps stop when off(A) <= 1e-14 ||A||_F.               */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_eigh_workspace_size(int32_t nblk, const int32_t* h_m, int32_t is_complex);
+int pdeshep_eigh(int32_t is_complex, int32_t nblk, const int32_t* h_m, void* d_a, double* d_lam,
+                 void* d_v, void* d_work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* FEAST spectrum slicing on the band (Algorithm 1 per slice; slices are     */
+/* level-L1 and quadrature nodes level-L2 of the paper's parallelism, here a  */
+/* batch on one GPU).  Slice i is [h_bounds[i], h_bounds[i+1]).               */
+/*  h_nodes/h_weights: ne complex nodes/weights per slice (slice-major), or   */
+/*    NULL for the Gauss-Legendre ellipse rule of pdeshep_contour_rule.       */
+/*  h_m0[i]: subspace size of slice i (must be >= the slice's exact count;    */
+/*    Section 3.2 suggests max(1.3 m_i, m_i + 10)).                            */
+/*  d_x0: n x sum(m0) start vectors (slice-major column blocks), same type as */
+/*    the band; e.g. random vectors or the previous SCF step's eigenvectors.  */
+/*  Outputs: d_evals[sum(m0)], d_evecs n x sum(m0) (same type as the band);   */
+/*    in slice block i the first h_nfound[i] pairs are the converged in-slice  */
+/*    eigenpairs (ascending), then the other Ritz pairs (ascending).          */
+/*    h_counts[i] = exact inertia count of slice i.  h_stats optional.         */
+/* Returns PDESHEP_NOT_CONVERGED if some slice did not converge (its outputs  */
+/* are the last Ritz pairs; converged slices are valid).                     */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_workspace_size(int64_t n, int32_t b, int32_t is_complex, int32_t nslices,
+                              const int32_t* h_m0, int32_t ne, const pdeshep_opts* opts);
+int pdeshep_band_slice(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                       int32_t nslices, const double* h_bounds, int32_t ne,
+                       const pdeshep_c128* h_nodes, const pdeshep_c128* h_weights,
+                       const int32_t* h_m0, const void* d_x0, void* d_work, size_t work_bytes,
+                       const pdeshep_opts* opts, double* d_evals, void* d_evecs, int32_t* h_counts,
+                       int32_t* h_nfound, pdeshep_stats* h_stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDESHEP_H */

@@ -1,0 +1,360 @@
+"""GB300 (sm_103a) banded FEAST spectrum slicing -- Python binding.
+
+A thin ``ctypes`` layer over ``libpdeshep.so`` (declared in
+``include/pdeshep.h``): it marshals PyTorch CUDA tensors into device pointers,
+sizes and the caller-owned workspace, and calls the C ABI.  Every step of the
+computation runs in the library's CUDA kernels; there is no CPU fallback --
+if the library or a GPU is missing, calls raise.
+
+Layouts (see the header): a band is a tensor of shape ``(n, ldab)`` (float64
+or complex128), row ``j`` holding ``B[j + d, j]`` for ``d = 0..b``; a block of
+``m`` vectors of length ``n`` is a contiguous tensor of shape ``(m, n)`` (row
+``c`` is vector ``c``), i.e. the column-major ``n x m`` matrix of the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpdeshep.so")
+
+FP64 = 0
+MIXED = 1
+REFINE_NONE = 0
+REFINE_RESIDUAL = 1
+
+STATUS = {
+    0: "ok", 1: "not converged", 2: "count mismatch", 3: "cholqr breakdown", 4: "non-finite input",
+    5: "workspace too small", 6: "device timeout", 7: "singular", 8: "cuda error",
+    9: "eig not converged",
+}
+
+EXPORTED = [
+    "pdeshep_opts_default", "pdeshep_status_string", "pdeshep_last_error", "pdeshep_version",
+    "pdeshep_inertia_workspace_size", "pdeshep_inertia", "pdeshep_bisect_workspace_size",
+    "pdeshep_bisect", "pdeshep_gershgorin", "pdeshep_contour_rule",
+    "pdeshep_shifted_solve_workspace_size", "pdeshep_shifted_solve", "pdeshep_band_matmul",
+    "pdeshep_cholqr_workspace_size", "pdeshep_cholqr", "pdeshep_eigh_workspace_size",
+    "pdeshep_eigh", "pdeshep_workspace_size", "pdeshep_band_slice",
+]
+
+
+class c128(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
+        ("refine_policy", C.c_int32), ("rhs_chunk", C.c_int32), ("ellipse_ratio", C.c_double),
+        ("bnorm", C.c_double), ("seed", C.c_uint64), ("hbm_cap_bytes", C.c_size_t),
+        ("autotune", C.c_int32), ("verbose", C.c_int32), ("stream", C.c_void_p),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int32), ("waves", C.c_int32), ("factorizations", C.c_int64),
+        ("rhs_sweeps", C.c_int64), ("ms_inertia", C.c_double), ("ms_factor", C.c_double),
+        ("ms_solve", C.c_double), ("ms_rr", C.c_double), ("ms_total", C.c_double),
+        ("max_residual", C.c_double), ("min_rel_error_est", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PdeshepError(RuntimeError):
+    def __init__(self, fn, status, msg=""):
+        self.status = status
+        text = STATUS.get(status, "invalid argument %d" % -status if status < 0 else str(status))
+        super().__init__(f"{fn} failed: {text}" + (f" ({msg})" if msg else ""))
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``libpdeshep.so`` (build it first with ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run paper_2012_00506_gb300/build.py (nvcc, sm_103a)")
+    lib = C.CDLL(path)
+    P, i64, i32, dbl, sz = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_size_t
+    sig = {
+        "pdeshep_opts_default": (None, [C.POINTER(Opts)]),
+        "pdeshep_status_string": (C.c_char_p, [C.c_int]),
+        "pdeshep_last_error": (C.c_char_p, []),
+        "pdeshep_version": (C.c_char_p, []),
+        "pdeshep_inertia_workspace_size": (sz, [i64, i32, i32, i32]),
+        "pdeshep_inertia": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P, P, sz, P]),
+        "pdeshep_bisect_workspace_size": (sz, [i64, i32, i32, i32, i32]),
+        "pdeshep_bisect": (C.c_int, [i64, i32, i32, P, i64, i32, P, dbl, i32, P, P, P, sz, P]),
+        "pdeshep_gershgorin": (C.c_int, [i64, i32, i32, P, i64, P, P, P, sz, P]),
+        "pdeshep_contour_rule": (C.c_int, [i32, dbl, dbl, dbl, P, P]),
+        "pdeshep_shifted_solve_workspace_size": (sz, [i64, i32, i32, i32, i32]),
+        "pdeshep_shifted_solve": (C.c_int, [i64, i32, i32, P, i64, i32, P, i32, P, i32, i32, P, P, P, sz, P]),
+        "pdeshep_band_matmul": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P]),
+        "pdeshep_cholqr_workspace_size": (sz, [i64, i32, P, i32]),
+        "pdeshep_cholqr": (C.c_int, [i64, i32, i32, P, P, i32, P, P, sz, P]),
+        "pdeshep_eigh_workspace_size": (sz, [i32, P, i32]),
+        "pdeshep_eigh": (C.c_int, [i32, i32, P, P, P, P, P, sz, P]),
+        "pdeshep_workspace_size": (sz, [i64, i32, i32, i32, P, i32, C.POINTER(Opts)]),
+        "pdeshep_band_slice": (C.c_int, [i64, i32, i32, P, i64, i32, P, i32, P, P, P, P, P, sz,
+                                         C.POINTER(Opts), P, P, P, P, C.POINTER(Stats)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _check(fn, st):
+    if st != 0:
+        msg = load().pdeshep_last_error().decode() if st == 8 else ""
+        raise PdeshepError(fn, st, msg)
+
+
+def _workspace(nbytes, device):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _band_args(band, b):
+    n, ldab = band.shape
+    b = ldab - 1 if b is None else int(b)
+    assert band.is_cuda and band.is_contiguous(), "band must be a contiguous CUDA tensor (n, ldab)"
+    cplx = 1 if band.is_complex() else 0
+    return n, b, cplx, ldab
+
+
+# ---------------------------------------------------------------------------- entry points
+def version() -> str:
+    return load().pdeshep_version().decode()
+
+
+def inertia(band, sigmas, b=None, pivots=False, stream=None):
+    """Eigenvalue counts below each sigma (pivot-free LDL^T inertia, FP64)."""
+    torch = _torch()
+    lib = load()
+    n, b, cplx, ldab = _band_args(band, b)
+    sig = np.ascontiguousarray(np.atleast_1d(np.asarray(sigmas, dtype=np.float64)))
+    neg = np.zeros(sig.size, dtype=np.int64)
+    ws = _workspace(lib.pdeshep_inertia_workspace_size(n, b, cplx, sig.size), band.device)
+    piv = torch.empty((sig.size, n), dtype=torch.float64, device=band.device) if pivots else None
+    st = lib.pdeshep_inertia(n, b, cplx, _ptr(band), ldab, sig.size, _np_ptr(sig), _np_ptr(neg), _ptr(piv),
+                             _ptr(ws), ws.numel(), _stream(stream))
+    _check("pdeshep_inertia", st)
+    return (neg, piv) if pivots else neg
+
+
+def bisect(band, idx, rtol=1e-12, fanout=8, b=None, stream=None):
+    """Enclosures [lo, hi) of the eigenvalues with the given 0-based indices."""
+    lib = load()
+    n, b, cplx, ldab = _band_args(band, b)
+    idx = np.ascontiguousarray(np.atleast_1d(np.asarray(idx, dtype=np.int64)))
+    lo = np.zeros(idx.size)
+    hi = np.zeros(idx.size)
+    ws = _workspace(lib.pdeshep_bisect_workspace_size(n, b, cplx, idx.size, fanout), band.device)
+    st = lib.pdeshep_bisect(n, b, cplx, _ptr(band), ldab, idx.size, _np_ptr(idx), float(rtol), int(fanout),
+                            _np_ptr(lo), _np_ptr(hi), _ptr(ws), ws.numel(), _stream(stream))
+    _check("pdeshep_bisect", st)
+    return lo, hi
+
+
+def gershgorin(band, b=None, stream=None):
+    lib = load()
+    n, b, cplx, ldab = _band_args(band, b)
+    lo, hi = C.c_double(), C.c_double()
+    ws = _workspace(4096, band.device)
+    st = lib.pdeshep_gershgorin(n, b, cplx, _ptr(band), ldab, C.byref(lo), C.byref(hi), _ptr(ws), ws.numel(),
+                                _stream(stream))
+    _check("pdeshep_gershgorin", st)
+    return lo.value, hi.value
+
+
+def contour_rule(ne, lo, hi, rho=0.3):
+    """Gauss-Legendre nodes/weights on the upper half ellipse (host computation)."""
+    lib = load()
+    z = np.zeros(ne, dtype=np.complex128)
+    w = np.zeros(ne, dtype=np.complex128)
+    _check("pdeshep_contour_rule", lib.pdeshep_contour_rule(int(ne), float(lo), float(hi), float(rho),
+                                                            _np_ptr(z), _np_ptr(w)))
+    return z, w
+
+
+def shifted_solve(band, shifts, rhs, trans=0, precision=FP64, b=None, return_ipiv=False, stream=None):
+    """X_s = (z_s I - B)^{-1} Y (trans=0) or (z_s I - B)^{-H} Y (trans=1).
+
+    ``rhs``: complex128 tensor (nrhs, n).  Returns complex128 tensor (nshift, nrhs, n).
+    """
+    torch = _torch()
+    lib = load()
+    n, b, cplx, ldab = _band_args(band, b)
+    sh = np.ascontiguousarray(np.atleast_1d(np.asarray(shifts, dtype=np.complex128)))
+    rhs = rhs.to(torch.complex128).contiguous()
+    nrhs = rhs.shape[0]
+    assert rhs.shape[1] == n
+    x = torch.empty((sh.size, nrhs, n), dtype=torch.complex128, device=band.device)
+    ipiv = torch.empty((sh.size, n), dtype=torch.int32, device=band.device) if return_ipiv else None
+    ws = _workspace(lib.pdeshep_shifted_solve_workspace_size(n, b, sh.size, nrhs, precision), band.device)
+    st = lib.pdeshep_shifted_solve(n, b, cplx, _ptr(band), ldab, sh.size, _np_ptr(sh), nrhs, _ptr(rhs),
+                                   int(trans), int(precision), _ptr(x), _ptr(ipiv), _ptr(ws), ws.numel(),
+                                   _stream(stream))
+    _check("pdeshep_shifted_solve", st)
+    return (x, ipiv) if return_ipiv else x
+
+
+def band_matmul(band, X, b=None, stream=None):
+    """Y = B X; X of shape (m, n) (float64 for real B, complex128 for complex B)."""
+    torch = _torch()
+    lib = load()
+    n, b, cplx, ldab = _band_args(band, b)
+    X = X.to(band.dtype).contiguous()
+    Y = torch.empty_like(X)
+    st = lib.pdeshep_band_matmul(n, b, cplx, _ptr(band), ldab, X.shape[0], _ptr(X), _ptr(Y), _stream(stream))
+    _check("pdeshep_band_matmul", st)
+    return Y
+
+
+def cholqr(Q, sizes, passes=2, stream=None):
+    """CholQR on column blocks of Q (shape (sum(sizes), n)); returns (Q_orth, [R_t])."""
+    torch = _torch()
+    lib = load()
+    Q = Q.clone().contiguous()
+    n = Q.shape[1]
+    cplx = 1 if Q.is_complex() else 0
+    m = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32))
+    R = torch.empty(int(np.sum(m.astype(np.int64) ** 2)), dtype=Q.dtype, device=Q.device)
+    ws = _workspace(lib.pdeshep_cholqr_workspace_size(n, m.size, _np_ptr(m), cplx), Q.device)
+    st = lib.pdeshep_cholqr(n, cplx, m.size, _np_ptr(m), _ptr(Q), int(passes), _ptr(R), _ptr(ws), ws.numel(),
+                            _stream(stream))
+    _check("pdeshep_cholqr", st)
+    out, off = [], 0
+    for mt in m:
+        out.append(R[off: off + mt * mt].reshape(mt, mt).T)  # column-major -> (row, col)
+        off += mt * mt
+    return Q, out
+
+
+def eigh(blocks, stream=None):
+    """Batched Hermitian eigensolver: list of (m, m) tensors -> list of (lam, V) (V[:, k] eigenvector)."""
+    torch = _torch()
+    lib = load()
+    dt = blocks[0].dtype
+    cplx = 1 if blocks[0].is_complex() else 0
+    m = np.asarray([b_.shape[0] for b_ in blocks], dtype=np.int32)
+    A = torch.cat([b_.to(dt).T.contiguous().reshape(-1) for b_ in blocks])  # column-major blocks
+    lam = torch.empty(int(m.sum()), dtype=torch.float64, device=A.device)
+    V = torch.empty_like(A)
+    ws = _workspace(lib.pdeshep_eigh_workspace_size(m.size, _np_ptr(m), cplx), A.device)
+    st = lib.pdeshep_eigh(cplx, m.size, _np_ptr(m), _ptr(A), _ptr(lam), _ptr(V), _ptr(ws), ws.numel(),
+                          _stream(stream))
+    _check("pdeshep_eigh", st)
+    out, off, voff = [], 0, 0
+    for mt in m:
+        out.append((lam[voff: voff + mt], V[off: off + mt * mt].reshape(mt, mt).T))
+        off += mt * mt
+        voff += mt
+    return out
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load().pdeshep_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def workspace_size(n, b, is_complex, m0, ne=8, opts=None) -> int:
+    lib = load()
+    o = opts if opts is not None else default_opts()
+    m = np.ascontiguousarray(np.asarray(m0, dtype=np.int32))
+    return int(lib.pdeshep_workspace_size(n, b, int(is_complex), m.size, _np_ptr(m), ne, C.byref(o)))
+
+
+@dataclass
+class SliceResult:
+    status: int
+    evals: object
+    evecs: object
+    counts: np.ndarray
+    nfound: np.ndarray
+    stats: dict = field(default_factory=dict)
+    m0: np.ndarray = None
+
+    def slice_pairs(self, i):
+        """(eigenvalues, eigenvectors (k, n)) of the converged pairs of slice i."""
+        off = int(np.sum(self.m0[:i]))
+        k = int(self.nfound[i])
+        return self.evals[off: off + k], self.evecs[off: off + k]
+
+
+def band_slice(band, bounds, m0, x0, ne=8, nodes=None, weights=None, workspace=None, stream=None,
+               b=None, raise_on_error=True, **opts) -> SliceResult:
+    """FEAST on every slice [bounds[i], bounds[i+1]) (Algorithm 1 per slice).
+
+    ``x0``: start vectors, tensor (sum(m0), n) of the band's dtype.  Options:
+    any ``Opts`` field (tol, max_iter, precision, refine_policy, ellipse_ratio, bnorm,
+    hbm_cap_bytes, ...).
+    """
+    torch = _torch()
+    lib = load()
+    n, b, cplx, ldab = _band_args(band, b)
+    bnd = np.ascontiguousarray(np.asarray(bounds, dtype=np.float64))
+    K = bnd.size - 1
+    m = np.ascontiguousarray(np.asarray(m0, dtype=np.int32))
+    assert m.size == K
+    o = default_opts(**opts)
+    o.stream = _stream(stream).value
+    x0 = x0.to(band.dtype).contiguous()
+    assert x0.shape == (int(m.sum()), n)
+    if nodes is not None:
+        nz = np.ascontiguousarray(np.asarray(nodes, dtype=np.complex128).reshape(-1))
+        nw = np.ascontiguousarray(np.asarray(weights, dtype=np.complex128).reshape(-1))
+        ne = nz.size // K
+    else:
+        nz = nw = None
+    if workspace is None:
+        workspace = _workspace(lib.pdeshep_workspace_size(n, b, cplx, K, _np_ptr(m), ne, C.byref(o)), band.device)
+    evals = torch.empty(int(m.sum()), dtype=torch.float64, device=band.device)
+    evecs = torch.empty_like(x0)
+    counts = np.zeros(K, dtype=np.int32)
+    nfound = np.zeros(K, dtype=np.int32)
+    stats = Stats()
+    st = lib.pdeshep_band_slice(n, b, cplx, _ptr(band), ldab, K, _np_ptr(bnd), int(ne),
+                                _np_ptr(nz) if nz is not None else None,
+                                _np_ptr(nw) if nw is not None else None, _np_ptr(m), _ptr(x0),
+                                _ptr(workspace), workspace.numel(), C.byref(o), _ptr(evals), _ptr(evecs),
+                                _np_ptr(counts), _np_ptr(nfound), C.byref(stats))
+    if st != 0 and (raise_on_error and st not in (1,)):
+        _check("pdeshep_band_slice", st)
+    return SliceResult(st, evals, evecs, counts, nfound, stats.as_dict(), m)

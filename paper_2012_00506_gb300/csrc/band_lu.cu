@@ -1,0 +1,630 @@
+// band_lu.cu -- shifted band LU with partial pivoting inside the band and the
+// multi-right-hand-side solves of eq. (10) of arXiv 2012.00506:
+//     (z_j I - B) Q^(j) = X~,   j = 1..n_e.
+//
+// The band of semi-bandwidth b is handled as a block band of T x T tiles
+// (T = 32, block semi-bandwidth bt = ceil(b/T)).  Partial pivoting over the
+// rows k..k+b of column k is the same as pivoting over the (bt+1)T rows of
+// the block panel, because the rows past k+b are structurally zero there, so
+// the pivots equal those of LAPACK's gbtrf (first maximum of |Re|+|Im|).
+// The U factor fills to 2b superdiagonals (2bt tiles).
+//
+// factor_kernel: one thread block per shifted system (the L2 level of the
+//   paper's parallelism is the batch dimension).  Per block column K: the
+//   panel ((bt+1)T x T) is factored in shared memory (warp-shuffle pivot
+//   search, row swaps, rank-1 updates); the panel permutation is gathered
+//   into each trailing block column on load; the top tile is multiplied by
+//   the inverted unit-lower diagonal block and the tiles below get the
+//   T-deep Schur update.  The inverses of the diagonal blocks are stored so
+//   that every solve step is a tile product.
+// solve kernels: one thread block per (system, 32-column block of right-hand
+//   sides); forward L sweep then backward U sweep (trans = 0), or U^H then
+//   L^H and the inverse permutation (trans = 1, the conjugate node conj(z)
+//   of a Hermitian band).  Factor tiles stream from L2/HBM through shared
+//   memory; each is reused by the 32 right-hand sides of the block.
+#include "band_lu.cuh"
+
+namespace pdeshep {
+
+constexpr int kThreads = 256;
+constexpr int kCW = 32;  // right-hand sides per solve thread block
+constexpr int kLdt = kTile + 1;
+
+// ---------------------------------------------------------------------------
+// init: tiles of z I - B (identity padding past n, zero fill slots)
+// ---------------------------------------------------------------------------
+template <typename C>
+__global__ void __launch_bounds__(kThreads) init_factor_kernel(FactorGeom g, int cplx,
+                                                              const double* __restrict__ band,
+                                                              int64_t ldab, const SysDesc* sys,
+                                                              char* arena) {
+  using R = typename real_of<C>::type;
+  const int s = blockIdx.y;
+  const SysDesc d = sys[s];
+  FactorPtr<C> f = factor_ptr<C>(g, arena + d.factor_off);
+  const int T = kTile;
+  for (int64_t t = blockIdx.x; t < g.tiles; t += gridDim.x) {
+    const int I = (int)(t / g.nslot);
+    const int J = I + (int)(t % g.nslot) - g.bt;
+    C* tile = f.tiles + t * g.tile_elems;
+    for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+      const int r = e % T, c = e / T;
+      const int64_t i = (int64_t)I * T + r, j = (int64_t)J * T + c;
+      R vr = 0, vi = 0;
+      if (J >= 0 && J < g.Nb) {
+        if (i >= g.n || j >= g.n) {
+          vr = (i == j) ? R(1) : R(0);
+        } else {
+          const int64_t dd = i - j;
+          if (dd >= -g.b && dd <= g.b) {
+            double br, bi;
+            if (dd >= 0) {
+              if (cplx) {
+                br = band[2 * (dd + j * ldab)];
+                bi = band[2 * (dd + j * ldab) + 1];
+              } else {
+                br = band[dd + j * ldab];
+                bi = 0.0;
+              }
+            } else {
+              if (cplx) {
+                br = band[2 * (-dd + i * ldab)];
+                bi = -band[2 * (-dd + i * ldab) + 1];
+              } else {
+                br = band[-dd + i * ldab];
+                bi = 0.0;
+              }
+            }
+            if (i == j) {
+              vr = (R)(d.zre - br);
+              vi = (R)d.zim;
+            } else {
+              vr = (R)(-br);
+              vi = (R)(-bi);
+            }
+          }
+        }
+      }
+      tile[e] = cmk<C>(vr, vi);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// factorization: one thread block per system
+// ---------------------------------------------------------------------------
+template <typename C>
+__global__ void __launch_bounds__(kThreads) factor_kernel(FactorGeom g, const SysDesc* sys,
+                                                         char* arena, int* status, int32_t* ipiv) {
+  using R = typename real_of<C>::type;
+  extern __shared__ __align__(16) char smem[];
+  const int T = kTile;
+  const int bt = g.bt;
+  const int Pmax = (bt + 1) * T;
+  const int ldp = Pmax + 1;
+  C* Pan = (C*)smem;
+  C* Cb = Pan + (size_t)ldp * T;
+  C* Li = Cb + (size_t)ldp * T;
+  C* Ui = Li + T * T;
+  int* perm = (int*)(Ui + T * T);
+  __shared__ int sh_p;
+  __shared__ R sh_best;
+  __shared__ int sh_status;
+
+  const int sidx = blockIdx.x;
+  const SysDesc d = sys[sidx];
+  FactorPtr<C> f = factor_ptr<C>(g, arena + d.factor_off);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) sh_status = 0;
+
+  for (int K = 0; K < g.Nb; ++K) {
+    const int nbb = min(bt, g.Nb - 1 - K);
+    const int nbr = min(2 * bt, g.Nb - 1 - K);
+    const int P = (nbb + 1) * T;
+    // load panel tiles (K+q, K)
+    for (int e = tid; e < P * T; e += blockDim.x) {
+      const int q = (e / (T * T)), w = e % (T * T);
+      const int r = w % T, c = w / T;
+      const C* tile = f.tiles + g.tile_index(K + q, K) * g.tile_elems;
+      Pan[q * T + r + c * ldp] = tile[w];
+    }
+    for (int r = tid; r < P; r += blockDim.x) perm[r] = r;
+    __syncthreads();
+    // panel LU with partial pivoting
+    for (int c = 0; c < T; ++c) {
+      if (warp == 0) {
+        R best = R(-1);
+        int idx = c;
+        for (int r = c + lane; r < P; r += 32) {
+          R v = cabs1(Pan[r + c * ldp]);
+          if (v > best) {
+            best = v;
+            idx = r;
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          R ob = __shfl_down_sync(0xffffffffu, best, o);
+          int oi = __shfl_down_sync(0xffffffffu, idx, o);
+          if (ob > best || (ob == best && oi < idx)) {
+            best = ob;
+            idx = oi;
+          }
+        }
+        if (lane == 0) {
+          sh_p = idx;
+          sh_best = best;
+        }
+      }
+      __syncthreads();
+      const int p = sh_p;
+      const R best = sh_best;
+      if (p != c) {
+        for (int j = tid; j < T; j += blockDim.x) {
+          C t = Pan[c + j * ldp];
+          Pan[c + j * ldp] = Pan[p + j * ldp];
+          Pan[p + j * ldp] = t;
+        }
+        if (tid == 0) {
+          int t = perm[c];
+          perm[c] = perm[p];
+          perm[p] = t;
+        }
+      }
+      if (tid == 0) {
+        const int64_t k = (int64_t)K * T + c;
+        if (ipiv && k < g.n) ipiv[(int64_t)sidx * g.n + k] = (int32_t)((int64_t)K * T + p);
+        if (!(best > R(0)) && sh_status == 0) sh_status = (int)(k + 1);
+      }
+      __syncthreads();
+      if (best > R(0)) {
+        const C inv = crecip(Pan[c + c * ldp]);
+        for (int r = c + 1 + tid; r < P; r += blockDim.x) {
+          const C l = cmul(Pan[r + c * ldp], inv);
+          Pan[r + c * ldp] = l;
+          for (int j = c + 1; j < T; ++j) cfms(Pan[r + j * ldp], l, Pan[c + j * ldp]);
+        }
+      }
+      __syncthreads();
+    }
+    // write back the panel (L multipliers and the packed diagonal block)
+    for (int e = tid; e < P * T; e += blockDim.x) {
+      const int q = (e / (T * T)), w = e % (T * T);
+      const int r = w % T, c = w / T;
+      C* tile = f.tiles + g.tile_index(K + q, K) * g.tile_elems;
+      tile[w] = Pan[q * T + r + c * ldp];
+    }
+    {
+      int16_t* pg = f.perm + (int64_t)K * Pmax;
+      for (int r = tid; r < Pmax; r += blockDim.x) pg[r] = (int16_t)(r < P ? perm[r] : r);
+    }
+    // inverses of the unit-lower and upper diagonal blocks
+    if (tid < T) {
+      const int j = tid;
+      for (int i = 0; i < T; ++i) Li[i + j * T] = cmk<C>(i == j ? R(1) : R(0), R(0));
+      for (int i = j + 1; i < T; ++i) {
+        C s = cmk<C>(0, 0);
+        for (int k = j; k < i; ++k) cfma(s, Pan[i + k * ldp], Li[k + j * T]);
+        Li[i + j * T] = cmk<C>(-s.x, -s.y);
+      }
+    } else if (tid >= 32 && tid < 32 + T) {
+      const int j = tid - 32;
+      for (int i = 0; i < T; ++i) Ui[i + j * T] = cmk<C>(0, 0);
+      Ui[j + j * T] = crecip(Pan[j + j * ldp]);
+      for (int i = j - 1; i >= 0; --i) {
+        C s = cmk<C>(0, 0);
+        for (int k = i + 1; k <= j; ++k) cfma(s, Pan[i + k * ldp], Ui[k + j * T]);
+        const C ri = crecip(Pan[i + i * ldp]);
+        Ui[i + j * T] = cmk<C>(-(s.x * ri.x - s.y * ri.y), -(s.x * ri.y + s.y * ri.x));
+      }
+    }
+    __syncthreads();
+    {
+      C* li = f.inv + (int64_t)(2 * K) * g.tile_elems;
+      C* ui = f.inv + (int64_t)(2 * K + 1) * g.tile_elems;
+      for (int e = tid; e < T * T; e += blockDim.x) {
+        li[e] = Li[e];
+        ui[e] = Ui[e];
+      }
+    }
+    // trailing block columns K+1 .. K+nbr
+    for (int jb = 1; jb <= nbr; ++jb) {
+      const int Jc = K + jb;
+      for (int e = tid; e < P * T; e += blockDim.x) {
+        const int r = e % P, c = e / P;
+        const int sr = perm[r];
+        const int q = sr / T, rr = sr % T;
+        const C* tile = f.tiles + g.tile_index(K + q, Jc) * g.tile_elems;
+        Cb[r + c * ldp] = tile[rr + c * T];
+      }
+      __syncthreads();
+      // top block: U(K, Jc) = Linv * Cb[0:T]
+      C acc[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[jj] = cmk<C>(0, 0);
+      for (int k = 0; k < T; ++k) {
+        const C a = Li[lane + k * T];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) cfma(acc[jj], a, Cb[k + (warp + 8 * jj) * ldp]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) Cb[lane + (warp + 8 * jj) * ldp] = acc[jj];
+      __syncthreads();
+      // rows below: Cb[T:P] -= L(panel rows T:P) * U(K, Jc)
+      for (int q = 1; q <= nbb; ++q) {
+        const int r = q * T + lane;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[jj] = Cb[r + (warp + 8 * jj) * ldp];
+        for (int k = 0; k < T; ++k) {
+          const C a = Pan[r + k * ldp];
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) cfms(acc[jj], a, Cb[k + (warp + 8 * jj) * ldp]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) Cb[r + (warp + 8 * jj) * ldp] = acc[jj];
+      }
+      __syncthreads();
+      for (int e = tid; e < P * T; e += blockDim.x) {
+        const int r = e % P, c = e / P;
+        const int q = r / T, rr = r % T;
+        C* tile = f.tiles + g.tile_index(K + q, Jc) * g.tile_elems;
+        tile[rr + c * T] = Cb[r + c * ldp];
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) status[sidx] = sh_status;
+}
+
+// ---------------------------------------------------------------------------
+// solve helpers
+// ---------------------------------------------------------------------------
+// Load one T x T tile into Tb (ld kLdt); conjugate-transposed if CT.
+template <typename C, bool CT>
+__device__ __forceinline__ void load_tile(C* Tb, const C* __restrict__ src) {
+  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+    const int r = e % kTile, c = e / kTile;
+    const C v = src[e];
+    if (CT)
+      Tb[c + r * kLdt] = cconj(v);
+    else
+      Tb[r + c * kLdt] = v;
+  }
+}
+
+// acc[jj] += / -= Tb(lane, :) * Bm(:, col_jj), Bm with leading dimension ldb.
+template <typename C, bool SUB>
+__device__ __forceinline__ void tile_mul(C acc[4], const C* Tb, const C* Bm, int ldb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 8
+  for (int k = 0; k < kTile; ++k) {
+    const C a = Tb[lane + k * kLdt];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const C bv = Bm[k + (warp + 8 * jj) * ldb];
+      if (SUB)
+        cfms(acc[jj], a, bv);
+      else
+        cfma(acc[jj], a, bv);
+    }
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void load_rhs_block(C* dst, int ldd, const C* __restrict__ Y, int64_t n,
+                                               int64_t row0, int col0, int ncols) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int c = warp + 8 * jj;
+    const int64_t i = row0 + lane;
+    C v = cmk<C>(0, 0);
+    if (i < n && col0 + c < ncols) v = Y[i + (int64_t)(col0 + c) * n];
+    dst[lane + c * ldd] = v;
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void store_rows(C* __restrict__ X, int64_t n, int64_t row0, int col0,
+                                           int ncols, const C acc[4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int c = warp + 8 * jj;
+    const int64_t i = row0 + lane;
+    if (i < n && col0 + c < ncols) X[i + (int64_t)(col0 + c) * n] = acc[jj];
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void load_acc(C acc[4], const C* __restrict__ X, int64_t n, int64_t row0,
+                                         int col0, int ncols) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int c = warp + 8 * jj;
+    const int64_t i = row0 + lane;
+    acc[jj] = (i < n && col0 + c < ncols) ? X[i + (int64_t)(col0 + c) * n] : cmk<C>(0, 0);
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void put_acc(C* dst, int ldd, const C acc[4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) dst[lane + (warp + 8 * jj) * ldd] = acc[jj];
+}
+
+template <typename C>
+__device__ __forceinline__ void get_acc(C acc[4], const C* src, int lds) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) acc[jj] = src[lane + (warp + 8 * jj) * lds];
+}
+
+// ---------------------------------------------------------------------------
+// trans = 0: forward (P, L) then backward (U)
+// ---------------------------------------------------------------------------
+template <typename C>
+__global__ void __launch_bounds__(kThreads) solve_n_kernel(FactorGeom g, const SysDesc* sys,
+                                                          const char* arena, const C* rhs, C* out) {
+  extern __shared__ __align__(16) char smem[];
+  const int T = kTile, bt = g.bt;
+  const int Pmax = (bt + 1) * T;
+  const int ldw = Pmax;
+  const SysDesc d = sys[blockIdx.y];
+  const int col0 = blockIdx.x * kCW;
+  if (col0 >= d.ncols) return;
+  const FactorPtr<C> f = factor_ptr<C>(g, (char*)arena + d.factor_off);
+  const C* Y = rhs + d.rhs_off;
+  C* X = out + d.out_off;
+  const int64_t n = g.n;
+  const int ncols = d.ncols;
+  const int tid = threadIdx.x;
+
+  C* Tb = (C*)smem;                    // T x kLdt
+  C* tS = Tb + T * kLdt;               // T x kCW
+  C* U0 = tS + T * kCW;                // union area
+  C* Wn = U0;                          // Pmax x kCW
+  C* G = U0 + (size_t)Pmax * kCW;      // Pmax x kCW
+  C* xwin = U0;                        // 2bt slots of T x kCW
+
+  // ---------------- forward ----------------
+  {
+    const int nbb0 = min(bt, g.Nb - 1);
+    for (int q = 0; q <= nbb0; ++q) load_rhs_block(Wn + q * T, ldw, Y, n, (int64_t)q * T, col0, ncols);
+    __syncthreads();
+    for (int K = 0; K < g.Nb; ++K) {
+      const int nbb = min(bt, g.Nb - 1 - K);
+      const int P = (nbb + 1) * T;
+      const int16_t* pm = f.perm + (int64_t)K * Pmax;
+      for (int e = tid; e < P * kCW; e += blockDim.x) {
+        const int r = e % P, c = e / P;
+        G[r + c * ldw] = Wn[pm[r] + c * ldw];
+      }
+      load_tile<C, false>(Tb, f.inv + (int64_t)(2 * K) * g.tile_elems);
+      __syncthreads();
+      C acc[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[jj] = cmk<C>(0, 0);
+      tile_mul<C, false>(acc, Tb, G, ldw);
+      __syncthreads();
+      put_acc(G, ldw, acc);
+      store_rows(X, n, (int64_t)K * T, col0, ncols, acc);
+      __syncthreads();
+      for (int q = 1; q <= nbb; ++q) {
+        load_tile<C, false>(Tb, f.tiles + g.tile_index(K + q, K) * g.tile_elems);
+        __syncthreads();
+        get_acc(acc, G + q * T, ldw);
+        tile_mul<C, true>(acc, Tb, G, ldw);
+        put_acc(G + q * T, ldw, acc);
+        __syncthreads();
+      }
+      if (K + 1 < g.Nb) {
+        for (int e = tid; e < nbb * T * kCW; e += blockDim.x) {
+          const int r = e % (nbb * T), c = e / (nbb * T);
+          Wn[r + c * ldw] = G[T + r + c * ldw];
+        }
+        const int nbn = min(bt, g.Nb - 2 - K);
+        if (nbn == nbb) load_rhs_block(Wn + nbb * T, ldw, Y, n, (int64_t)(K + bt + 1) * T, col0, ncols);
+        __syncthreads();
+      }
+    }
+  }
+  // ---------------- backward ----------------
+  {
+    const int ns = 2 * bt;
+    for (int K = g.Nb - 1; K >= 0; --K) {
+      const int nbr = min(2 * bt, g.Nb - 1 - K);
+      C acc[4];
+      load_acc(acc, X, n, (int64_t)K * T, col0, ncols);
+      for (int q = 1; q <= nbr; ++q) {
+        load_tile<C, false>(Tb, f.tiles + g.tile_index(K, K + q) * g.tile_elems);
+        __syncthreads();
+        tile_mul<C, true>(acc, Tb, xwin + ((K + q) % ns) * T * kCW, T);
+        __syncthreads();
+      }
+      put_acc(tS, T, acc);
+      load_tile<C, false>(Tb, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
+      __syncthreads();
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[jj] = cmk<C>(0, 0);
+      tile_mul<C, false>(acc, Tb, tS, T);
+      put_acc(xwin + (K % ns) * T * kCW, T, acc);
+      store_rows(X, n, (int64_t)K * T, col0, ncols, acc);
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// trans = 1: forward U^H, backward L^H then P^T
+// ---------------------------------------------------------------------------
+template <typename C>
+__global__ void __launch_bounds__(kThreads) solve_c_kernel(FactorGeom g, const SysDesc* sys,
+                                                          const char* arena, const C* rhs, C* out) {
+  extern __shared__ __align__(16) char smem[];
+  const int T = kTile, bt = g.bt;
+  const int Pmax = (bt + 1) * T;
+  const int ldw = Pmax;
+  const SysDesc d = sys[blockIdx.y];
+  const int col0 = blockIdx.x * kCW;
+  if (col0 >= d.ncols) return;
+  const FactorPtr<C> f = factor_ptr<C>(g, (char*)arena + d.factor_off);
+  const C* Y = rhs + d.rhs_off;
+  C* X = out + d.out2_off;
+  const int64_t n = g.n;
+  const int ncols = d.ncols;
+  const int tid = threadIdx.x;
+
+  C* Tb = (C*)smem;
+  C* tS = Tb + T * kLdt;
+  C* U0 = tS + T * kCW;
+  C* wwin = U0;                        // 2bt slots of T x kCW
+  C* V = U0;                           // Pmax x kCW
+  C* Vn = U0 + (size_t)Pmax * kCW;     // Pmax x kCW
+
+  // ---------------- forward: U^H w = y ----------------
+  {
+    const int ns = 2 * bt;
+    for (int K = 0; K < g.Nb; ++K) {
+      C acc[4];
+      load_acc(acc, Y, n, (int64_t)K * T, col0, ncols);
+      const int nq = min(2 * bt, K);
+      for (int q = 1; q <= nq; ++q) {
+        load_tile<C, true>(Tb, f.tiles + g.tile_index(K - q, K) * g.tile_elems);
+        __syncthreads();
+        tile_mul<C, true>(acc, Tb, wwin + ((K - q) % ns) * T * kCW, T);
+        __syncthreads();
+      }
+      put_acc(tS, T, acc);
+      load_tile<C, true>(Tb, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
+      __syncthreads();
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[jj] = cmk<C>(0, 0);
+      tile_mul<C, false>(acc, Tb, tS, T);
+      put_acc(wwin + (K % ns) * T * kCW, T, acc);
+      store_rows(X, n, (int64_t)K * T, col0, ncols, acc);
+      __syncthreads();
+    }
+  }
+  // ---------------- backward: x = P_0^T E_0^H ... P_{Nb-1}^T E_{Nb-1}^H w ----------------
+  {
+    for (int K = g.Nb - 1; K >= 0; --K) {
+      const int nbb = min(bt, g.Nb - 1 - K);
+      const int P = (nbb + 1) * T;
+      C acc[4];
+      load_acc(acc, X, n, (int64_t)K * T, col0, ncols);
+      for (int q = 1; q <= nbb; ++q) {
+        load_tile<C, true>(Tb, f.tiles + g.tile_index(K + q, K) * g.tile_elems);
+        __syncthreads();
+        tile_mul<C, true>(acc, Tb, V + q * T, ldw);
+        __syncthreads();
+      }
+      put_acc(tS, T, acc);
+      load_tile<C, true>(Tb, f.inv + (int64_t)(2 * K) * g.tile_elems);
+      __syncthreads();
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[jj] = cmk<C>(0, 0);
+      tile_mul<C, false>(acc, Tb, tS, T);
+      put_acc(V, ldw, acc);
+      __syncthreads();
+      const int16_t* pm = f.perm + (int64_t)K * Pmax;
+      for (int e = tid; e < P * kCW; e += blockDim.x) {
+        const int r = e % P, c = e / P;
+        Vn[pm[r] + c * ldw] = V[r + c * ldw];
+      }
+      __syncthreads();
+      if (nbb == bt) {
+        // block K+bt is final
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[jj] = Vn[bt * T + (tid & 31) + ((tid >> 5) + 8 * jj) * ldw];
+        store_rows(X, n, (int64_t)(K + bt) * T, col0, ncols, acc);
+      }
+      const int nbn = min(bt, g.Nb - K);  // window blocks kept for step K-1 (beyond its top block)
+      for (int e = tid; e < nbn * T * kCW; e += blockDim.x) {
+        const int r = e % (nbn * T), c = e / (nbn * T);
+        V[T + r + c * ldw] = Vn[r + c * ldw];
+      }
+      __syncthreads();
+    }
+    // remaining window blocks 0 .. min(bt, Nb)-1 sit in V[T : ...]
+    const int nrem = min(bt, g.Nb);
+    for (int q = 0; q < nrem; ++q) {
+      C acc[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[jj] = V[T + q * T + (tid & 31) + ((tid >> 5) + 8 * jj) * ldw];
+      store_rows(X, n, (int64_t)q * T, col0, ncols, acc);
+    }
+  }
+}
+
+size_t solve_smem_bytes(const FactorGeom& g, int chunk, size_t es, int trans) {
+  (void)trans;
+  (void)chunk;
+  const int T = kTile;
+  const size_t Pmax = (size_t)(g.bt + 1) * T;
+  size_t uni = 2 * Pmax * kCW;
+  size_t win = (size_t)2 * g.bt * T * kCW;
+  if (win > uni) uni = win;
+  return es * ((size_t)T * kLdt + (size_t)T * kCW + uni);
+}
+
+static size_t factor_smem_bytes(const FactorGeom& g, size_t es) {
+  const int T = kTile;
+  const size_t Pmax = (size_t)(g.bt + 1) * T;
+  return es * (2 * (Pmax + 1) * T + 2 * (size_t)T * T) + sizeof(int) * Pmax;
+}
+
+template <typename C>
+int launch_factor(const FactorGeom& g, int cplx, const void* band, int64_t ldab, int nsys,
+                  const SysDesc* d_sys, char* factor_arena, int* d_status, int32_t* d_ipiv,
+                  cudaStream_t st) {
+  if (nsys <= 0) return 0;
+  dim3 gi((unsigned)(g.tiles < 4096 ? g.tiles : 4096), (unsigned)nsys);
+  init_factor_kernel<C><<<gi, kThreads, 0, st>>>(g, cplx, (const double*)band, ldab, d_sys, factor_arena);
+  PD_CK_LAUNCH();
+  const size_t smem = factor_smem_bytes(g, sizeof(C));
+  if (smem > 227 * 1024) {
+    set_last_error_msg("band too wide for the factor kernel's shared memory");
+    return PDESHEP_CUDA_ERROR;
+  }
+  PD_CK(cudaFuncSetAttribute(factor_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  factor_kernel<C><<<nsys, kThreads, smem, st>>>(g, d_sys, factor_arena, d_status, d_ipiv);
+  PD_CK_LAUNCH();
+  return 0;
+}
+
+template <typename C>
+int launch_solve(const FactorGeom& g, int trans, int nsys, int max_cols, const SysDesc* d_sys,
+                 const char* factor_arena, const C* rhs_arena, C* out_arena, int chunk,
+                 cudaStream_t st) {
+  (void)chunk;
+  if (nsys <= 0 || max_cols <= 0) return 0;
+  const size_t smem = solve_smem_bytes(g, kCW, sizeof(C), trans);
+  if (smem > 227 * 1024) {
+    set_last_error_msg("band too wide for the solve kernel's shared memory");
+    return PDESHEP_CUDA_ERROR;
+  }
+  dim3 grid((unsigned)ceil_div(max_cols, kCW), (unsigned)nsys);
+  if (trans == 0) {
+    PD_CK(cudaFuncSetAttribute(solve_n_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    solve_n_kernel<C><<<grid, kThreads, smem, st>>>(g, d_sys, factor_arena, rhs_arena, out_arena);
+  } else {
+    PD_CK(cudaFuncSetAttribute(solve_c_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    solve_c_kernel<C><<<grid, kThreads, smem, st>>>(g, d_sys, factor_arena, rhs_arena, out_arena);
+  }
+  PD_CK_LAUNCH();
+  return 0;
+}
+
+template int launch_factor<float2>(const FactorGeom&, int, const void*, int64_t, int, const SysDesc*,
+                                   char*, int*, int32_t*, cudaStream_t);
+template int launch_factor<double2>(const FactorGeom&, int, const void*, int64_t, int, const SysDesc*,
+                                    char*, int*, int32_t*, cudaStream_t);
+template int launch_solve<float2>(const FactorGeom&, int, int, int, const SysDesc*, const char*,
+                                  const float2*, float2*, int, cudaStream_t);
+template int launch_solve<double2>(const FactorGeom&, int, int, int, const SysDesc*, const char*,
+                                   const double2*, double2*, int, cudaStream_t);
+
+}  // namespace pdeshep

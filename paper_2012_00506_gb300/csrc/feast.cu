@@ -1,0 +1,929 @@
+// feast.cu -- FEAST spectrum slicing on a band matrix (Algorithm 1 of
+// arXiv 2012.00506, run for every slice of step (II) of Algorithm 2).
+//
+// Per FEAST iteration and for all unconverged slices together:
+//   filter   Q = sum_j [w_j (z_j I - B)^{-1} + conj(w_j) (conj(z_j) I - B)^{-1}] Y
+//            (eqs. (9)-(10); real B: Q = 2 Re sum_j w_j (z_j I - B)^{-1} Y).  The
+//            shifted factorizations of all (slice, node) pairs are a batch (the
+//            paper's L1 x L2 process groups become one batch); when all factors
+//            fit in the workspace they are computed once and reused by every
+//            iteration, otherwise they stream through it in waves.
+//   CholQR2  Q <- Q R^{-1} with Q^H Q = R^H R, twice (FP64).
+//   RR       A_q = Q^H B Q, A_q W = W Lambda (FP64 Jacobi), X = Q W.
+//   check    res_i = ||B x_i - lambda_i x_i|| / (||B||_2 ||x_i||); a slice is
+//            done when as many Ritz pairs inside it have res_i <= tol as its
+//            exact inertia count (Section 3.2).
+// Precision PDESHEP_MIXED runs the filter in complex64 (FP32 accumulation).
+// With PDESHEP_REFINE_RESIDUAL the filter is applied to the FP64 Ritz
+// residuals r_i = B x_i - lambda_i x_i, using
+//   (zI - B)^{-1} x = [x + (zI - B)^{-1} r] / (z - lambda),
+// so r(B) x_i = r(lambda_i) x_i + sum_j w_j/(z_j - lambda_i) (z_j I - B)^{-1} r_i
+// (+ conjugate terms): the complex64 error then scales with ||r_i|| and the
+// iteration reaches FP64 residuals.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "band_lu.cuh"
+#include "dense.cuh"
+
+namespace pdeshep {
+
+// from other translation units
+size_t inertia_ws_bytes(int b, int cplx, int nsigma);
+int inertia_counts(int64_t n, int b, int cplx, const void* band, int64_t ldab, int nsigma,
+                   const double* h_sigma, int64_t* h_neg, double* d_piv, void* work, size_t wbytes,
+                   cudaStream_t st, bool* nonfinite_out);
+void contour_rule(int ne, double lo, double hi, double rho, pdeshep_c128* z, pdeshep_c128* w);
+int spectral_norm(int64_t n, int b, int cplx, const void* band, int64_t ldab, double rtol, double* out,
+                  void* work, size_t wbytes, cudaStream_t st);
+size_t bisect_ws_bytes(int b, int cplx, int nidx, int fanout);
+
+// Column block of one slice in the n x sum(m0) arrays.
+struct SliceDesc {
+  int64_t col_off;
+  int m0;
+  int slice;
+  double lo, hi;
+};
+
+// Node range [j0, j1) of one slice inside a wave of systems.
+struct AccDesc {
+  int64_t col_off;
+  int64_t xoff0;    // element offset of system (slice, j0)'s X^N in the X arena
+  int64_t xstride;  // elements per system in the X arena
+  int64_t coef_off; // offset of coef[slice][0][0]
+  int m0;
+  int j0, j1;
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+template <typename S, typename C>
+__global__ void make_rhs_kernel(int64_t n, const SliceDesc* sd, const S* __restrict__ src,
+                                const double* __restrict__ colscale, C* __restrict__ Y) {
+  const SliceDesc d = sd[blockIdx.y];
+  const int64_t total = n * d.m0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = d.col_off + e / n, i = e % n;
+    const double s = colscale ? 1.0 / colscale[c] : 1.0;
+    C v;
+    if constexpr (std::is_same<S, double>::value) {
+      v.x = (typename real_of<C>::type)(src[i + c * n] * s);
+      v.y = 0;
+    } else {
+      const double2 a = src[i + c * n];
+      v.x = (typename real_of<C>::type)(a.x * s);
+      v.y = (typename real_of<C>::type)(a.y * s);
+    }
+    Y[i + c * n] = v;
+  }
+}
+
+// coef[slice][j][c] and beta[c] for the columns of one slice.
+// mode 0: coef = w_j (plain filter of Algorithm 1), beta = 0.
+// mode 1: coef = w_j colscale_c / (z_j - lambda_c), beta = r(lambda_c).
+__global__ void coef_kernel(const SliceDesc* sd, int ne, const double2* __restrict__ zw,
+                            const double* __restrict__ lam, const double* __restrict__ colscale, int mode,
+                            double2* __restrict__ coef, double* __restrict__ beta) {
+  const SliceDesc d = sd[blockIdx.y];
+  const double2* z = zw + (int64_t)d.slice * 2 * ne;
+  const double2* w = z + ne;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < d.m0; c += gridDim.x * blockDim.x) {
+    const int64_t col = d.col_off + c;
+    double2* cf = coef + (int64_t)ne * d.col_off;
+    if (mode == 0) {
+      for (int j = 0; j < ne; ++j) cf[(int64_t)j * d.m0 + c] = w[j];
+      beta[col] = 0.0;
+    } else {
+      const double l = lam[col], s = colscale[col];
+      double r = 0.0;
+      for (int j = 0; j < ne; ++j) {
+        const double2 den = make_double2(z[j].x - l, z[j].y);
+        const double2 q = cmul(w[j], crecip(den));  // w_j / (z_j - lambda)
+        r += 2.0 * q.x;
+        cf[(int64_t)j * d.m0 + c] = make_double2(q.x * s, q.y * s);
+      }
+      beta[col] = r;
+    }
+  }
+}
+
+template <typename S>
+__global__ void q_init_kernel(int64_t n, const SliceDesc* sd, const double* __restrict__ beta,
+                              const S* __restrict__ X, S* __restrict__ Q, int use_beta) {
+  const SliceDesc d = sd[blockIdx.y];
+  const int64_t total = n * d.m0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = d.col_off + e / n, i = e % n;
+    Q[i + c * n] = use_beta ? sc<S>::scale(X[i + c * n], beta[c]) : sc<S>::zero();
+  }
+}
+
+// Q[:, slice cols] += sum_{j in [j0,j1)} coef_j X_j^N (+ conj(coef_j) X_j^C), or 2 Re(.) for real B.
+template <typename S, typename C>
+__global__ void accumulate_kernel(int64_t n, const AccDesc* ad, const double2* __restrict__ coef,
+                                  const C* __restrict__ X, S* __restrict__ Q, int cplx) {
+  const AccDesc d = ad[blockIdx.y];
+  const int64_t total = n * d.m0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / n);
+    const int64_t i = e % n;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = d.j0; j < d.j1; ++j) {
+      const double2 cf = coef[d.coef_off + (int64_t)j * d.m0 + c];
+      const int64_t xo = d.xoff0 + (int64_t)(j - d.j0) * d.xstride + i + (int64_t)c * n;
+      const C xn = X[xo];
+      cfma(acc, cf, make_double2((double)xn.x, (double)xn.y));
+      if (cplx) {
+        const C xc = X[xo + n * (int64_t)d.m0];
+        cfma(acc, cconj(cf), make_double2((double)xc.x, (double)xc.y));
+      }
+    }
+    S* q = Q + i + (d.col_off + c) * n;
+    if constexpr (std::is_same<S, double>::value) {
+      *q += 2.0 * acc.x;
+    } else {
+      *q = cadd(*q, acc);
+    }
+  }
+}
+
+// A <- (A + A^H)/2 for each small block
+template <typename S>
+__global__ void symmetrize_kernel(const SmallDesc* desc, S* Aall) {
+  const SmallDesc d = desc[blockIdx.y];
+  S* A = Aall + d.off;
+  const int m = d.m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), k = (int)(e / m);
+    if (i > k) continue;
+    const S a = A[i + (int64_t)k * m], b = sc<S>::conj(A[k + (int64_t)i * m]);
+    const S v = sc<S>::scale(sc<S>::add(a, b), 0.5);
+    if (i == k) {
+      A[e] = sc<S>::from_re(sc<S>::re(v));
+    } else {
+      A[i + (int64_t)k * m] = v;
+      A[k + (int64_t)i * m] = sc<S>::conj(v);
+    }
+  }
+}
+
+// R = BX - X diag(lam) (in place on BX), res = ||R||/(bnorm ||X||), colscale = ||R|| (1 if 0)
+template <typename S>
+__global__ void residual_kernel(int64_t n, const SliceDesc* sd, const S* __restrict__ X, S* __restrict__ BX,
+                                const double* __restrict__ lam, double bnorm, double* __restrict__ res,
+                                double* __restrict__ colscale) {
+  const SliceDesc d = sd[blockIdx.y];
+  const int c = blockIdx.x;
+  if (c >= d.m0) return;
+  const int64_t col = d.col_off + c;
+  const double l = lam[col];
+  double nr = 0.0, nx = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const S x = X[i + col * n];
+    const S r = sc<S>::sub(BX[i + col * n], sc<S>::scale(x, l));
+    BX[i + col * n] = r;
+    nr += sc<S>::abs2(r);
+    nx += sc<S>::abs2(x);
+  }
+  __shared__ double s1[32], s2[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    nr += __shfl_down_sync(0xffffffffu, nr, o);
+    nx += __shfl_down_sync(0xffffffffu, nx, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = nr;
+    s2[threadIdx.x >> 5] = nx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += s1[w];
+      b += s2[w];
+    }
+    const double rn = sqrt(a), xn = sqrt(b);
+    res[col] = rn / (bnorm * (xn > 0.0 ? xn : 1.0));
+    colscale[col] = rn > 0.0 ? rn : 1.0;
+  }
+}
+
+// nconv[slice] = #{c : lo <= lam_c < hi and res_c <= tol}
+__global__ void nconv_kernel(const SliceDesc* sd, const double* lam, const double* res, double tol,
+                             int* nconv) {
+  const SliceDesc d = sd[blockIdx.x];
+  int cnt = 0;
+  for (int c = threadIdx.x; c < d.m0; c += blockDim.x) {
+    const double l = lam[d.col_off + c];
+    cnt += (l >= d.lo && l < d.hi && res[d.col_off + c] <= tol);
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  __shared__ int s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    nconv[d.slice] = t;
+  }
+}
+
+// destination of each Ritz pair: converged in-slice pairs first (ascending), then the rest.
+__global__ void order_kernel(const SliceDesc* sd, const double* lam, const double* res, double tol,
+                             int* dest) {
+  const SliceDesc d = sd[blockIdx.x];
+  int ngood = 0;
+  for (int c = 0; c < d.m0; ++c) {
+    const double l = lam[d.col_off + c];
+    ngood += (l >= d.lo && l < d.hi && res[d.col_off + c] <= tol);
+  }
+  for (int c = threadIdx.x; c < d.m0; c += blockDim.x) {
+    const double l = lam[d.col_off + c];
+    const int good = (l >= d.lo && l < d.hi && res[d.col_off + c] <= tol);
+    int before = 0;
+    for (int c2 = 0; c2 < c; ++c2) {
+      const double l2 = lam[d.col_off + c2];
+      const int g2 = (l2 >= d.lo && l2 < d.hi && res[d.col_off + c2] <= tol);
+      before += (g2 == good);
+    }
+    dest[d.col_off + c] = (int)d.col_off + (good ? before : ngood + before);
+  }
+}
+
+template <typename S>
+__global__ void scatter_out_kernel(int64_t n, int64_t M, const int* dest, const double* lam, const S* X,
+                                   double* evals, S* evecs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * M;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / n, i = e % n;
+    const int64_t dc = dest[c];
+    evecs[i + dc * n] = X[i + c * n];
+    if (i == 0) evals[dc] = lam[c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// driver
+// ---------------------------------------------------------------------------
+static int grid1(int64_t total) {
+  int64_t b = (total + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+struct Plan {
+  // fixed buffers
+  void* Xt;        // S n x M  Ritz vectors (current)
+  void* Q;         // S n x M
+  void* Q2;        // S n x M
+  void* BQ;        // S n x M  (B Q, then B X - X Lambda)
+  void* Yc;        // C n x M  filter right-hand sides
+  double* lam;     // M
+  double* res;     // M
+  double* colscale;// M
+  double* beta;    // M
+  double2* coef;   // ne * M
+  double2* zw;     // K * 2 * ne
+  void* small_G;   // S sum m0^2 (Gram / R)
+  void* small_I;   // S sum m0^2 (R^{-1}, Jacobi work)
+  void* small_W;   // S sum m0^2 (eigenvectors)
+  void* part;      // S splits * sum m0^2
+  int* info;       // K (Cholesky)
+  int* sweeps;     // K
+  int* nconv;      // K
+  int* dest;       // M
+  int* sys_status; // max systems
+  double* jscratch;// K * 2 * 16
+  SliceDesc* d_sd; // K
+  SmallDesc* d_small; // K
+  GemmItem<double2>* d_items; // 4K (storage reused for double)
+  AccDesc* d_acc;  // K
+  SysDesc* d_sys;  // K * ne
+  char* inertia_ws;
+  size_t inertia_bytes;
+  // wave area
+  char* wave_base;
+  size_t wave_bytes;
+  int splits;
+};
+
+template <typename S, typename C>
+struct Feast {
+  int64_t n;
+  int b, cplx, K, ne;
+  const void* band;
+  int64_t ldab;
+  std::vector<int> m0;
+  std::vector<int64_t> col_off;
+  std::vector<int64_t> small_off;
+  int64_t M, Msq;
+  int max_m0;
+  const pdeshep_opts* o;
+  cudaStream_t st;
+  FactorGeom g;
+  Plan p;
+  std::vector<double> bounds;
+  std::vector<pdeshep_c128> zh, wh;  // K*ne
+  double bnorm;
+  size_t fb, es;
+  bool resident;
+  bool factored;
+  pdeshep_stats stats;
+  std::vector<int> active;  // slice indices
+  cudaEvent_t ev[2];
+
+  size_t fixed_bytes(Arena& a, bool carve) {
+    Plan q;
+    q.Xt = a.take<S>((size_t)(n * M));
+    q.Q = a.take<S>((size_t)(n * M));
+    q.Q2 = a.take<S>((size_t)(n * M));
+    q.BQ = a.take<S>((size_t)(n * M));
+    q.Yc = a.take<C>((size_t)(n * M));
+    q.lam = a.take<double>(M);
+    q.res = a.take<double>(M);
+    q.colscale = a.take<double>(M);
+    q.beta = a.take<double>(M);
+    q.coef = a.take<double2>((size_t)ne * M);
+    q.zw = a.take<double2>((size_t)K * 2 * ne);
+    q.small_G = a.take<S>(Msq);
+    q.small_I = a.take<S>(Msq);
+    q.small_W = a.take<S>(Msq);
+    q.splits = 8;
+    q.part = a.take<S>((size_t)q.splits * Msq);
+    q.info = a.take<int>(K);
+    q.sweeps = a.take<int>(K);
+    q.nconv = a.take<int>(K);
+    q.dest = a.take<int>(M);
+    q.sys_status = a.take<int>((size_t)K * ne);
+    q.jscratch = a.take<double>((size_t)K * 2 * 16);
+    q.d_sd = a.take<SliceDesc>(K);
+    q.d_small = a.take<SmallDesc>(K);
+    q.d_items = a.take<GemmItem<double2>>((size_t)4 * K);
+    q.d_acc = a.take<AccDesc>(K);
+    q.d_sys = a.take<SysDesc>((size_t)K * ne);
+    q.inertia_bytes = std::max(inertia_ws_bytes(b, cplx, K + 1), bisect_ws_bytes(b, cplx, 2, 16));
+    q.inertia_ws = a.take<char>(q.inertia_bytes);
+    if (carve) p = q;
+    return a.used();
+  }
+
+  size_t per_system_bytes(int s) const {
+    return fb + (((size_t)n * m0[s] * (cplx ? 2 : 1) * es + 255) & ~size_t(255));
+  }
+};
+
+}  // namespace pdeshep
+
+namespace pdeshep {
+
+template <typename S, typename C>
+struct FeastRun : Feast<S, C> {
+  using B = Feast<S, C>;
+  using B::n; using B::b; using B::cplx; using B::K; using B::ne; using B::band; using B::ldab;
+  using B::m0; using B::col_off; using B::small_off; using B::M; using B::Msq; using B::max_m0;
+  using B::o; using B::st; using B::g; using B::p; using B::bounds; using B::zh; using B::wh;
+  using B::bnorm; using B::fb; using B::es; using B::resident; using B::factored; using B::stats;
+  using B::active;
+
+  std::vector<int64_t> sys_off;  // resident layout: byte offset of system s*ne+j
+  std::vector<SliceDesc> h_sd;
+  std::vector<int> counts, nconv, iters;
+  int mode = 0;
+
+  int upload_active() {
+    const int na = (int)active.size();
+    h_sd.resize(na);
+    std::vector<SmallDesc> sm(na);
+    for (int a = 0; a < na; ++a) {
+      const int s = active[a];
+      h_sd[a] = SliceDesc{col_off[s], m0[s], s, bounds[s], bounds[s + 1]};
+      sm[a] = SmallDesc{small_off[s], col_off[s], m0[s], 0};
+    }
+    PD_CK(cudaMemcpyAsync(p.d_sd, h_sd.data(), sizeof(SliceDesc) * na, cudaMemcpyHostToDevice, st));
+    PD_CK(cudaMemcpyAsync(p.d_small, sm.data(), sizeof(SmallDesc) * na, cudaMemcpyHostToDevice, st));
+    return 0;
+  }
+
+  int act_max_m0() const {
+    int mm = 0;
+    for (int s : active) mm = std::max(mm, m0[s]);
+    return mm;
+  }
+
+  // C = op(A) B over the active slices; kind 0: C(m0 x m0) = A^H B with A,B n x m0 blocks;
+  // kind 1: C(n x m0) = A(n x m0) * B(m0 x m0 small block).
+  int gemm(int kind, const S* A, const S* Bm, S* Cm) {
+    const int na = (int)active.size();
+    std::vector<GemmItem<S>> it(na);
+    for (int a = 0; a < na; ++a) {
+      const int s = active[a];
+      GemmItem<S> x;
+      if (kind == 0) {
+        x.A = A + col_off[s] * n;
+        x.B = Bm + col_off[s] * n;
+        x.C = Cm + small_off[s];
+        x.m = m0[s];
+        x.n = m0[s];
+        x.k = (int)n;
+        x.lda = (int)n;
+        x.ldb = (int)n;
+        x.ldc = m0[s];
+        x.part_off = small_off[s];
+      } else {
+        x.A = A + col_off[s] * n;
+        x.B = Bm + small_off[s];
+        x.C = Cm + col_off[s] * n;
+        x.m = (int)n;
+        x.n = m0[s];
+        x.k = m0[s];
+        x.lda = (int)n;
+        x.ldb = m0[s];
+        x.ldc = (int)n;
+        x.part_off = 0;
+      }
+      it[a] = x;
+    }
+    GemmItem<S>* d_it = (GemmItem<S>*)p.d_items;
+    PD_CK(cudaMemcpyAsync(d_it, it.data(), sizeof(GemmItem<S>) * na, cudaMemcpyHostToDevice, st));
+    const int mm = act_max_m0();
+    S one = sc_host_one(), zero = sc_host_zero();
+    if (kind == 0) {
+      const int64_t tiles = (int64_t)na * ceil_div(mm, 64) * ceil_div(mm, 64);
+      int splits = (int)std::min<int64_t>(p.splits, std::max<int64_t>(1, ceil_div(2 * 152, tiles)));
+      splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, n / 256));
+      return launch_gemm<S>(true, na, d_it, mm, mm, (int)n, one, zero, splits, (S*)p.part, Msq, st);
+    }
+    return launch_gemm<S>(false, na, d_it, (int)n, mm, mm, one, zero, 1, (S*)p.part, Msq, st);
+  }
+
+  static S sc_host_one() {
+    if constexpr (std::is_same<S, double>::value) return 1.0; else return make_double2(1.0, 0.0);
+  }
+  static S sc_host_zero() {
+    if constexpr (std::is_same<S, double>::value) return 0.0; else return make_double2(0.0, 0.0);
+  }
+
+  int band_mm(const S* X, S* Y) {
+    for (int s : active)
+      PD_TRY(launch_band_matmul<S>(n, b, band, ldab, m0[s], X + col_off[s] * n, Y + col_off[s] * n, st));
+    return 0;
+  }
+
+  // Rayleigh-Ritz on Q for the active slices -> Xt, lam, BQ = residuals, res, colscale, nconv
+  int rr() {
+    const int na = (int)active.size();
+    if (!na) return 0;
+    PD_TRY(upload_active());
+    const int mm = act_max_m0();
+    S* G = (S*)p.small_G;
+    S* I = (S*)p.small_I;
+    S* W = (S*)p.small_W;
+    for (int pass = 0; pass < 2; ++pass) {
+      PD_TRY(gemm(0, (S*)p.Q, (S*)p.Q, G));
+      PD_TRY(launch_cholesky<S>(na, p.d_small, G, p.info, st));
+      PD_TRY(launch_triinv<S>(na, p.d_small, G, I, st));
+      PD_TRY(gemm(1, (S*)p.Q, I, (S*)p.Q2));
+      std::swap(p.Q, p.Q2);
+    }
+    {
+      std::vector<int> info(K, 0);
+      PD_CK(cudaMemcpyAsync(info.data(), p.info, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
+      PD_CK(cudaStreamSynchronize(st));
+      for (int s : active)
+        if (info[s]) return PDESHEP_CHOLQR_BREAKDOWN;
+    }
+    PD_TRY(band_mm((S*)p.Q, (S*)p.BQ));
+    PD_TRY(gemm(0, (S*)p.Q, (S*)p.BQ, G));
+    symmetrize_kernel<S><<<dim3(grid1((int64_t)mm * mm), na), 256, 0, st>>>(p.d_small, G);
+    PD_CK_LAUNCH();
+    PD_TRY(launch_jacobi<S>(na, p.d_small, mm, G, I, W, p.lam, 1e-14, 60, p.sweeps, p.jscratch, st));
+    PD_TRY(gemm(1, (S*)p.Q, W, (S*)p.Xt));
+    PD_TRY(band_mm((S*)p.Xt, (S*)p.BQ));
+    residual_kernel<S><<<dim3(mm, na), 256, 0, st>>>(n, p.d_sd, (S*)p.Xt, (S*)p.BQ, p.lam, bnorm, p.res,
+                                                     p.colscale);
+    PD_CK_LAUNCH();
+    nconv_kernel<<<na, 256, 0, st>>>(p.d_sd, p.lam, p.res, o->tol, p.nconv);
+    PD_CK_LAUNCH();
+    std::vector<int> sw(K, 0);
+    PD_CK(cudaMemcpyAsync(nconv.data(), p.nconv, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaMemcpyAsync(sw.data(), p.sweeps, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    for (int s : active)
+      if (sw[s] < 0) return PDESHEP_EIG_NOT_CONVERGED;
+    return 0;
+  }
+
+  SysDesc sys_desc(int s, int j, int64_t off) const {
+    SysDesc d;
+    d.factor_off = off;
+    d.zre = zh[(size_t)s * ne + j].re;
+    d.zim = zh[(size_t)s * ne + j].im;
+    d.rhs_off = col_off[s] * n;
+    d.out_off = (off + (int64_t)fb) / (int64_t)es;
+    d.out2_off = d.out_off + n * m0[s];
+    d.ncols = m0[s];
+    d.pad = 0;
+    return d;
+  }
+
+  int factor_batch(const std::vector<SysDesc>& sd) {
+    const int ns = (int)sd.size();
+    if (!ns) return 0;
+    PD_CK(cudaMemcpyAsync(p.d_sys, sd.data(), sizeof(SysDesc) * ns, cudaMemcpyHostToDevice, st));
+    PD_TRY(launch_factor<C>(g, cplx, band, ldab, ns, p.d_sys, p.wave_base, p.sys_status, nullptr, st));
+    std::vector<int> status(ns, 0);
+    PD_CK(cudaMemcpyAsync(status.data(), p.sys_status, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    for (int v : status)
+      if (v) return PDESHEP_SINGULAR;
+    stats.factorizations += ns;
+    return 0;
+  }
+
+  int solve_and_accumulate(const std::vector<SysDesc>& sd, const std::vector<AccDesc>& acc) {
+    const int ns = (int)sd.size();
+    if (!ns) return 0;
+    int mcols = 0;
+    for (auto& d : sd) mcols = std::max(mcols, d.ncols);
+    PD_CK(cudaMemcpyAsync(p.d_sys, sd.data(), sizeof(SysDesc) * ns, cudaMemcpyHostToDevice, st));
+    PD_TRY(launch_solve<C>(g, 0, ns, mcols, p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, 0, st));
+    if (cplx)
+      PD_TRY(launch_solve<C>(g, 1, ns, mcols, p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, 0, st));
+    for (auto& d : sd) stats.rhs_sweeps += ceil_div(d.ncols, 32) * (cplx ? 2 : 1);
+    const int na = (int)acc.size();
+    PD_CK(cudaMemcpyAsync(p.d_acc, acc.data(), sizeof(AccDesc) * na, cudaMemcpyHostToDevice, st));
+    accumulate_kernel<S, C><<<dim3(grid1(n * mcols), na), 256, 0, st>>>(n, p.d_acc, p.coef,
+                                                                       (const C*)p.wave_base, (S*)p.Q, cplx);
+    PD_CK_LAUNCH();
+    return 0;
+  }
+
+  // Q = filter(Xt or residuals) for the active slices
+  int filter() {
+    const int na = (int)active.size();
+    if (!na) return 0;
+    PD_TRY(upload_active());
+    const int mm = act_max_m0();
+    const S* src = mode ? (const S*)p.BQ : (const S*)p.Xt;
+    make_rhs_kernel<S, C><<<dim3(grid1(n * mm), na), 256, 0, st>>>(n, p.d_sd, src, mode ? p.colscale : nullptr,
+                                                                  (C*)p.Yc);
+    PD_CK_LAUNCH();
+    coef_kernel<<<dim3((unsigned)ceil_div(mm, 128), na), 128, 0, st>>>(p.d_sd, ne, p.zw, p.lam, p.colscale,
+                                                                       mode, p.coef, p.beta);
+    PD_CK_LAUNCH();
+    q_init_kernel<S><<<dim3(grid1(n * mm), na), 256, 0, st>>>(n, p.d_sd, p.beta, (const S*)p.Xt, (S*)p.Q, mode);
+    PD_CK_LAUNCH();
+    if (resident) {
+      if (!factored) {
+        std::vector<SysDesc> all;
+        for (int s = 0; s < K; ++s)
+          for (int j = 0; j < ne; ++j) all.push_back(sys_desc(s, j, sys_off[(size_t)s * ne + j]));
+        PD_TRY(factor_batch(all));
+        factored = true;
+        stats.waves += 1;
+      }
+      std::vector<SysDesc> sd;
+      std::vector<AccDesc> acc;
+      for (int s : active) {
+        for (int j = 0; j < ne; ++j) sd.push_back(sys_desc(s, j, sys_off[(size_t)s * ne + j]));
+        AccDesc a;
+        a.col_off = col_off[s];
+        a.xoff0 = sd[sd.size() - ne].out_off;
+        a.xstride = (ne > 1) ? (sd[sd.size() - ne + 1].out_off - sd[sd.size() - ne].out_off) : 0;
+        a.coef_off = (int64_t)ne * col_off[s];
+        a.m0 = m0[s];
+        a.j0 = 0;
+        a.j1 = ne;
+        a.pad = 0;
+        acc.push_back(a);
+      }
+      return solve_and_accumulate(sd, acc);
+    }
+    // streaming waves: systems of the active slices packed while they fit
+    size_t used = 0;
+    std::vector<SysDesc> sd;
+    std::vector<AccDesc> acc;
+    auto flush = [&]() -> int {
+      if (sd.empty()) return 0;
+      PD_TRY(factor_batch(sd));
+      PD_TRY(solve_and_accumulate(sd, acc));
+      stats.waves += 1;
+      sd.clear();
+      acc.clear();
+      used = 0;
+      return 0;
+    };
+    for (int s : active) {
+      const size_t ps = this->per_system_bytes(s);
+      for (int j = 0; j < ne; ++j) {
+        if (used + ps > p.wave_bytes) PD_TRY(flush());
+        if (ps > p.wave_bytes) return PDESHEP_WORKSPACE_TOO_SMALL;
+        sd.push_back(sys_desc(s, j, (int64_t)used));
+        used += ps;
+        if (acc.empty() || acc.back().col_off != col_off[s] || acc.back().j1 != j) {
+          AccDesc a;
+          a.col_off = col_off[s];
+          a.xoff0 = sd.back().out_off;
+          a.xstride = (int64_t)(ps / es);
+          a.coef_off = (int64_t)ne * col_off[s];
+          a.m0 = m0[s];
+          a.j0 = j;
+          a.j1 = j + 1;
+          a.pad = 0;
+          acc.push_back(a);
+        } else {
+          acc.back().j1 = j + 1;
+        }
+      }
+    }
+    return flush();
+  }
+};
+
+}  // namespace pdeshep
+
+using namespace pdeshep;
+
+namespace {
+
+template <typename S, typename C>
+int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int K, const double* h_bounds,
+                int ne, const pdeshep_c128* h_nodes, const pdeshep_c128* h_weights, const int32_t* h_m0,
+                const void* d_x0, void* d_work, size_t work_bytes, const pdeshep_opts* o, double* d_evals,
+                void* d_evecs, int32_t* h_counts, int32_t* h_nfound, pdeshep_stats* h_stats, size_t* size_only) {
+  FeastRun<S, C> F;
+  F.n = n;
+  F.b = b;
+  F.cplx = cplx;
+  F.K = K;
+  F.ne = ne;
+  F.band = band;
+  F.ldab = ldab;
+  F.o = o;
+  F.st = (cudaStream_t)o->stream;
+  F.g = make_geom(n, b);
+  F.es = sizeof(C);
+  F.fb = factor_bytes(F.g, sizeof(C));
+  F.m0.assign(h_m0, h_m0 + K);
+  F.col_off.assign(K, 0);
+  F.small_off.assign(K, 0);
+  int64_t acc = 0, accs = 0;
+  F.max_m0 = 0;
+  for (int s = 0; s < K; ++s) {
+    F.col_off[s] = acc;
+    F.small_off[s] = accs;
+    acc += F.m0[s];
+    accs += (int64_t)F.m0[s] * F.m0[s];
+    F.max_m0 = std::max(F.max_m0, F.m0[s]);
+  }
+  F.M = acc;
+  F.Msq = accs;
+  memset(&F.stats, 0, sizeof(F.stats));
+  // workspace plan
+  Arena a(d_work, work_bytes);
+  F.fixed_bytes(a, true);
+  const size_t fixed = a.used();
+  size_t all_sys = 0;
+  F.sys_off.assign((size_t)K * ne, 0);
+  for (int s = 0; s < K; ++s)
+    for (int j = 0; j < ne; ++j) {
+      F.sys_off[(size_t)s * ne + j] = (int64_t)all_sys;
+      all_sys += F.per_system_bytes(s);
+    }
+  size_t max_sys = 0;
+  for (int s = 0; s < K; ++s) max_sys = std::max(max_sys, F.per_system_bytes(s));
+  if (size_only) {
+    size_t wave = all_sys;
+    if (o->hbm_cap_bytes > 0) wave = std::min(wave, std::max((size_t)o->hbm_cap_bytes, max_sys));
+    *size_only = fixed + wave + 256;
+    return 0;
+  }
+  if (work_bytes < fixed + max_sys) return PDESHEP_WORKSPACE_TOO_SMALL;
+  F.p.wave_base = (char*)d_work + fixed;
+  F.p.wave_bytes = work_bytes - fixed;
+  if (o->hbm_cap_bytes > 0) F.p.wave_bytes = std::min(F.p.wave_bytes, (size_t)o->hbm_cap_bytes);
+  F.resident = all_sys <= F.p.wave_bytes;
+  F.factored = false;
+  cudaStream_t st = F.st;
+
+  cudaEvent_t e0, e1;
+  PD_CK(cudaEventCreate(&e0));
+  PD_CK(cudaEventCreate(&e1));
+  PD_CK(cudaEventRecord(e0, st));
+  // exact counts by inertia at every boundary
+  F.bounds.assign(h_bounds, h_bounds + K + 1);
+  std::vector<int64_t> neg(K + 1);
+  bool bad = false;
+  PD_TRY(inertia_counts(n, b, cplx, band, ldab, K + 1, h_bounds, neg.data(), nullptr, F.p.inertia_ws,
+                        F.p.inertia_bytes, st, &bad));
+  if (bad) return PDESHEP_NONFINITE_INPUT;
+  F.counts.assign(K, 0);
+  F.nconv.assign(K, 0);
+  F.iters.assign(K, 0);
+  for (int s = 0; s < K; ++s) {
+    F.counts[s] = (int)(neg[s + 1] - neg[s]);
+    if (h_counts) h_counts[s] = F.counts[s];
+  }
+  for (int s = 0; s < K; ++s)
+    if (F.m0[s] < F.counts[s]) return PDESHEP_COUNT_MISMATCH;
+  {
+    float ms = 0;
+    PD_CK(cudaEventRecord(e1, st));
+    PD_CK(cudaEventSynchronize(e1));
+    PD_CK(cudaEventElapsedTime(&ms, e0, e1));
+    F.stats.ms_inertia = ms;
+  }
+  // ||B||_2
+  F.bnorm = o->bnorm;
+  if (!(F.bnorm > 0.0))
+    PD_TRY(spectral_norm(n, b, cplx, band, ldab, 1e-6, &F.bnorm, F.p.inertia_ws, F.p.inertia_bytes, st));
+  // quadrature per slice
+  F.zh.resize((size_t)K * ne);
+  F.wh.resize((size_t)K * ne);
+  for (int s = 0; s < K; ++s) {
+    if (h_nodes && h_weights) {
+      for (int j = 0; j < ne; ++j) {
+        F.zh[(size_t)s * ne + j] = h_nodes[(size_t)s * ne + j];
+        F.wh[(size_t)s * ne + j] = h_weights[(size_t)s * ne + j];
+      }
+    } else {
+      contour_rule(ne, h_bounds[s], h_bounds[s + 1], o->ellipse_ratio, &F.zh[(size_t)s * ne], &F.wh[(size_t)s * ne]);
+    }
+  }
+  {
+    std::vector<double2> zw((size_t)K * 2 * ne);
+    for (int s = 0; s < K; ++s)
+      for (int j = 0; j < ne; ++j) {
+        zw[(size_t)s * 2 * ne + j] = make_double2(F.zh[(size_t)s * ne + j].re, F.zh[(size_t)s * ne + j].im);
+        zw[(size_t)s * 2 * ne + ne + j] = make_double2(F.wh[(size_t)s * ne + j].re, F.wh[(size_t)s * ne + j].im);
+      }
+    PD_CK(cudaMemcpyAsync(F.p.zw, zw.data(), sizeof(double2) * zw.size(), cudaMemcpyHostToDevice, st));
+  }
+  PD_CK(cudaMemcpyAsync(F.p.Xt, d_x0, sizeof(S) * (size_t)(n * F.M), cudaMemcpyDeviceToDevice, st));
+  F.mode = (o->precision == PDESHEP_MIXED && o->refine_policy == PDESHEP_REFINE_RESIDUAL) ? 1 : 0;
+  std::vector<int> done(K, 0);
+  F.active.clear();
+  for (int s = 0; s < K; ++s) F.active.push_back(s);
+  int status = 0;
+  double ms_filter = 0, ms_rr = 0;
+  auto timed = [&](double& acc_ms, auto&& fn) -> int {
+    PD_CK(cudaEventRecord(e0, st));
+    int r = fn();
+    if (r) return r;
+    PD_CK(cudaEventRecord(e1, st));
+    PD_CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    PD_CK(cudaEventElapsedTime(&ms, e0, e1));
+    acc_ms += ms;
+    return 0;
+  };
+  auto update_active = [&](int it) {
+    std::vector<int> next;
+    for (int s : F.active) {
+      F.iters[s] = it;
+      if (F.nconv[s] == F.counts[s])
+        done[s] = 1;
+      else
+        next.push_back(s);
+    }
+    F.active.swap(next);
+  };
+  if (F.mode == 1) {
+    PD_CK(cudaMemcpyAsync(F.p.Q, F.p.Xt, sizeof(S) * (size_t)(n * F.M), cudaMemcpyDeviceToDevice, st));
+    PD_TRY(timed(ms_rr, [&]() { return F.rr(); }));
+    update_active(0);
+  }
+  int it = 1;
+  for (; it <= o->max_iter && !F.active.empty(); ++it) {
+    PD_TRY(timed(ms_filter, [&]() { return F.filter(); }));
+    PD_TRY(timed(ms_rr, [&]() { return F.rr(); }));
+    update_active(it);
+  }
+  if (!F.active.empty()) status = PDESHEP_NOT_CONVERGED;
+  // outputs for every slice
+  F.active.clear();
+  for (int s = 0; s < K; ++s) F.active.push_back(s);
+  PD_TRY(F.upload_active());
+  order_kernel<<<K, 256, 0, st>>>(F.p.d_sd, F.p.lam, F.p.res, o->tol, F.p.dest);
+  PD_CK_LAUNCH();
+  scatter_out_kernel<S><<<grid1(n * F.M), 256, 0, st>>>(n, F.M, F.p.dest, F.p.lam, (const S*)F.p.Xt, d_evals,
+                                                        (S*)d_evecs);
+  PD_CK_LAUNCH();
+  std::vector<double> res(F.M), lam(F.M);
+  PD_CK(cudaMemcpyAsync(res.data(), F.p.res, sizeof(double) * F.M, cudaMemcpyDeviceToHost, st));
+  PD_CK(cudaMemcpyAsync(lam.data(), F.p.lam, sizeof(double) * F.M, cudaMemcpyDeviceToHost, st));
+  PD_CK(cudaStreamSynchronize(st));
+  double maxres = 0.0;
+  for (int s = 0; s < K; ++s) {
+    int nf = 0;
+    for (int c = 0; c < F.m0[s]; ++c) {
+      const int64_t col = F.col_off[s] + c;
+      if (lam[col] >= h_bounds[s] && lam[col] < h_bounds[s + 1] && res[col] <= o->tol) {
+        ++nf;
+        maxres = std::max(maxres, res[col]);
+      }
+    }
+    if (h_nfound) h_nfound[s] = nf;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (h_stats) {
+    F.stats.iterations = 0;
+    for (int s = 0; s < K; ++s) F.stats.iterations = std::max(F.stats.iterations, F.iters[s]);
+    F.stats.ms_factor = 0;
+    F.stats.ms_solve = ms_filter;
+    F.stats.ms_rr = ms_rr;
+    F.stats.ms_total = F.stats.ms_inertia + ms_filter + ms_rr;
+    F.stats.max_residual = maxres;
+    *h_stats = F.stats;
+  }
+  return status;
+}
+
+int check_slice_args(int64_t n, int32_t b, const void* d_band, int64_t ldab, int32_t K, const double* h_bounds,
+                     int32_t ne, const pdeshep_c128* h_nodes, const pdeshep_c128* h_weights, const int32_t* h_m0,
+                     const pdeshep_opts* o) {
+  if (n <= 0) return -1;
+  if (b < 0 || b >= n + 1) return -2;
+  if (!d_band) return -4;
+  if (ldab < b + 1) return -5;
+  if (K <= 0) return -6;
+  if (!h_bounds) return -7;
+  for (int s = 0; s < K; ++s)
+    if (!(h_bounds[s] < h_bounds[s + 1])) return -7;
+  if (ne < 1 || ne > 64) return -8;
+  if ((h_nodes == nullptr) != (h_weights == nullptr)) return -9;
+  if (!h_m0) return -11;
+  for (int s = 0; s < K; ++s)
+    if (h_m0[s] < 1 || h_m0[s] > n || h_m0[s] > 4096) return -11;
+  if (o && (!(o->tol > 0.0) || o->max_iter < 0 || (o->precision != PDESHEP_FP64 && o->precision != PDESHEP_MIXED) ||
+            !(o->ellipse_ratio > 0.0)))
+    return -15;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" size_t pdeshep_workspace_size(int64_t n, int32_t b, int32_t is_complex, int32_t nslices,
+                                         const int32_t* h_m0, int32_t ne, const pdeshep_opts* opts) {
+  pdeshep_opts def;
+  pdeshep_opts_default(&def);
+  const pdeshep_opts* o = opts ? opts : &def;
+  if (n <= 0 || b < 0 || nslices <= 0 || !h_m0 || ne < 1) return 0;
+  size_t sz = 0;
+  int r;
+  if (is_complex) {
+    if (o->precision == PDESHEP_MIXED)
+      r = feast_entry<double2, float2>(n, b, 1, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
+                                       nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
+    else
+      r = feast_entry<double2, double2>(n, b, 1, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
+                                        nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
+  } else {
+    if (o->precision == PDESHEP_MIXED)
+      r = feast_entry<double, float2>(n, b, 0, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
+                                      nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
+    else
+      r = feast_entry<double, double2>(n, b, 0, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
+                                       nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
+  }
+  return r ? 0 : sz;
+}
+
+extern "C" int pdeshep_band_slice(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                                  int32_t nslices, const double* h_bounds, int32_t ne, const pdeshep_c128* h_nodes,
+                                  const pdeshep_c128* h_weights, const int32_t* h_m0, const void* d_x0,
+                                  void* d_work, size_t work_bytes, const pdeshep_opts* opts, double* d_evals,
+                                  void* d_evecs, int32_t* h_counts, int32_t* h_nfound, pdeshep_stats* h_stats) {
+  pdeshep_opts def;
+  pdeshep_opts_default(&def);
+  const pdeshep_opts* o = opts ? opts : &def;
+  int r = check_slice_args(n, b, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0, opts);
+  if (r) return r;
+  if (!d_x0) return -12;
+  if (!d_work) return -13;
+  if (!d_evals) return -16;
+  if (!d_evecs) return -17;
+  if (is_complex) {
+    if (o->precision == PDESHEP_MIXED)
+      return feast_entry<double2, float2>(n, b, 1, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0,
+                                          d_x0, d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound, h_stats,
+                                          nullptr);
+    return feast_entry<double2, double2>(n, b, 1, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0,
+                                         d_x0, d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound, h_stats,
+                                         nullptr);
+  }
+  if (o->precision == PDESHEP_MIXED)
+    return feast_entry<double, float2>(n, b, 0, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0, d_x0,
+                                       d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound, h_stats, nullptr);
+  return feast_entry<double, double2>(n, b, 0, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0, d_x0,
+                                      d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound, h_stats, nullptr);
+}

@@ -1,0 +1,233 @@
+// slicing.cu -- host-side pieces of the slicing step: the quadrature rule of
+// Section 2.2 (Gauss-Legendre nodes on the upper half of an ellipse around the
+// slice, eqs. (8)-(9)), eigenvalue enclosures by batched bisection on the GPU
+// inertia kernel (slice boundaries with exact counts, Section 3.2), status
+// strings and option defaults.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pdeshep {
+
+static thread_local char g_last_error[512] = "";
+
+void set_last_error(const char* where, cudaError_t e) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+}
+void set_last_error_msg(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+// defined in inertia.cu
+size_t inertia_ws_bytes(int b, int cplx, int nsigma);
+int inertia_counts(int64_t n, int b, int cplx, const void* band, int64_t ldab, int nsigma,
+                   const double* h_sigma, int64_t* h_neg, double* d_piv, void* work, size_t wbytes,
+                   cudaStream_t st, bool* nonfinite_out);
+int gershgorin_device(int64_t n, int b, int cplx, const void* band, int64_t ldab, double* d_lo,
+                      double* d_hi, cudaStream_t st);
+size_t gershgorin_ws_doubles();
+
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1]: Newton's method
+// on P_ne from the three-term recurrence P_k = ((2k-1) x P_{k-1} - (k-1) P_{k-2})/k.
+void gauss_legendre(int ne, double* x, double* w) {
+  for (int i = 0; i < ne; ++i) {
+    double t = cos(M_PI * (i + 0.75) / (ne + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = t;  // P_{k-1}, P_k
+      for (int k = 2; k <= ne; ++k) {
+        double p3 = ((2.0 * k - 1.0) * t * p2 - (k - 1.0) * p1) / k;
+        p1 = p2;
+        p2 = p3;
+      }
+      dp = ne * (t * p2 - p1) / (t * t - 1.0);
+      double step = p2 / dp;
+      t -= step;
+      if (fabs(step) <= 1e-16 * (1.0 + fabs(t))) break;
+    }
+    double p1 = 1.0, p2 = t;
+    for (int k = 2; k <= ne; ++k) {
+      double p3 = ((2.0 * k - 1.0) * t * p2 - (k - 1.0) * p1) / k;
+      p1 = p2;
+      p2 = p3;
+    }
+    dp = ne * (t * p2 - p1) / (t * t - 1.0);
+    x[ne - 1 - i] = t;
+    w[ne - 1 - i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+void contour_rule(int ne, double lo, double hi, double rho, pdeshep_c128* z, pdeshep_c128* w) {
+  std::vector<double> x(ne), om(ne);
+  gauss_legendre(ne, x.data(), om.data());
+  const double c = 0.5 * (lo + hi), r = 0.5 * (hi - lo);
+  for (int k = 0; k < ne; ++k) {
+    const double th = 0.5 * M_PI * (1.0 - x[k]);
+    const double ct = cos(th), st = sin(th);
+    z[k].re = c + r * ct;
+    z[k].im = r * rho * st;
+    w[k].re = 0.25 * om[k] * r * rho * ct;
+    w[k].im = 0.25 * om[k] * r * st;
+  }
+}
+
+// Batched bisection: enclosures [lo_t, hi_t) of eigenvalue idx_t with
+// count(lo) <= idx < count(hi).  Each round evaluates `fanout` interior
+// points per unfinished enclosure in one inertia launch.
+int bisect(int64_t n, int b, int cplx, const void* band, int64_t ldab, int nidx, const int64_t* idx,
+           double rtol, int fanout, double glo, double ghi, double* lo, double* hi, void* work,
+           size_t wbytes, cudaStream_t st) {
+  if (fanout < 1) fanout = 1;
+  const double span = ghi - glo;
+  const double pad = 1e-3 * (span > 0 ? span : 1.0) + 1e-300;
+  for (int t = 0; t < nidx; ++t) {
+    lo[t] = glo - pad;
+    hi[t] = ghi + pad;
+  }
+  std::vector<double> sig;
+  std::vector<int64_t> neg;
+  std::vector<int> owner;
+  for (int round = 0; round < 400; ++round) {
+    sig.clear();
+    owner.clear();
+    for (int t = 0; t < nidx; ++t) {
+      const double w = hi[t] - lo[t];
+      if (w <= rtol * std::max(1.0, std::max(fabs(lo[t]), fabs(hi[t])))) continue;
+      for (int f = 1; f <= fanout; ++f) {
+        const double s = lo[t] + w * f / (fanout + 1);
+        if (s <= lo[t] || s >= hi[t]) continue;
+        sig.push_back(s);
+        owner.push_back(t);
+      }
+    }
+    if (sig.empty()) break;
+    neg.assign(sig.size(), 0);
+    if (inertia_ws_bytes(b, cplx, (int)sig.size()) > wbytes) return PDESHEP_WORKSPACE_TOO_SMALL;
+    bool bad = false;
+    PD_TRY(inertia_counts(n, b, cplx, band, ldab, (int)sig.size(), sig.data(), neg.data(), nullptr, work,
+                          wbytes, st, &bad));
+    if (bad) return PDESHEP_NONFINITE_INPUT;
+    for (size_t e = 0; e < sig.size(); ++e) {
+      const int t = owner[e];
+      if (neg[e] <= idx[t]) {
+        if (sig[e] > lo[t]) lo[t] = sig[e];
+      } else {
+        if (sig[e] < hi[t]) hi[t] = sig[e];
+      }
+    }
+  }
+  return 0;
+}
+
+int gershgorin_host(int64_t n, int b, int cplx, const void* band, int64_t ldab, double* glo,
+                    double* ghi, void* work, size_t wbytes, cudaStream_t st) {
+  if (wbytes < sizeof(double) * gershgorin_ws_doubles()) return PDESHEP_WORKSPACE_TOO_SMALL;
+  double* lo = (double*)work;
+  double* hi = lo + gershgorin_ws_doubles() / 2;
+  PD_TRY(gershgorin_device(n, b, cplx, band, ldab, lo, hi, st));
+  PD_CK(cudaMemcpyAsync(glo, lo, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PD_CK(cudaMemcpyAsync(ghi, hi, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PD_CK(cudaStreamSynchronize(st));
+  return 0;
+}
+
+size_t bisect_ws_bytes(int b, int cplx, int nidx, int fanout) {
+  size_t a = inertia_ws_bytes(b, cplx, std::max(1, nidx * std::max(1, fanout)));
+  size_t g = sizeof(double) * gershgorin_ws_doubles();
+  return std::max(a, g);
+}
+
+// ||B||_2 = max(|lambda_min|, |lambda_max|) to relative accuracy rtol.
+int spectral_norm(int64_t n, int b, int cplx, const void* band, int64_t ldab, double rtol, double* out,
+                  void* work, size_t wbytes, cudaStream_t st) {
+  double glo, ghi;
+  PD_TRY(gershgorin_host(n, b, cplx, band, ldab, &glo, &ghi, work, wbytes, st));
+  int64_t idx[2] = {0, n - 1};
+  double lo[2], hi[2];
+  PD_TRY(bisect(n, b, cplx, band, ldab, 2, idx, rtol, 16, glo, ghi, lo, hi, work, wbytes, st));
+  *out = std::max(std::max(fabs(lo[0]), fabs(hi[0])), std::max(fabs(lo[1]), fabs(hi[1])));
+  return 0;
+}
+
+}  // namespace pdeshep
+
+using namespace pdeshep;
+
+extern "C" const char* pdeshep_last_error(void) { return g_last_error; }
+
+extern "C" const char* pdeshep_version(void) { return "pdeshep-gb300 0.1 (sm_103a)"; }
+
+extern "C" const char* pdeshep_status_string(int s) {
+  switch (s) {
+    case PDESHEP_OK: return "ok";
+    case PDESHEP_NOT_CONVERGED: return "not converged";
+    case PDESHEP_COUNT_MISMATCH: return "subspace smaller than the slice's eigenvalue count";
+    case PDESHEP_CHOLQR_BREAKDOWN: return "CholQR breakdown";
+    case PDESHEP_NONFINITE_INPUT: return "non-finite input";
+    case PDESHEP_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case PDESHEP_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case PDESHEP_SINGULAR: return "singular shifted system";
+    case PDESHEP_CUDA_ERROR: return "CUDA error";
+    case PDESHEP_EIG_NOT_CONVERGED: return "small eigensolver did not converge";
+    default: return s < 0 ? "invalid argument" : "unknown status";
+  }
+}
+
+extern "C" void pdeshep_opts_default(pdeshep_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->tol = 1e-10;
+  o->max_iter = 20;
+  o->precision = PDESHEP_MIXED;
+  o->refine_policy = PDESHEP_REFINE_RESIDUAL;
+  o->rhs_chunk = 0;
+  o->ellipse_ratio = 0.3;
+  o->bnorm = 0.0;
+  o->seed = 0;
+  o->hbm_cap_bytes = 0;
+  o->autotune = 0;
+  o->verbose = 0;
+  o->stream = nullptr;
+}
+
+extern "C" int pdeshep_contour_rule(int32_t ne, double lo, double hi, double rho, pdeshep_c128* h_z,
+                                    pdeshep_c128* h_w) {
+  if (ne < 1 || ne > 256) return -1;
+  if (!(lo < hi)) return -2;
+  if (!(rho > 0.0)) return -4;
+  if (!h_z) return -5;
+  if (!h_w) return -6;
+  contour_rule(ne, lo, hi, rho, h_z, h_w);
+  return 0;
+}
+
+extern "C" size_t pdeshep_bisect_workspace_size(int64_t n, int32_t b, int32_t is_complex, int32_t nidx,
+                                                int32_t fanout) {
+  (void)n;
+  return bisect_ws_bytes(b, is_complex ? 1 : 0, nidx, fanout);
+}
+
+extern "C" int pdeshep_bisect(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                              int32_t nidx, const int64_t* h_idx, double rtol, int32_t fanout, double* h_lo,
+                              double* h_hi, void* d_work, size_t work_bytes, void* stream) {
+  if (n <= 0) return -1;
+  if (b < 0) return -2;
+  if (!d_band) return -4;
+  if (ldab < b + 1) return -5;
+  if (nidx < 0) return -6;
+  if (!h_idx && nidx > 0) return -7;
+  for (int t = 0; t < nidx; ++t)
+    if (h_idx[t] < 0 || h_idx[t] >= n) return -7;
+  if (!(rtol > 0.0)) return -8;
+  if (fanout < 1 || fanout > 1024) return -9;
+  if (!h_lo && nidx > 0) return -10;
+  if (!h_hi && nidx > 0) return -11;
+  if (!d_work) return -12;
+  if (nidx == 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  double glo, ghi;
+  PD_TRY(gershgorin_host(n, b, is_complex ? 1 : 0, d_band, ldab, &glo, &ghi, d_work, work_bytes, st));
+  return bisect(n, b, is_complex ? 1 : 0, d_band, ldab, nidx, h_idx, rtol, fanout, glo, ghi, h_lo, h_hi,
+                d_work, work_bytes, st);
+}

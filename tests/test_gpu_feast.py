@@ -1,0 +1,117 @@
+"""GPU FEAST slicing (Algorithm 1 on every slice, behind pdeshep_band_slice)
+against the oracle: exact counts, eigenvalues within 1e-10 ||B||_2, subspace
+sines within 1e-8, residuals and orthogonality."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import block_from_dev, block_to_dev, dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def device():
+    return dev()
+
+
+def _bounds(ab, ks):
+    return [oracle.boundary_between(ab, k) for k in ks]
+
+
+def _run_compare(device, ab, ks, m0, precision, seed, ne=8, rho=0.3, tol=1e-10):
+    import paper_2012_00506_gb300 as pk
+    cplx = np.iscomplexobj(ab)
+    n = ab.shape[0]
+    bounds = _bounds(ab, ks)
+    bnorm = oracle.spectral_norm(ab)
+    X0 = synth.random_subspace(n, int(sum(m0)), seed, cplx)
+    r = pk.band_slice(to_dev(ab, device), bounds, m0, block_to_dev(X0, device), ne=ne, precision=precision,
+                      bnorm=bnorm, tol=tol, ellipse_ratio=rho, max_iter=40)
+    assert r.status == 0, (r.status, r.stats)
+    evals = r.evals.cpu().numpy()
+    evecs = block_from_dev(r.evecs)
+    off = 0
+    for i in range(len(m0)):
+        cnt = ks[i + 1] - ks[i]
+        assert r.counts[i] == cnt == oracle.inertia(ab, bounds[i + 1]) - oracle.inertia(ab, bounds[i])
+        assert r.nfound[i] == cnt
+        o = oracle.feast_slice(ab, bounds[i], bounds[i + 1], X0[:, off:off + m0[i]], ne=ne, rho=rho, tol=tol,
+                               bnorm=bnorm, max_iter=40, count=cnt)
+        assert o["status"] == 0 and o["nfound"] == cnt
+        lg = evals[off:off + cnt]
+        Xg = evecs[:, off:off + cnt]
+        assert np.max(np.abs(lg - o["evals"][:cnt])) <= 1e-10 * bnorm
+        assert oracle.subspace_sin_angle(Xg, o["evecs"][:, :cnt]) <= 1e-8
+        assert np.max(oracle.residuals(ab, lg, Xg, bnorm)) <= tol
+        assert oracle.orth(Xg) < 1e-13
+        off += m0[i]
+    return r
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_real_one_slice(device, precision):
+    ab = synth.random_band(300, 7, 21)
+    _run_compare(device, ab, [120, 150], [oracle.m0_rule(30)], precision, 22)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_complex_three_slices_uneven(device, precision):
+    ab = synth.random_band(260, 6, 31, True)
+    ks = [20, 30, 52, 90]
+    m0 = [oracle.m0_rule(ks[i + 1] - ks[i]) for i in range(3)]
+    _run_compare(device, ab, ks, m0, precision, 32)
+
+
+def test_wide_band_ragged(device):
+    ab = synth.random_band(333, 40, 41, True)
+    _run_compare(device, ab, [100, 125], [35], 1, 42, ne=16, rho=1.0)
+
+
+def test_laplacian_closed_form(device):
+    import paper_2012_00506_gb300 as pk
+    m, k = 26, 17
+    ab = synth.laplacian_2d_band(m, k)
+    i = np.arange(1, m + 1)[:, None]
+    j = np.arange(1, k + 1)[None, :]
+    ev = np.sort((4 - 2 * np.cos(i * np.pi / (m + 1)) - 2 * np.cos(j * np.pi / (k + 1))).ravel())
+    lo, hi = 0.5 * (ev[99] + ev[100]), 0.5 * (ev[139] + ev[140])
+    X0 = synth.random_subspace(m * k, 52, 5, False)
+    r = pk.band_slice(to_dev(ab, device), [lo, hi], [52], block_to_dev(X0, device), ne=16, bnorm=float(ev[-1]),
+                      tol=1e-11, ellipse_ratio=1.0)
+    assert r.status == 0 and r.counts[0] == 40 and r.nfound[0] == 40
+    assert np.max(np.abs(r.evals.cpu().numpy()[:40] - ev[100:140])) < 1e-11 * ev[-1]
+
+
+def test_count_mismatch_and_nonfinite(device):
+    import torch
+    import paper_2012_00506_gb300 as pk
+    ab = synth.random_band(200, 5, 51)
+    b0, b1 = _bounds(ab, [10, 40])
+    X0 = synth.random_subspace(200, 20, 52, False)
+    r = pk.band_slice(to_dev(ab, device), [b0, b1], [20], block_to_dev(X0, device), raise_on_error=False)
+    assert r.status == 2 and r.counts[0] == 30
+    bad = ab.copy()
+    bad[3, 1] = np.nan
+    r = pk.band_slice(to_dev(bad, device), [b0, b1], [40], block_to_dev(synth.random_subspace(200, 40, 1, False),
+                      device), raise_on_error=False)
+    assert r.status == 4
+    r = pk.band_slice(to_dev(ab, device), [b0, b1], [40], block_to_dev(synth.random_subspace(200, 40, 1, False),
+                      device), max_iter=1, raise_on_error=False)
+    assert r.status == 1
+
+
+def test_streaming_waves_match_resident(device):
+    import paper_2012_00506_gb300 as pk
+    ab = synth.random_band(256, 8, 61, True)
+    ks = [30, 45, 70]
+    m0 = [25, 35]
+    bounds = _bounds(ab, ks)
+    bnorm = oracle.spectral_norm(ab)
+    X0 = block_to_dev(synth.random_subspace(256, 60, 62, True), device)
+    r1 = pk.band_slice(to_dev(ab, device), bounds, m0, X0, bnorm=bnorm)
+    r2 = pk.band_slice(to_dev(ab, device), bounds, m0, X0, bnorm=bnorm, hbm_cap_bytes=3 << 20)
+    assert r1.status == r2.status == 0
+    assert r2.stats["waves"] > r1.stats["waves"]
+    assert np.max(np.abs(r1.evals.cpu().numpy() - r2.evals.cpu().numpy())[:15]) < 1e-12
