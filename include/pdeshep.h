@@ -77,6 +77,16 @@ typedef struct {
   void* stream;            /* cudaStream_t */
 } pdeshep_opts;
 
+/* Kernel groups timed separately (CUDA events around each launch). */
+#define PDESHEP_KG_INERTIA 0     /* LDL^T inertia (and the band amax reduction) */
+#define PDESHEP_KG_FACTOR 1      /* shifted band LU (tile init + factorization) */
+#define PDESHEP_KG_SOLVE 2       /* multi-RHS band solves (forward + backward sweeps) */
+#define PDESHEP_KG_ACCUM 3       /* right-hand-side preparation and weighted accumulation of Q */
+#define PDESHEP_KG_GEMM 4        /* FP64 tall products (Gram, projection, basis updates) */
+#define PDESHEP_KG_SMALL 5       /* FP64 Cholesky, triangular inverse, Jacobi */
+#define PDESHEP_KG_BANDMM 6      /* FP64 band times block (B Q, B X) and residual norms */
+#define PDESHEP_KG_COUNT 7
+
 typedef struct {
   int32_t iterations;      /* FEAST iterations of the slowest slice */
   int32_t waves;           /* factorization waves issued */
@@ -89,6 +99,12 @@ typedef struct {
   double ms_total;
   double max_residual;     /* over the converged in-slice pairs */
   double min_rel_error_est;/* reserved */
+  /* per kernel group (PDESHEP_KG_*): summed device time of its launches, launch
+     count, and algorithmic work (real flops, complex multiply-add = 8) */
+  double kg_ms[PDESHEP_KG_COUNT];
+  int64_t kg_launches[PDESHEP_KG_COUNT];
+  double kg_flops[PDESHEP_KG_COUNT];
+  int64_t rhs_columns;     /* sum over solve sweeps of the right-hand sides swept */
 } pdeshep_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -102,6 +118,9 @@ const char* pdeshep_last_error(void);
 
 /* Library version string. */
 const char* pdeshep_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far. */
+uint64_t pdeshep_kernel_launches(void);
 
 /* ------------------------------------------------------------------------ */
 /* Sylvester inertia (Section 3.2; Section 3.1): for every sigma_s counts the  */

@@ -35,6 +35,7 @@ STATUS = {
 
 EXPORTED = [
     "pdeshep_opts_default", "pdeshep_status_string", "pdeshep_last_error", "pdeshep_version",
+    "pdeshep_kernel_launches",
     "pdeshep_inertia_workspace_size", "pdeshep_inertia", "pdeshep_bisect_workspace_size",
     "pdeshep_bisect", "pdeshep_gershgorin", "pdeshep_contour_rule",
     "pdeshep_shifted_solve_workspace_size", "pdeshep_shifted_solve", "pdeshep_band_matmul",
@@ -56,16 +57,27 @@ class Opts(C.Structure):
     ]
 
 
+KERNEL_GROUPS = ["inertia", "factor", "solve", "accum", "gemm", "small", "bandmm"]
+
+
 class Stats(C.Structure):
     _fields_ = [
         ("iterations", C.c_int32), ("waves", C.c_int32), ("factorizations", C.c_int64),
         ("rhs_sweeps", C.c_int64), ("ms_inertia", C.c_double), ("ms_factor", C.c_double),
         ("ms_solve", C.c_double), ("ms_rr", C.c_double), ("ms_total", C.c_double),
         ("max_residual", C.c_double), ("min_rel_error_est", C.c_double),
+        ("kg_ms", C.c_double * 7), ("kg_launches", C.c_int64 * 7), ("kg_flops", C.c_double * 7),
+        ("rhs_columns", C.c_int64),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            if k.startswith("kg_"):
+                v = {g: float(v[i]) if k != "kg_launches" else int(v[i]) for i, g in enumerate(KERNEL_GROUPS)}
+            out[k] = v
+        return out
 
 
 class PdeshepError(RuntimeError):
@@ -92,6 +104,7 @@ def load(path: str = LIB_PATH):
         "pdeshep_status_string": (C.c_char_p, [C.c_int]),
         "pdeshep_last_error": (C.c_char_p, []),
         "pdeshep_version": (C.c_char_p, []),
+        "pdeshep_kernel_launches": (C.c_uint64, []),
         "pdeshep_inertia_workspace_size": (sz, [i64, i32, i32, i32]),
         "pdeshep_inertia": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P, P, sz, P]),
         "pdeshep_bisect_workspace_size": (sz, [i64, i32, i32, i32, i32]),
@@ -158,6 +171,11 @@ def _band_args(band, b):
 # ---------------------------------------------------------------------------- entry points
 def version() -> str:
     return load().pdeshep_version().decode()
+
+
+def kernel_launches() -> int:
+    """CUDA kernels launched by the library so far in this process."""
+    return int(load().pdeshep_kernel_launches())
 
 
 def inertia(band, sigmas, b=None, pivots=False, stream=None):

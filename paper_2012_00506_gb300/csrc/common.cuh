@@ -19,6 +19,9 @@ namespace pdeshep {
 // ----------------------------------------------------------------------------
 void set_last_error(const char* where, cudaError_t e);
 void set_last_error_msg(const char* msg);
+// process-wide count of kernels launched by this library
+void count_launch();
+unsigned long long launches_so_far();
 
 #define PD_CK(...)                                    \
   do {                                                \
@@ -31,6 +34,7 @@ void set_last_error_msg(const char* msg);
 
 #define PD_CK_LAUNCH()                                \
   do {                                                \
+    ::pdeshep::count_launch();                        \
     cudaError_t _e = cudaGetLastError();              \
     if (_e != cudaSuccess) {                          \
       ::pdeshep::set_last_error("kernel launch", _e); \

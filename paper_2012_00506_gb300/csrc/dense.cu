@@ -155,6 +155,7 @@ static int launch_cluster(K kernel, int nblk, size_t smem, cudaStream_t st, Args
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   PD_CK(cudaLaunchKernelEx(&cfg, kernel, args...));
+  count_launch();
   return 0;
 }
 

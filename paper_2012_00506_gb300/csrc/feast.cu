@@ -315,6 +315,55 @@ struct Plan {
   int splits;
 };
 
+// CUDA-event timing of kernel groups (only when the caller asks for stats).
+struct KTimer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> grp;
+  int used = 0, cur_g = 0;
+  unsigned long long cur_l0 = 0;
+  double ms[PDESHEP_KG_COUNT] = {};
+  long long nl[PDESHEP_KG_COUNT] = {};
+  double fl[PDESHEP_KG_COUNT] = {};
+  int begin(int g) {
+    if (!on) return 0;
+    while ((int)ev.size() < used + 2) {
+      cudaEvent_t e;
+      PD_CK(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+    PD_CK(cudaEventRecord(ev[used], st));
+    cur_g = g;
+    cur_l0 = launches_so_far();
+    return 0;
+  }
+  int end(double flops) {
+    if (!on) return 0;
+    PD_CK(cudaEventRecord(ev[used + 1], st));
+    grp.push_back(cur_g);
+    nl[cur_g] += (long long)(launches_so_far() - cur_l0);
+    fl[cur_g] += flops;
+    used += 2;
+    return 0;
+  }
+  int collect() {
+    if (!on || used == 0) return 0;
+    PD_CK(cudaEventSynchronize(ev[used - 1]));
+    for (int i = 0; i < used / 2; ++i) {
+      float t = 0;
+      PD_CK(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
+      ms[grp[i]] += t;
+    }
+    used = 0;
+    grp.clear();
+    return 0;
+  }
+  ~KTimer() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
 template <typename S, typename C>
 struct Feast {
   int64_t n;
@@ -338,7 +387,8 @@ struct Feast {
   bool factored;
   pdeshep_stats stats;
   std::vector<int> active;  // slice indices
-  cudaEvent_t ev[2];
+  KTimer kt;
+  double cw() const { return cplx ? 8.0 : 2.0; }  // real flops per multiply-add of the FP64 subspace type
 
   size_t fixed_bytes(Arena& a, bool carve) {
     Plan q;
@@ -455,13 +505,18 @@ struct FeastRun : Feast<S, C> {
     PD_CK(cudaMemcpyAsync(d_it, it.data(), sizeof(GemmItem<S>) * na, cudaMemcpyHostToDevice, st));
     const int mm = act_max_m0();
     S one = sc_host_one(), zero = sc_host_zero();
+    double fl = 0.0;
+    for (int s : active) fl += this->cw() * (double)n * m0[s] * m0[s];
+    PD_TRY(this->kt.begin(PDESHEP_KG_GEMM));
     if (kind == 0) {
       const int64_t tiles = (int64_t)na * ceil_div(mm, 64) * ceil_div(mm, 64);
       int splits = (int)std::min<int64_t>(p.splits, std::max<int64_t>(1, ceil_div(2 * 152, tiles)));
       splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, n / 256));
-      return launch_gemm<S>(true, na, d_it, mm, mm, (int)n, one, zero, splits, (S*)p.part, Msq, st);
+      PD_TRY(launch_gemm<S>(true, na, d_it, mm, mm, (int)n, one, zero, splits, (S*)p.part, Msq, st));
+    } else {
+      PD_TRY(launch_gemm<S>(false, na, d_it, (int)n, mm, mm, one, zero, 1, (S*)p.part, Msq, st));
     }
-    return launch_gemm<S>(false, na, d_it, (int)n, mm, mm, one, zero, 1, (S*)p.part, Msq, st);
+    return this->kt.end(fl);
   }
 
   static S sc_host_one() {
@@ -472,9 +527,12 @@ struct FeastRun : Feast<S, C> {
   }
 
   int band_mm(const S* X, S* Y) {
+    double fl = 0.0;
+    for (int s : active) fl += this->cw() * (2.0 * b + 1.0) * (double)n * m0[s];
+    PD_TRY(this->kt.begin(PDESHEP_KG_BANDMM));
     for (int s : active)
       PD_TRY(launch_band_matmul<S>(n, b, band, ldab, m0[s], X + col_off[s] * n, Y + col_off[s] * n, st));
-    return 0;
+    return this->kt.end(fl);
   }
 
   // Rayleigh-Ritz on Q for the active slices -> Xt, lam, BQ = residuals, res, colscale, nconv
@@ -486,10 +544,14 @@ struct FeastRun : Feast<S, C> {
     S* G = (S*)p.small_G;
     S* I = (S*)p.small_I;
     S* W = (S*)p.small_W;
+    double flsmall = 0.0;
+    for (int s : active) flsmall += this->cw() * (double)m0[s] * m0[s] * m0[s] / 3.0;
     for (int pass = 0; pass < 2; ++pass) {
       PD_TRY(gemm(0, (S*)p.Q, (S*)p.Q, G));
+      PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
       PD_TRY(launch_cholesky<S>(na, p.d_small, G, p.info, st));
       PD_TRY(launch_triinv<S>(na, p.d_small, G, I, st));
+      PD_TRY(this->kt.end(flsmall));
       PD_TRY(gemm(1, (S*)p.Q, I, (S*)p.Q2));
       std::swap(p.Q, p.Q2);
     }
@@ -502,14 +564,18 @@ struct FeastRun : Feast<S, C> {
     }
     PD_TRY(band_mm((S*)p.Q, (S*)p.BQ));
     PD_TRY(gemm(0, (S*)p.Q, (S*)p.BQ, G));
+    PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
     symmetrize_kernel<S><<<dim3(grid1((int64_t)mm * mm), na), 256, 0, st>>>(p.d_small, G);
     PD_CK_LAUNCH();
     PD_TRY(launch_jacobi<S>(na, p.d_small, mm, G, I, W, p.lam, 1e-14, 60, p.sweeps, p.jscratch, st));
+    PD_TRY(this->kt.end(0.0));
     PD_TRY(gemm(1, (S*)p.Q, W, (S*)p.Xt));
     PD_TRY(band_mm((S*)p.Xt, (S*)p.BQ));
+    PD_TRY(this->kt.begin(PDESHEP_KG_BANDMM));
     residual_kernel<S><<<dim3(mm, na), 256, 0, st>>>(n, p.d_sd, (S*)p.Xt, (S*)p.BQ, p.lam, bnorm, p.res,
                                                      p.colscale);
     PD_CK_LAUNCH();
+    PD_TRY(this->kt.end(0.0));
     nconv_kernel<<<na, 256, 0, st>>>(p.d_sd, p.lam, p.res, o->tol, p.nconv);
     PD_CK_LAUNCH();
     std::vector<int> sw(K, 0);
@@ -518,7 +584,7 @@ struct FeastRun : Feast<S, C> {
     PD_CK(cudaStreamSynchronize(st));
     for (int s : active)
       if (sw[s] < 0) return PDESHEP_EIG_NOT_CONVERGED;
-    return 0;
+    return this->kt.collect();
   }
 
   SysDesc sys_desc(int s, int j, int64_t off) const {
@@ -538,7 +604,9 @@ struct FeastRun : Feast<S, C> {
     const int ns = (int)sd.size();
     if (!ns) return 0;
     PD_CK(cudaMemcpyAsync(p.d_sys, sd.data(), sizeof(SysDesc) * ns, cudaMemcpyHostToDevice, st));
+    PD_TRY(this->kt.begin(PDESHEP_KG_FACTOR));
     PD_TRY(launch_factor<C>(g, cplx, band, ldab, ns, p.d_sys, p.wave_base, p.sys_status, nullptr, st));
+    PD_TRY(this->kt.end(16.0 * ns * (double)n * b * b));
     std::vector<int> status(ns, 0);
     PD_CK(cudaMemcpyAsync(status.data(), p.sys_status, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
@@ -554,16 +622,22 @@ struct FeastRun : Feast<S, C> {
     int mcols = 0;
     for (auto& d : sd) mcols = std::max(mcols, d.ncols);
     PD_CK(cudaMemcpyAsync(p.d_sys, sd.data(), sizeof(SysDesc) * ns, cudaMemcpyHostToDevice, st));
+    double cols = 0.0;
+    for (auto& d : sd) cols += d.ncols;
+    PD_TRY(this->kt.begin(PDESHEP_KG_SOLVE));
     PD_TRY(launch_solve<C>(g, 0, ns, mcols, p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, 0, st));
     if (cplx)
       PD_TRY(launch_solve<C>(g, 1, ns, mcols, p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, 0, st));
+    PD_TRY(this->kt.end(24.0 * (double)n * b * cols * (cplx ? 2 : 1)));
     for (auto& d : sd) stats.rhs_sweeps += ceil_div(d.ncols, 32) * (cplx ? 2 : 1);
+    stats.rhs_columns += (int64_t)cols * (cplx ? 2 : 1);
     const int na = (int)acc.size();
     PD_CK(cudaMemcpyAsync(p.d_acc, acc.data(), sizeof(AccDesc) * na, cudaMemcpyHostToDevice, st));
+    PD_TRY(this->kt.begin(PDESHEP_KG_ACCUM));
     accumulate_kernel<S, C><<<dim3(grid1(n * mcols), na), 256, 0, st>>>(n, p.d_acc, p.coef,
                                                                        (const C*)p.wave_base, (S*)p.Q, cplx);
     PD_CK_LAUNCH();
-    return 0;
+    return this->kt.end(8.0 * (double)n * cols * (cplx ? 2 : 1));
   }
 
   // Q = filter(Xt or residuals) for the active slices
@@ -573,6 +647,7 @@ struct FeastRun : Feast<S, C> {
     PD_TRY(upload_active());
     const int mm = act_max_m0();
     const S* src = mode ? (const S*)p.BQ : (const S*)p.Xt;
+    PD_TRY(this->kt.begin(PDESHEP_KG_ACCUM));
     make_rhs_kernel<S, C><<<dim3(grid1(n * mm), na), 256, 0, st>>>(n, p.d_sd, src, mode ? p.colscale : nullptr,
                                                                   (C*)p.Yc);
     PD_CK_LAUNCH();
@@ -581,6 +656,7 @@ struct FeastRun : Feast<S, C> {
     PD_CK_LAUNCH();
     q_init_kernel<S><<<dim3(grid1(n * mm), na), 256, 0, st>>>(n, p.d_sd, p.beta, (const S*)p.Xt, (S*)p.Q, mode);
     PD_CK_LAUNCH();
+    PD_TRY(this->kt.end(0.0));
     if (resident) {
       if (!factored) {
         std::vector<SysDesc> all;
@@ -672,6 +748,8 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   F.g = make_geom(n, b);
   F.es = sizeof(C);
   F.fb = factor_bytes(F.g, sizeof(C));
+  F.kt.on = (h_stats != nullptr);
+  F.kt.st = (cudaStream_t)o->stream;
   F.m0.assign(h_m0, h_m0 + K);
   F.col_off.assign(K, 0);
   F.small_off.assign(K, 0);
@@ -722,8 +800,10 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   F.bounds.assign(h_bounds, h_bounds + K + 1);
   std::vector<int64_t> neg(K + 1);
   bool bad = false;
+  PD_TRY(F.kt.begin(PDESHEP_KG_INERTIA));
   PD_TRY(inertia_counts(n, b, cplx, band, ldab, K + 1, h_bounds, neg.data(), nullptr, F.p.inertia_ws,
                         F.p.inertia_bytes, st, &bad));
+  PD_TRY(F.kt.end((K + 1) * (double)n * b * b * (cplx ? 4.0 : 1.0)));
   if (bad) return PDESHEP_NONFINITE_INPUT;
   F.counts.assign(K, 0);
   F.nconv.assign(K, 0);
@@ -838,11 +918,17 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   if (h_stats) {
     F.stats.iterations = 0;
     for (int s = 0; s < K; ++s) F.stats.iterations = std::max(F.stats.iterations, F.iters[s]);
-    F.stats.ms_factor = 0;
     F.stats.ms_solve = ms_filter;
     F.stats.ms_rr = ms_rr;
     F.stats.ms_total = F.stats.ms_inertia + ms_filter + ms_rr;
     F.stats.max_residual = maxres;
+    PD_TRY(F.kt.collect());
+    for (int gi = 0; gi < PDESHEP_KG_COUNT; ++gi) {
+      F.stats.kg_ms[gi] = F.kt.ms[gi];
+      F.stats.kg_launches[gi] = F.kt.nl[gi];
+      F.stats.kg_flops[gi] = F.kt.fl[gi];
+    }
+    F.stats.ms_factor = F.kt.ms[PDESHEP_KG_FACTOR];
     *h_stats = F.stats;
   }
   return status;

@@ -13,6 +13,10 @@
 namespace pdeshep {
 
 static thread_local char g_last_error[512] = "";
+static unsigned long long g_launches = 0;
+
+void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+unsigned long long launches_so_far() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 void set_last_error(const char* where, cudaError_t e) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
@@ -157,6 +161,8 @@ using namespace pdeshep;
 extern "C" const char* pdeshep_last_error(void) { return g_last_error; }
 
 extern "C" const char* pdeshep_version(void) { return "pdeshep-gb300 0.1 (sm_103a)"; }
+
+extern "C" uint64_t pdeshep_kernel_launches(void) { return (uint64_t)launches_so_far(); }
 
 extern "C" const char* pdeshep_status_string(int s) {
   switch (s) {
