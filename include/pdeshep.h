@@ -215,8 +215,10 @@ int pdeshep_cholqr(int64_t n, int32_t is_complex, int32_t nblk, const int32_t* h
 /* sum_{u<t} m_u^2 of d_a (overwritten), eigenvalues ascending into d_lam     */
 /* (offset sum_{u<t} m_u), eigenvectors into d_v (same layout as d_a), each   */
 /* scaled so its first largest-magnitude component is real positive.         */
-/* FP64 cyclic Jacobi in parallel (round-robin) order, one thread-block      */
-/* cluster per block; sweeps stop when off(A) <= 1e-14 ||A||_F.               */
+/* Cyclic Jacobi in parallel (round-robin) order on a thread-block cluster    */
+/* per block: FP32 sweeps give V32, then H = V32^H A V32 (FP64) is nearly     */
+/* diagonal and FP64 sweeps finish it (off(H) <= 1e-14 ||H||_F); the          */
+/* eigenvectors are V32 W.                                                    */
 /* ------------------------------------------------------------------------ */
 size_t pdeshep_eigh_workspace_size(int32_t nblk, const int32_t* h_m, int32_t is_complex);
 int pdeshep_eigh(int32_t is_complex, int32_t nblk, const int32_t* h_m, void* d_a, double* d_lam,

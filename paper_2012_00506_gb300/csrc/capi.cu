@@ -152,15 +152,17 @@ static int cholqr(int64_t n, int nblk, const int32_t* m, S* Q, int passes, S* R,
       it[t] = GemmItem<S>{cur + coff[t] * n, cur + coff[t] * n, (S*)w.G + soff[t], m[t], m[t], (int)n, (int)n,
                           (int)n, m[t], soff[t]};
     PD_CK(cudaMemcpyAsync(w.items, it.data(), sizeof(GemmItem<S>) * nblk, cudaMemcpyHostToDevice, st));
-    int splits = (int)std::max<int64_t>(1, std::min<int64_t>(kCholSplits, n / 256));
-    PD_TRY(launch_gemm<S>(true, nblk, (GemmItem<S>*)w.items, mm, mm, (int)n, one, zero, splits, (S*)w.part, msq, st));
+    int splits = (int)std::max<int64_t>(1, std::min<int64_t>(kCholSplits, n / 512));
+    PD_TRY(launch_gemm<S>(true, nblk, (GemmItem<S>*)w.items, mm, mm, (int)n, one, zero, splits, (S*)w.part, msq, st,
+                          1, 0));
     PD_TRY(launch_cholesky<S>(nblk, w.desc, (S*)w.G, w.info, st));
     PD_TRY(launch_triinv<S>(nblk, w.desc, (S*)w.G, (S*)w.I, st));
     for (int t = 0; t < nblk; ++t)
       it[t] = GemmItem<S>{cur + coff[t] * n, (S*)w.I + soff[t], nxt + coff[t] * n, (int)n, m[t], m[t], (int)n, m[t],
                           (int)n, 0};
     PD_CK(cudaMemcpyAsync(w.items, it.data(), sizeof(GemmItem<S>) * nblk, cudaMemcpyHostToDevice, st));
-    PD_TRY(launch_gemm<S>(false, nblk, (GemmItem<S>*)w.items, (int)n, mm, mm, one, zero, 1, (S*)w.part, msq, st));
+    PD_TRY(launch_gemm<S>(false, nblk, (GemmItem<S>*)w.items, (int)n, mm, mm, one, zero, 1, (S*)w.part, msq, st,
+                          0, 1));
     std::swap(cur, nxt);
   }
   if (cur != Q) PD_CK(cudaMemcpyAsync(Q, cur, sizeof(S) * n * c, cudaMemcpyDeviceToDevice, st));
@@ -176,28 +178,16 @@ static int cholqr(int64_t n, int nblk, const int32_t* m, S* Q, int passes, S* R,
 // ---------------------------------------------------------------------------
 // small Hermitian eigensolver
 // ---------------------------------------------------------------------------
-struct EighWs {
-  void* Vw;
-  int* sweeps;
-  double* scratch;
-  SmallDesc* desc;
-};
-
-static EighWs plan_eigh(Arena& a, int nblk, const int32_t* m, size_t es) {
-  EighWs w;
-  int64_t msq = 0;
-  for (int t = 0; t < nblk; ++t) msq += (int64_t)m[t] * m[t];
-  w.Vw = a.take<char>(msq * es);
-  w.sweeps = a.take<int>(nblk);
-  w.scratch = a.take<double>((size_t)nblk * 2 * 16);
-  w.desc = a.take<SmallDesc>(nblk);
-  return w;
-}
-
 template <typename S>
 static int eigh(int nblk, const int32_t* m, S* A, double* lam, S* V, void* work, size_t wbytes, cudaStream_t st) {
   Arena a(work, wbytes);
-  EighWs w = plan_eigh(a, nblk, m, sizeof(S));
+  int64_t msq = 0, mtot = 0;
+  for (int t = 0; t < nblk; ++t) {
+    msq += (int64_t)m[t] * m[t];
+    mtot += m[t];
+  }
+  EighScratch<S> w = plan_eigh_scratch<S>(a, msq, mtot, nblk);
+  SmallDesc* d_desc = a.take<SmallDesc>(nblk);
   if (!a.fits()) return PDESHEP_WORKSPACE_TOO_SMALL;
   std::vector<SmallDesc> desc(nblk);
   int64_t so = 0, vo = 0;
@@ -208,14 +198,29 @@ static int eigh(int nblk, const int32_t* m, S* A, double* lam, S* V, void* work,
     vo += m[t];
     mm = std::max(mm, (int)m[t]);
   }
-  PD_CK(cudaMemcpyAsync(w.desc, desc.data(), sizeof(SmallDesc) * nblk, cudaMemcpyHostToDevice, st));
-  PD_TRY(launch_jacobi<S>(nblk, w.desc, mm, A, (S*)w.Vw, V, lam, 1e-14, 60, w.sweeps, w.scratch, st));
+  PD_CK(cudaMemcpyAsync(d_desc, desc.data(), sizeof(SmallDesc) * nblk, cudaMemcpyHostToDevice, st));
+  PD_TRY(eigh_mixed<S>(nblk, d_desc, desc.data(), mm, A, lam, V, w, st));
   std::vector<int> sw(nblk);
   PD_CK(cudaMemcpyAsync(sw.data(), w.sweeps, sizeof(int) * nblk, cudaMemcpyDeviceToHost, st));
   PD_CK(cudaStreamSynchronize(st));
   for (int v : sw)
     if (v < 0) return PDESHEP_EIG_NOT_CONVERGED;
   return 0;
+}
+
+static size_t eigh_ws(int nblk, const int32_t* m, size_t es) {
+  Arena a;
+  int64_t msq = 0, mtot = 0;
+  for (int t = 0; t < nblk; ++t) {
+    msq += (int64_t)m[t] * m[t];
+    mtot += m[t];
+  }
+  if (es == sizeof(double2))
+    plan_eigh_scratch<double2>(a, msq, mtot, nblk);
+  else
+    plan_eigh_scratch<double>(a, msq, mtot, nblk);
+  a.take<SmallDesc>(nblk);
+  return a.used();
 }
 
 }  // namespace pdeshep
@@ -297,9 +302,7 @@ extern "C" int pdeshep_cholqr(int64_t n, int32_t is_complex, int32_t nblk, const
 
 extern "C" size_t pdeshep_eigh_workspace_size(int32_t nblk, const int32_t* h_m, int32_t is_complex) {
   if (nblk <= 0 || !h_m) return 0;
-  Arena a;
-  plan_eigh(a, nblk, h_m, is_complex ? sizeof(double2) : sizeof(double));
-  return a.used();
+  return eigh_ws(nblk, h_m, is_complex ? sizeof(double2) : sizeof(double));
 }
 
 extern "C" int pdeshep_eigh(int32_t is_complex, int32_t nblk, const int32_t* h_m, void* d_a, double* d_lam,

@@ -210,6 +210,58 @@ struct sc<double2> {
   static __device__ __forceinline__ double2 from_re(double r) { return make_double2(r, 0.0); }
 };
 
+template <>
+struct sc<float> {
+  static __device__ __forceinline__ float zero() { return 0.0f; }
+  static __device__ __forceinline__ float conj(float a) { return a; }
+  static __device__ __forceinline__ void fma_(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
+  static __device__ __forceinline__ float abs2(float a) { return a * a; }
+  static __device__ __forceinline__ float re(float a) { return a; }
+  static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+  static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+  static __device__ __forceinline__ float scale(float a, float s) { return a * s; }
+  static __device__ __forceinline__ float from_re(float r) { return r; }
+};
+template <>
+struct sc<float2> {
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.0f, 0.0f); }
+  static __device__ __forceinline__ float2 conj(float2 a) { return make_float2(a.x, -a.y); }
+  static __device__ __forceinline__ void fma_(float2& acc, float2 a, float2 b) { cfma(acc, a, b); }
+  static __device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+  static __device__ __forceinline__ float re(float2 a) { return a.x; }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return cmul(a, b); }
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return csub(a, b); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return cadd(a, b); }
+  static __device__ __forceinline__ float2 scale(float2 a, float s) { return cscale(a, s); }
+  static __device__ __forceinline__ float2 from_re(float r) { return make_float2(r, 0.0f); }
+};
+
+// real type of a scalar (double for double/double2, float for float/float2)
+template <typename S>
+struct real_t {
+  using type = double;
+};
+template <>
+struct real_t<float> {
+  using type = float;
+};
+template <>
+struct real_t<float2> {
+  using type = float;
+};
+// single-precision counterpart of an FP64 scalar type
+template <typename S>
+struct lowp;
+template <>
+struct lowp<double> {
+  using type = float;
+};
+template <>
+struct lowp<double2> {
+  using type = float2;
+};
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace pdeshep

@@ -22,9 +22,11 @@ struct GemmItem {
 
 // Launch a batch of products.  splits > 1 splits the k dimension; then `part`
 // must hold splits * sum_i(m_i * n_i) elements (deterministic reduction).
+// herm: output Hermitian (only upper tiles computed, lower mirrored); triB: B upper triangular.
 template <typename S>
 int launch_gemm(bool conjA, int nitems, const GemmItem<S>* d_items, int max_m, int max_n, int max_k,
-                S alpha, S beta, int splits, S* part, int64_t part_stride, cudaStream_t st);
+                S alpha, S beta, int splits, S* part, int64_t part_stride, cudaStream_t st, int herm = 0,
+                int triB = 0);
 
 // Per-slice small dense kernels.  Blocks of slice t start at offset off[t]
 // (elements) with order m[t]; one thread-block cluster per slice.
@@ -37,8 +39,12 @@ struct SmallDesc {
 
 // In-place upper Cholesky G = R^H R (upper triangle of G becomes R, lower
 // cleared).  info[t] = j+1 if pivot j is not positive.
+// diag0 (optional, vector layout voff) receives the diagonal of G before factorization and
+// minratio[t] (optional) = min_c R(c,c)^2 / G(c,c): the squared sine of the smallest angle
+// between a column and the span of the ones before it.
 template <typename S>
-int launch_cholesky(int nblk, const SmallDesc* d_desc, S* G, int* info, cudaStream_t st);
+int launch_cholesky(int nblk, const SmallDesc* d_desc, S* G, int* info, cudaStream_t st,
+                    double* diag0 = nullptr, double* minratio = nullptr);
 
 // Rinv = R^{-1} for upper triangular R (out of place, same layout).
 template <typename S>
@@ -50,6 +56,29 @@ int launch_triinv(int nblk, const SmallDesc* d_desc, const S* R, S* Rinv, cudaSt
 template <typename S>
 int launch_jacobi(int nblk, const SmallDesc* d_desc, int max_m, S* A, S* Vwork, S* Vout, double* lam,
                   double tol, int max_sweeps, int* sweeps_out, double* scratch, cudaStream_t st);
+
+// Mixed-precision small Hermitian eigensolver: FP32 Jacobi gives V32; in FP64
+// H = V32^H A V32 is nearly diagonal and a few FP64 Jacobi sweeps finish it;
+// the eigenvectors are V32 W64.  Same layout and outputs as launch_jacobi.
+template <typename S>
+struct EighScratch {
+  typename lowp<S>::type* A32;
+  typename lowp<S>::type* V32w;
+  typename lowp<S>::type* V32;
+  S* Vd;
+  S* T;
+  S* Vw;
+  S* W64;
+  double* lam32;
+  int* sweeps;
+  double* jscratch;
+  GemmItem<S>* items;
+};
+template <typename S>
+EighScratch<S> plan_eigh_scratch(Arena& a, int64_t msq, int64_t mtot, int nblk);
+template <typename S>
+int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int max_m, S* A, double* lam, S* W,
+               const EighScratch<S>& w, cudaStream_t st, int* fp64_sweeps_out = nullptr);
 
 // Y = B X for the Hermitian band (lower storage), X, Y n x ncols (ld n).
 template <typename S>

@@ -297,6 +297,8 @@ struct Plan {
   void* small_W;   // S sum m0^2 (eigenvectors)
   void* part;      // S splits * sum m0^2
   int* info;       // K (Cholesky)
+  double* minratio;// K (Cholesky conditioning indicator)
+  double* diag0;   // M (Gram diagonal)
   int* sweeps;     // K
   int* nconv;      // K
   int* dest;       // M
@@ -387,6 +389,8 @@ struct Feast {
   bool factored;
   pdeshep_stats stats;
   std::vector<int> active;  // slice indices
+  std::vector<SmallDesc> h_small;  // small-block descriptors of the active slices
+  EighScratch<S> eig;
   KTimer kt;
   double cw() const { return cplx ? 8.0 : 2.0; }  // real flops per multiply-add of the FP64 subspace type
 
@@ -409,6 +413,8 @@ struct Feast {
     q.splits = 8;
     q.part = a.take<S>((size_t)q.splits * Msq);
     q.info = a.take<int>(K);
+    q.minratio = a.take<double>(K);
+    q.diag0 = a.take<double>(M);
     q.sweeps = a.take<int>(K);
     q.nconv = a.take<int>(K);
     q.dest = a.take<int>(M);
@@ -419,6 +425,10 @@ struct Feast {
     q.d_items = a.take<GemmItem<double2>>((size_t)4 * K);
     q.d_acc = a.take<AccDesc>(K);
     q.d_sys = a.take<SysDesc>((size_t)K * ne);
+    {
+      EighScratch<S> e = plan_eigh_scratch<S>(a, Msq, M, K);
+      if (carve) eig = e;
+    }
     q.inertia_bytes = std::max(inertia_ws_bytes(b, cplx, K + 1), bisect_ws_bytes(b, cplx, 2, 16));
     q.inertia_ws = a.take<char>(q.inertia_bytes);
     if (carve) p = q;
@@ -451,14 +461,14 @@ struct FeastRun : Feast<S, C> {
   int upload_active() {
     const int na = (int)active.size();
     h_sd.resize(na);
-    std::vector<SmallDesc> sm(na);
+    this->h_small.resize(na);
     for (int a = 0; a < na; ++a) {
       const int s = active[a];
       h_sd[a] = SliceDesc{col_off[s], m0[s], s, bounds[s], bounds[s + 1]};
-      sm[a] = SmallDesc{small_off[s], col_off[s], m0[s], 0};
+      this->h_small[a] = SmallDesc{small_off[s], col_off[s], m0[s], 0};
     }
     PD_CK(cudaMemcpyAsync(p.d_sd, h_sd.data(), sizeof(SliceDesc) * na, cudaMemcpyHostToDevice, st));
-    PD_CK(cudaMemcpyAsync(p.d_small, sm.data(), sizeof(SmallDesc) * na, cudaMemcpyHostToDevice, st));
+    PD_CK(cudaMemcpyAsync(p.d_small, this->h_small.data(), sizeof(SmallDesc) * na, cudaMemcpyHostToDevice, st));
     return 0;
   }
 
@@ -470,7 +480,7 @@ struct FeastRun : Feast<S, C> {
 
   // C = op(A) B over the active slices; kind 0: C(m0 x m0) = A^H B with A,B n x m0 blocks;
   // kind 1: C(n x m0) = A(n x m0) * B(m0 x m0 small block).
-  int gemm(int kind, const S* A, const S* Bm, S* Cm) {
+  int gemm(int kind, const S* A, const S* Bm, S* Cm, int tri = 0) {
     const int na = (int)active.size();
     std::vector<GemmItem<S>> it(na);
     for (int a = 0; a < na; ++a) {
@@ -505,16 +515,17 @@ struct FeastRun : Feast<S, C> {
     PD_CK(cudaMemcpyAsync(d_it, it.data(), sizeof(GemmItem<S>) * na, cudaMemcpyHostToDevice, st));
     const int mm = act_max_m0();
     S one = sc_host_one(), zero = sc_host_zero();
-    double fl = 0.0;
-    for (int s : active) fl += this->cw() * (double)n * m0[s] * m0[s];
+    double fl = 0.0;  // algorithmic: Hermitian or triangular products count half
+    for (int s : active) fl += this->cw() * (double)n * m0[s] * m0[s] * ((kind == 0 || tri) ? 0.5 : 1.0);
     PD_TRY(this->kt.begin(PDESHEP_KG_GEMM));
     if (kind == 0) {
-      const int64_t tiles = (int64_t)na * ceil_div(mm, 64) * ceil_div(mm, 64);
-      int splits = (int)std::min<int64_t>(p.splits, std::max<int64_t>(1, ceil_div(2 * 152, tiles)));
-      splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, n / 256));
-      PD_TRY(launch_gemm<S>(true, na, d_it, mm, mm, (int)n, one, zero, splits, (S*)p.part, Msq, st));
+      const int64_t t1 = ceil_div(mm, 32);
+      const int64_t tiles = (int64_t)na * t1 * (t1 + 1) / 2;
+      int splits = (int)std::min<int64_t>(p.splits, std::max<int64_t>(1, ceil_div(8 * 152, tiles)));
+      splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, n / 512));
+      PD_TRY(launch_gemm<S>(true, na, d_it, mm, mm, (int)n, one, zero, splits, (S*)p.part, Msq, st, 1, 0));
     } else {
-      PD_TRY(launch_gemm<S>(false, na, d_it, (int)n, mm, mm, one, zero, 1, (S*)p.part, Msq, st));
+      PD_TRY(launch_gemm<S>(false, na, d_it, (int)n, mm, mm, one, zero, 1, (S*)p.part, Msq, st, 0, tri));
     }
     return this->kt.end(fl);
   }
@@ -535,6 +546,25 @@ struct FeastRun : Feast<S, C> {
     return this->kt.end(fl);
   }
 
+  // One CholQR pass on the active slices' blocks of p.Q (result back in p.Q).
+  int cholqr_pass() {
+    const int na = (int)active.size();
+    S* G = (S*)p.small_G;
+    S* I = (S*)p.small_I;
+    double flsmall = 0.0;
+    for (int s : active) flsmall += this->cw() * (double)m0[s] * m0[s] * m0[s] / 3.0;
+    PD_TRY(gemm(0, (S*)p.Q, (S*)p.Q, G));
+    PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
+    PD_TRY(launch_cholesky<S>(na, p.d_small, G, p.info, st, p.diag0, p.minratio));
+    PD_TRY(launch_triinv<S>(na, p.d_small, G, I, st));
+    PD_TRY(this->kt.end(flsmall));
+    PD_TRY(gemm(1, (S*)p.Q, I, (S*)p.Q2, 1));
+    for (int s : active)
+      PD_CK(cudaMemcpyAsync((S*)p.Q + col_off[s] * n, (S*)p.Q2 + col_off[s] * n, sizeof(S) * n * m0[s],
+                            cudaMemcpyDeviceToDevice, st));
+    return 0;
+  }
+
   // Rayleigh-Ritz on Q for the active slices -> Xt, lam, BQ = residuals, res, colscale, nconv
   int rr() {
     const int na = (int)active.size();
@@ -544,30 +574,38 @@ struct FeastRun : Feast<S, C> {
     S* G = (S*)p.small_G;
     S* I = (S*)p.small_I;
     S* W = (S*)p.small_W;
-    double flsmall = 0.0;
-    for (int s : active) flsmall += this->cw() * (double)m0[s] * m0[s] * m0[s] / 3.0;
-    for (int pass = 0; pass < 2; ++pass) {
-      PD_TRY(gemm(0, (S*)p.Q, (S*)p.Q, G));
-      PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
-      PD_TRY(launch_cholesky<S>(na, p.d_small, G, p.info, st));
-      PD_TRY(launch_triinv<S>(na, p.d_small, G, I, st));
-      PD_TRY(this->kt.end(flsmall));
-      PD_TRY(gemm(1, (S*)p.Q, I, (S*)p.Q2));
-      std::swap(p.Q, p.Q2);
-    }
-    {
-      std::vector<int> info(K, 0);
+    // CholQR: one pass, repeated for the slices whose columns were far from
+    // orthogonal (min_c R(c,c)^2/G(c,c) < 1/4), i.e. CholQR2 where it matters.
+    PD_TRY(cholqr_pass());
+    std::vector<int> info(K, 0);
+    std::vector<double> mr(K, 1.0);
+    PD_CK(cudaMemcpyAsync(info.data(), p.info, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaMemcpyAsync(mr.data(), p.minratio, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    // per-slice kernel outputs (info, minratio, sweeps) are indexed by position in the active batch
+    for (int a = 0; a < na; ++a)
+      if (info[a]) return PDESHEP_CHOLQR_BREAKDOWN;
+    std::vector<int> again;
+    for (int a = 0; a < na; ++a)
+      if (mr[a] < 0.25) again.push_back(active[a]);
+    if (!again.empty()) {
+      std::vector<int> keep = active;
+      active = again;
+      PD_TRY(upload_active());
+      PD_TRY(cholqr_pass());
+      active = keep;
+      PD_TRY(upload_active());
       PD_CK(cudaMemcpyAsync(info.data(), p.info, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
       PD_CK(cudaStreamSynchronize(st));
-      for (int s : active)
-        if (info[s]) return PDESHEP_CHOLQR_BREAKDOWN;
+      for (int a = 0; a < (int)again.size(); ++a)
+        if (info[a]) return PDESHEP_CHOLQR_BREAKDOWN;
     }
     PD_TRY(band_mm((S*)p.Q, (S*)p.BQ));
     PD_TRY(gemm(0, (S*)p.Q, (S*)p.BQ, G));
     PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
     symmetrize_kernel<S><<<dim3(grid1((int64_t)mm * mm), na), 256, 0, st>>>(p.d_small, G);
     PD_CK_LAUNCH();
-    PD_TRY(launch_jacobi<S>(na, p.d_small, mm, G, I, W, p.lam, 1e-14, 60, p.sweeps, p.jscratch, st));
+    PD_TRY(eigh_mixed<S>(na, p.d_small, this->h_small.data(), mm, G, p.lam, W, this->eig, st, p.sweeps));
     PD_TRY(this->kt.end(0.0));
     PD_TRY(gemm(1, (S*)p.Q, W, (S*)p.Xt));
     PD_TRY(band_mm((S*)p.Xt, (S*)p.BQ));
@@ -582,8 +620,8 @@ struct FeastRun : Feast<S, C> {
     PD_CK(cudaMemcpyAsync(nconv.data(), p.nconv, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaMemcpyAsync(sw.data(), p.sweeps, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
-    for (int s : active)
-      if (sw[s] < 0) return PDESHEP_EIG_NOT_CONVERGED;
+    for (int a = 0; a < na; ++a)
+      if (sw[a] < 0) return PDESHEP_EIG_NOT_CONVERGED;
     return this->kt.collect();
   }
 
@@ -876,13 +914,13 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
     }
     F.active.swap(next);
   };
-  if (F.mode == 1) {
-    PD_CK(cudaMemcpyAsync(F.p.Q, F.p.Xt, sizeof(S) * (size_t)(n * F.M), cudaMemcpyDeviceToDevice, st));
-    PD_TRY(timed(ms_rr, [&]() { return F.rr(); }));
-    update_active(0);
-  }
+  // The first iteration filters the start vectors themselves (Algorithm 1); in
+  // mixed precision with residual refinement the later ones filter the FP64
+  // residuals of the Ritz pairs.
+  const int refine = F.mode;
   int it = 1;
   for (; it <= o->max_iter && !F.active.empty(); ++it) {
+    F.mode = (refine && it > 1) ? 1 : 0;
     PD_TRY(timed(ms_filter, [&]() { return F.filter(); }));
     PD_TRY(timed(ms_rr, [&]() { return F.rr(); }));
     update_active(it);
