@@ -140,6 +140,32 @@ int pdeshep_inertia(int64_t n, int32_t b, int32_t is_complex, const void* d_band
                     void* d_work, size_t work_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Allocation-free inertia.  The paper has no counterpart: this entry point   */
+/* exists for callers that cannot hand the library any device memory -- for  */
+/* example code whose device memory is wholly owned by another allocator, or */
+/* a callback that may only run kernels on buffers it is given -- and so      */
+/* cannot supply the workspace of pdeshep_inertia.  It computes the same      */
+/* counts as pdeshep_inertia (same kernel, same arithmetic) but keeps its     */
+/* scratch (a few words plus the shifts and counts) in one fixed 20 KiB       */
+/* device array inside the library; every GPU that loads the library holds   */
+/* that array until the process exits.  It never allocates or frees device  */
+/* memory.                                                                   */
+/*  Limits: nsigma <= 1024 (else -6) and the LDL^T window must fit in shared */
+/*  memory: real b <= 141, complex b <= 105 (else -2); the reason is then in */
+/*  pdeshep_last_error().                                                    */
+/*  The first call on a device looks up the array's device address for that */
+/*  device (cudaGetSymbolAddress), so make that first call before any stream */
+/*  capture.  All calls share the one array and it keeps the last call's     */
+/*  contents (each call clears and rewrites what it uses): calls that may    */
+/*  overlap on the GPU -- concurrent streams, or host threads on the same    */
+/*  device -- race on it and must be serialised by the caller.  Synchronous: */
+/*  returns after h_neg is written.                                          */
+/* ------------------------------------------------------------------------ */
+int pdeshep_inertia_noalloc(int64_t n, int32_t b, int32_t is_complex, const void* d_band,
+                            int64_t ldab, int32_t nsigma, const double* h_sigma, int64_t* h_neg,
+                            void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Eigenvalue enclosures by bisection on inertia (slice boundaries with exact */
 /* counts; the fall-back of the slice proposer).  For each requested index   */
 /* k_t (0-based, ascending order of eigenvalues) returns h_lo[t] < h_hi[t]    */

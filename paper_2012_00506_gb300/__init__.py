@@ -36,7 +36,8 @@ STATUS = {
 EXPORTED = [
     "pdeshep_opts_default", "pdeshep_status_string", "pdeshep_last_error", "pdeshep_version",
     "pdeshep_kernel_launches",
-    "pdeshep_inertia_workspace_size", "pdeshep_inertia", "pdeshep_bisect_workspace_size",
+    "pdeshep_inertia_workspace_size", "pdeshep_inertia", "pdeshep_inertia_noalloc",
+    "pdeshep_bisect_workspace_size",
     "pdeshep_bisect", "pdeshep_gershgorin", "pdeshep_contour_rule",
     "pdeshep_shifted_solve_workspace_size", "pdeshep_shifted_solve", "pdeshep_band_matmul",
     "pdeshep_cholqr_workspace_size", "pdeshep_cholqr", "pdeshep_eigh_workspace_size",
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
         "pdeshep_kernel_launches": (C.c_uint64, []),
         "pdeshep_inertia_workspace_size": (sz, [i64, i32, i32, i32]),
         "pdeshep_inertia": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P, P, sz, P]),
+        "pdeshep_inertia_noalloc": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P]),
         "pdeshep_bisect_workspace_size": (sz, [i64, i32, i32, i32, i32]),
         "pdeshep_bisect": (C.c_int, [i64, i32, i32, P, i64, i32, P, dbl, i32, P, P, P, sz, P]),
         "pdeshep_gershgorin": (C.c_int, [i64, i32, i32, P, i64, P, P, P, sz, P]),
@@ -191,6 +193,24 @@ def inertia(band, sigmas, b=None, pivots=False, stream=None):
                              _ptr(ws), ws.numel(), _stream(stream))
     _check("pdeshep_inertia", st)
     return (neg, piv) if pivots else neg
+
+
+def inertia_noalloc(band, sigmas, b=None, stream=None):
+    """Eigenvalue counts below each sigma without any device allocation.
+
+    For callers that cannot give the library device memory: the scratch is a
+    fixed array inside the library (limits: at most 1024 shifts; real b <= 141,
+    complex b <= 105).  Calls that may overlap on the GPU share that array and
+    must be serialised by the caller.
+    """
+    lib = load()
+    n, b, cplx, ldab = _band_args(band, b)
+    sig = np.ascontiguousarray(np.atleast_1d(np.asarray(sigmas, dtype=np.float64)))
+    neg = np.zeros(sig.size, dtype=np.int64)
+    st = lib.pdeshep_inertia_noalloc(n, b, cplx, _ptr(band), ldab, sig.size, _np_ptr(sig), _np_ptr(neg),
+                                     _stream(stream))
+    _check("pdeshep_inertia_noalloc", st)
+    return neg
 
 
 def bisect(band, idx, rtol=1e-12, fanout=8, b=None, stream=None):

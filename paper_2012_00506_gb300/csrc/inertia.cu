@@ -18,6 +18,8 @@
 // and only the real part applied on the diagonal.
 #include <float.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace pdeshep {
@@ -357,9 +359,82 @@ int gershgorin_device(int64_t n, int b, int cplx, const void* band, int64_t ldab
 }
 size_t gershgorin_ws_doubles() { return 2 * kGershBlocks; }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  Its scratch (the amax word, the non-finite flag,
+// the shifts and the counts) lives in a fixed device array that every GPU
+// loading this library holds until the process exits; the LDL^T window must
+// then fit in shared memory.  Host code cannot use the array's name as a
+// device address, so the address is looked up once per device with
+// cudaGetSymbolAddress (on the first call made on that device).
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxSigma = 1024;
+constexpr size_t kNoAllocBytes = 20 * 1024;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[256] = {};
+
+static int noalloc_scratch_address(void** out) {
+  int dev = 0;
+  PD_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) {
+    set_last_error_msg("pdeshep_inertia_noalloc: device ordinal out of range");
+    return PDESHEP_CUDA_ERROR;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    PD_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return 0;
+}
+
 }  // namespace pdeshep
 
 using namespace pdeshep;
+
+extern "C" int pdeshep_inertia_noalloc(int64_t n, int32_t b, int32_t is_complex, const void* d_band,
+                                       int64_t ldab, int32_t nsigma, const double* h_sigma,
+                                       int64_t* h_neg, void* stream) {
+  if (n < 0) return -1;
+  const int cplx = is_complex ? 1 : 0;
+  if (b < 0 || !window_in_smem(b, cplx)) {
+    set_last_error_msg("pdeshep_inertia_noalloc: band too wide for the shared-memory window "
+                       "(real b <= 141, complex b <= 105)");
+    return -2;
+  }
+  if (!d_band && n > 0) return -4;
+  if (ldab < b + 1) return -5;
+  if (nsigma < 0 || nsigma > kNoAllocMaxSigma) {
+    set_last_error_msg("pdeshep_inertia_noalloc: nsigma must be in [0, 1024]");
+    return -6;
+  }
+  if (!h_sigma && nsigma > 0) return -7;
+  if (!h_neg && nsigma > 0) return -8;
+  if (n == 0 || nsigma == 0) {
+    for (int s = 0; s < nsigma; ++s) h_neg[s] = 0;
+    return 0;
+  }
+  void* base = nullptr;
+  PD_TRY(noalloc_scratch_address(&base));
+  char* p = (char*)base;
+  unsigned long long* amax = (unsigned long long*)p;
+  int* nonfinite = (int*)(p + 64);
+  double* sigma = (double*)(p + 256);
+  int64_t* neg = (int64_t*)(p + 256 + sizeof(double) * kNoAllocMaxSigma);
+  cudaStream_t st = (cudaStream_t)stream;
+  // amax and the flag are cleared here; sigma and neg are overwritten by this call
+  PD_TRY(launch_band_amax(n, b, cplx, d_band, ldab, amax, nonfinite, st));
+  PD_CK(cudaMemcpyAsync(sigma, h_sigma, sizeof(double) * nsigma, cudaMemcpyHostToDevice, st));
+  PD_TRY(launch_inertia(n, b, cplx, d_band, ldab, nsigma, sigma, amax, neg, nullptr, nullptr, 0, st));
+  int bad = 0;
+  PD_CK(cudaMemcpyAsync(h_neg, neg, sizeof(int64_t) * nsigma, cudaMemcpyDeviceToHost, st));
+  PD_CK(cudaMemcpyAsync(&bad, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PD_CK(cudaStreamSynchronize(st));
+  return bad ? PDESHEP_NONFINITE_INPUT : 0;
+}
 
 extern "C" size_t pdeshep_inertia_workspace_size(int64_t n, int32_t b, int32_t is_complex,
                                                  int32_t nsigma) {
