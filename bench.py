@@ -230,13 +230,15 @@ def run_gpu(args):
     kg_ms = {g: 0.0 for g in pk.KERNEL_GROUPS}
     kg_fl = {g: 0.0 for g in pk.KERNEL_GROUPS}
     kg_n = {g: 0 for g in pk.KERNEL_GROUPS}
-    iters, statuses = [], []
+    iters, statuses, sweeps = [], [], []
     for k in range(W, W + K):
         inputs.append((k, x0, bounds))
         r = seq.step(k, x0, bounds, pk.MIXED)
         statuses.append(r.status)
         pairs += good_pairs(r, seq.m0)
         iters.append(r.stats["iterations"])
+        cluster_ctas = r.stats["cluster_ctas"]
+        sweeps.append((r.stats["rr_calls"], r.stats["jacobi_sweeps32"], r.stats["jacobi_sweeps64"]))
         for g in pk.KERNEL_GROUPS:
             kg_ms[g] += r.stats["kg_ms"][g]
             kg_fl[g] += r.stats["kg_flops"][g]
@@ -282,7 +284,8 @@ def run_gpu(args):
                       "m0": seq.m0.tolist(), "tol": TOL, "ellipse_ratio": RHO,
                       "l2": "inputs larger than L2 (factor set ~1.2 GB per step)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
-           "iterations_per_step": iters, "status_per_step": statuses,
+           "iterations_per_step": iters, "status_per_step": statuses, "cluster_ctas": cluster_ctas,
+           "rr_calls_sweeps32_sweeps64": sweeps,
            "kernel_groups": groups, "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
 
     if rank == 0 and not args.no_plain and args.plain_steps > 0:

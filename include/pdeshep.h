@@ -105,6 +105,10 @@ typedef struct {
   int64_t kg_launches[PDESHEP_KG_COUNT];
   double kg_flops[PDESHEP_KG_COUNT];
   int64_t rhs_columns;     /* sum over solve sweeps of the right-hand sides swept */
+  int32_t cluster_ctas;    /* thread blocks per slice in the small dense kernels */
+  int32_t jacobi_sweeps64; /* FP64 Jacobi sweeps, summed over Rayleigh-Ritz calls (max over slices) */
+  int32_t jacobi_sweeps32; /* FP32 Jacobi sweeps, same accounting */
+  int32_t rr_calls;        /* Rayleigh-Ritz calls */
 } pdeshep_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -68,7 +68,8 @@ class Stats(C.Structure):
         ("ms_solve", C.c_double), ("ms_rr", C.c_double), ("ms_total", C.c_double),
         ("max_residual", C.c_double), ("min_rel_error_est", C.c_double),
         ("kg_ms", C.c_double * 7), ("kg_launches", C.c_int64 * 7), ("kg_flops", C.c_double * 7),
-        ("rhs_columns", C.c_int64),
+        ("rhs_columns", C.c_int64), ("cluster_ctas", C.c_int32), ("jacobi_sweeps64", C.c_int32),
+        ("jacobi_sweeps32", C.c_int32), ("rr_calls", C.c_int32),
     ]
 
     def as_dict(self):

@@ -8,6 +8,8 @@
 // slice with the matrix in L2 and cluster barriers between phases.
 #include <cooperative_groups.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -147,7 +149,18 @@ int launch_gemm(bool conjA, int nitems, const GemmItem<S>* d_items, int max_m, i
 // cluster helpers
 // ---------------------------------------------------------------------------
 constexpr int kSmallThreads = 256;
-static int g_cluster_ctas = 16;  // CTAs per slice; falls back to the portable 8 if 16 cannot launch
+// Cluster shape of the per-slice kernels: 16 CTAs (non-portable) with one CTA
+// per SM (forced by a large dynamic shared-memory request, since these kernels
+// are FP64-pipe bound and two CTAs on one SM would share it); falls back to
+// 8 CTAs, then to 8 CTAs without the SM-spreading request.
+struct ClusterShape {
+  int ctas;
+  size_t spread_smem;
+};
+static const ClusterShape kShapes[] = {{16, 120 * 1024}, {8, 120 * 1024}, {8, 0}};
+static int g_shape = 0;
+
+int cluster_ctas_used() { return kShapes[g_shape].ctas; }
 
 __device__ __forceinline__ int cl_rank() { return (int)cg::this_cluster().block_rank(); }
 __device__ __forceinline__ int cl_size() { return (int)cg::this_cluster().num_blocks(); }
@@ -155,34 +168,36 @@ __device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
 __device__ __forceinline__ int cl_slice() { return blockIdx.x / cl_size(); }
 
 template <typename K, typename... Args>
-static int launch_cluster(K kernel, int nblk, size_t smem, cudaStream_t st, Args... args) {
+static int launch_cluster_t(K kernel, int nblk, size_t smem, int threads, cudaStream_t st, Args... args) {
   for (;;) {
-    const int G = g_cluster_ctas;
-    if (G > 8) PD_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    const ClusterShape sh = kShapes[g_shape];
+    const size_t dyn = std::max(smem, sh.spread_smem);
+    const bool last = g_shape == (int)(sizeof(kShapes) / sizeof(kShapes[0])) - 1;
+    cudaError_t e = cudaSuccess;
+    if (sh.ctas > 8) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess && dyn > 48 * 1024)
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(nblk * G));
-    cfg.blockDim = dim3(kSmallThreads);
-    cfg.dynamicSmemBytes = smem;
+    cfg.gridDim = dim3((unsigned)(nblk * sh.ctas));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = dyn;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = G;
+    attr[0].val.clusterDim.x = sh.ctas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (G > 8) {
+    if (e == cudaSuccess && !last) {
       int nclusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg) != cudaSuccess || nclusters < 1) {
-        cudaGetLastError();
-        g_cluster_ctas = 8;
-        continue;
-      }
+      e = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg);
+      if (e == cudaSuccess && nclusters < 1) e = cudaErrorInvalidConfiguration;
     }
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
-    if (e != cudaSuccess && G > 8) {
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, kernel, args...);
+    if (e != cudaSuccess && !last) {
       cudaGetLastError();
-      g_cluster_ctas = 8;
+      ++g_shape;
       continue;
     }
     PD_CK(e);
@@ -191,11 +206,17 @@ static int launch_cluster(K kernel, int nblk, size_t smem, cudaStream_t st, Args
   }
 }
 
+template <typename K, typename... Args>
+static int launch_cluster(K kernel, int nblk, size_t smem, cudaStream_t st, Args... args) {
+  return launch_cluster_t(kernel, nblk, smem, kSmallThreads, st, args...);
+}
+
 // ---------------------------------------------------------------------------
 // Cholesky G = R^H R, upper, in place; one cluster per block
 // ---------------------------------------------------------------------------
 template <typename S>
-__global__ void cholesky_kernel(const SmallDesc* desc, S* Gall, int* info, double* diag0, double* minratio) {
+__global__ void __launch_bounds__(1024) cholesky_kernel(const SmallDesc* desc, S* Gall, int* info, double* diag0,
+                                                        double* minratio) {
   const int t = cl_slice();
   const SmallDesc d = desc[t];
   const int m = d.m;
@@ -261,38 +282,76 @@ template <typename S>
 int launch_cholesky(int nblk, const SmallDesc* d_desc, S* G, int* info, cudaStream_t st, double* diag0,
                     double* minratio) {
   if (nblk <= 0) return 0;
-  return launch_cluster(cholesky_kernel<S>, nblk, 0, st, d_desc, G, info, diag0, minratio);
+  return launch_cluster_t(cholesky_kernel<S>, nblk, 0, 1024, st, d_desc, G, info, diag0, minratio);
 }
 
 // ---------------------------------------------------------------------------
-// upper triangular inverse, column per thread
+// upper triangular inverse X = R^{-1}, blocked in 32 x 32 tiles: invert the
+// diagonal tiles (one thread per column), then for tile distance d = 1, 2, ...
+// T_ij = sum_{k=i+1..j} R_ik X_kj (kept transposed in the still-unused lower
+// tile (j,i), so every index stays inside the m x m block even when the last
+// tile is partial) and X_ij = -X_ii T_ij; two cluster barriers per distance.
 // ---------------------------------------------------------------------------
 template <typename S>
-__global__ void triinv_kernel(const SmallDesc* desc, const S* Rall, S* Iall) {
+__global__ void __launch_bounds__(1024) triinv_kernel(const SmallDesc* desc, const S* Rall, S* Xall) {
   const int t = cl_slice();
-  const SmallDesc d = desc[t];
-  const int m = d.m;
-  const S* R = Rall + d.off;
-  S* X = Iall + d.off;
+  const SmallDesc dsc = desc[t];
+  const int m = dsc.m;
+  const S* R = Rall + dsc.off;
+  S* X = Xall + dsc.off;
   const int gid = cl_rank() * blockDim.x + threadIdx.x, gsz = cl_size() * blockDim.x;
-  for (int j = gid; j < m; j += gsz) {
-    S* x = X + (int64_t)j * m;
-    for (int i = j + 1; i < m; ++i) x[i] = sc<S>::zero();
-    const double rjj = sc<S>::re(R[j + (int64_t)j * m]);
-    x[j] = sc<S>::from_re(1.0 / rjj);
-    for (int i = j - 1; i >= 0; --i) {
-      S s = sc<S>::zero();
-      for (int k = i + 1; k <= j; ++k) sc<S>::fma_(s, R[i + (int64_t)k * m], x[k]);
-      const double rii = sc<S>::re(R[i + (int64_t)i * m]);
-      x[i] = sc<S>::scale(s, -1.0 / rii);
+  const int nb = (m + 31) / 32;
+  for (int64_t e = gid; e < (int64_t)m * m; e += gsz) X[e] = sc<S>::zero();
+  cl_sync();
+  for (int it = gid; it < nb * 32; it += gsz) {
+    const int i = it / 32, c = it % 32;
+    const int j = 32 * i + c;
+    if (j >= m) continue;
+    X[j + (int64_t)j * m] = sc<S>::from_re(1.0 / sc<S>::re(R[j + (int64_t)j * m]));
+    for (int r = c - 1; r >= 0; --r) {
+      const int row = 32 * i + r;
+      S acc = sc<S>::zero();
+      for (int k = r + 1; k <= c; ++k) sc<S>::fma_(acc, R[row + (int64_t)(32 * i + k) * m], X[32 * i + k + (int64_t)j * m]);
+      X[row + (int64_t)j * m] = sc<S>::scale(acc, -1.0 / sc<S>::re(R[row + (int64_t)row * m]));
     }
+  }
+  cl_sync();
+  for (int d = 1; d < nb; ++d) {
+    const int nblkd = nb - d;
+    for (int it = gid; it < nblkd * 1024; it += gsz) {
+      const int i = it / 1024, r = (it % 1024) % 32, c = (it % 1024) / 32;
+      const int j = i + d;
+      const int row = 32 * i + r, col = 32 * j + c;
+      if (row >= m || col >= m) continue;
+      S acc = sc<S>::zero();
+      const int qend = min(32 * (j + 1), m);
+      for (int q = 32 * (i + 1); q < qend; ++q) sc<S>::fma_(acc, R[row + (int64_t)q * m], X[q + (int64_t)col * m]);
+      X[(32 * j + c) + (int64_t)(32 * i + r) * m] = acc;  // T_ij(r,c), transposed into the lower tile (j,i)
+    }
+    cl_sync();
+    for (int it = gid; it < nblkd * 1024; it += gsz) {
+      const int i = it / 1024, r = (it % 1024) % 32, c = (it % 1024) / 32;
+      const int j = i + d;
+      const int row = 32 * i + r, col = 32 * j + c;
+      if (row >= m || col >= m) continue;
+      S acc = sc<S>::zero();
+      const int send = min(32, m - 32 * i);
+      for (int q = r; q < send; ++q)
+        sc<S>::fma_(acc, X[row + (int64_t)(32 * i + q) * m], X[(32 * j + c) + (int64_t)(32 * i + q) * m]);
+      X[row + (int64_t)col * m] = sc<S>::scale(acc, -1.0);
+    }
+    cl_sync();
+  }
+  for (int64_t e = gid; e < (int64_t)m * m; e += gsz) {
+    const int row = (int)(e % m), col = (int)(e / m);
+    if (row / 32 > col / 32) X[e] = sc<S>::zero();
   }
 }
 
 template <typename S>
 int launch_triinv(int nblk, const SmallDesc* d_desc, const S* R, S* Rinv, cudaStream_t st) {
   if (nblk <= 0) return 0;
-  return launch_cluster(triinv_kernel<S>, nblk, 0, st, d_desc, R, Rinv);
+  return launch_cluster_t(triinv_kernel<S>, nblk, 0, 1024, st, d_desc, R, Rinv);
 }
 
 // ---------------------------------------------------------------------------
@@ -336,12 +395,12 @@ __device__ __forceinline__ void make_rot(const S* A, int m, int p, int q, Rot<S>
 }
 
 template <typename S>
-__global__ void jacobi_kernel(const SmallDesc* desc, S* Aall, S* Vall, S* Vout, double* lamall,
+__global__ void __launch_bounds__(512) jacobi_kernel(const SmallDesc* desc, S* Aall, S* Vall, S* Vout, double* lamall,
                               double tol, int max_sweeps, int* sweeps_out, double* scratch) {
   using R = typename real_t<S>::type;
   extern __shared__ __align__(16) char smem[];
   Rot<S>* rot = (Rot<S>*)smem;
-  __shared__ double red[2][kSmallThreads / 32];
+  __shared__ double red[2][32];
   const int t = cl_slice();
   const SmallDesc d = desc[t];
   const int m = d.m;
@@ -412,42 +471,77 @@ __global__ void jacobi_kernel(const SmallDesc* desc, S* Aall, S* Vall, S* Vout, 
       }
       // every CTA must have read the pivots of this round before any column changes
       cl_sync();
-      // columns of A and V: A <- A J, V <- V J
-      for (int64_t e = gid; e < (int64_t)np * m; e += gsz) {
-        const int i = (int)(e / m), k = (int)(e % m);
-        const Rot<S> ro = rot[i];
-        if (ro.p < 0) continue;
-        const S uc = sc<S>::scale(ro.u, ro.c), us = sc<S>::scale(ro.u, ro.s);
-        S* ap = A + (int64_t)ro.p * m;
-        S* aq = A + (int64_t)ro.q * m;
-        S akp = ap[k], akq = aq[k];
-        ap[k] = sc<S>::sub(sc<S>::mul(akp, uc), sc<S>::scale(akq, ro.s));
-        aq[k] = sc<S>::add(sc<S>::mul(akp, us), sc<S>::scale(akq, ro.c));
-        S* vp = V + (int64_t)ro.p * m;
-        S* vq = V + (int64_t)ro.q * m;
-        S vkp = vp[k], vkq = vq[k];
-        vp[k] = sc<S>::sub(sc<S>::mul(vkp, uc), sc<S>::scale(vkq, ro.s));
-        vq[k] = sc<S>::add(sc<S>::mul(vkp, us), sc<S>::scale(vkq, ro.c));
+      // columns of A and V: A <- A J, V <- V J (four independent updates in flight per thread)
+      constexpr int U = 4;
+      const int64_t tc = (int64_t)np * m;
+      for (int64_t e0 = gid; e0 < tc; e0 += (int64_t)gsz * U) {
+        S akp[U], akq[U], vkp[U], vkq[U];
+        int ip[U], iq[U], kk[U], ri[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t e = e0 + (int64_t)u * gsz;
+          ri[u] = -1;
+          if (e < tc) {
+            const int i = (int)(e / m);
+            if (rot[i].p >= 0) {
+              ri[u] = i;
+              ip[u] = rot[i].p;
+              iq[u] = rot[i].q;
+              kk[u] = (int)(e % m);
+              akp[u] = A[kk[u] + (int64_t)ip[u] * m];
+              akq[u] = A[kk[u] + (int64_t)iq[u] * m];
+              vkp[u] = V[kk[u] + (int64_t)ip[u] * m];
+              vkq[u] = V[kk[u] + (int64_t)iq[u] * m];
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (ri[u] < 0) continue;
+          const Rot<S> ro = rot[ri[u]];
+          const S uc = sc<S>::scale(ro.u, ro.c), us = sc<S>::scale(ro.u, ro.s);
+          A[kk[u] + (int64_t)ip[u] * m] = sc<S>::sub(sc<S>::mul(akp[u], uc), sc<S>::scale(akq[u], ro.s));
+          A[kk[u] + (int64_t)iq[u] * m] = sc<S>::add(sc<S>::mul(akp[u], us), sc<S>::scale(akq[u], ro.c));
+          V[kk[u] + (int64_t)ip[u] * m] = sc<S>::sub(sc<S>::mul(vkp[u], uc), sc<S>::scale(vkq[u], ro.s));
+          V[kk[u] + (int64_t)iq[u] * m] = sc<S>::add(sc<S>::mul(vkp[u], us), sc<S>::scale(vkq[u], ro.c));
+        }
       }
       cl_sync();
       // rows of A: A <- J^H A
-      for (int64_t e = gid; e < (int64_t)np * m; e += gsz) {
-        const int i = (int)(e % np), k = (int)(e / np);
-        const Rot<S> ro = rot[i];
-        if (ro.p < 0) continue;
-        const S ucc = sc<S>::conj(sc<S>::scale(ro.u, ro.c)), usc = sc<S>::conj(sc<S>::scale(ro.u, ro.s));
-        S* col = A + (int64_t)k * m;
-        const S apk = col[ro.p], aqk = col[ro.q];
-        S np_ = sc<S>::sub(sc<S>::mul(ucc, apk), sc<S>::scale(aqk, ro.s));
-        S nq_ = sc<S>::add(sc<S>::mul(usc, apk), sc<S>::scale(aqk, ro.c));
-        if (k == ro.q) np_ = sc<S>::zero();
-        if (k == ro.p) {
-          nq_ = sc<S>::zero();
-          np_ = sc<S>::from_re(sc<S>::re(np_));
+      for (int64_t e0 = gid; e0 < tc; e0 += (int64_t)gsz * U) {
+        S apk[U], aqk[U];
+        int ri[U], kk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t e = e0 + (int64_t)u * gsz;
+          ri[u] = -1;
+          if (e < tc) {
+            const int i = (int)(e % np);
+            if (rot[i].p >= 0) {
+              ri[u] = i;
+              kk[u] = (int)(e / np);
+              apk[u] = A[rot[i].p + (int64_t)kk[u] * m];
+              aqk[u] = A[rot[i].q + (int64_t)kk[u] * m];
+            }
+          }
         }
-        if (k == ro.q) nq_ = sc<S>::from_re(sc<S>::re(nq_));
-        col[ro.p] = np_;
-        col[ro.q] = nq_;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (ri[u] < 0) continue;
+          const Rot<S> ro = rot[ri[u]];
+          const int k = kk[u];
+          const S ucc = sc<S>::conj(sc<S>::scale(ro.u, ro.c)), usc = sc<S>::conj(sc<S>::scale(ro.u, ro.s));
+          S np_ = sc<S>::sub(sc<S>::mul(ucc, apk[u]), sc<S>::scale(aqk[u], ro.s));
+          S nq_ = sc<S>::add(sc<S>::mul(usc, apk[u]), sc<S>::scale(aqk[u], ro.c));
+          if (k == ro.q) np_ = sc<S>::zero();
+          if (k == ro.p) {
+            nq_ = sc<S>::zero();
+            np_ = sc<S>::from_re(sc<S>::re(np_));
+          }
+          if (k == ro.q) nq_ = sc<S>::from_re(sc<S>::re(nq_));
+          A[ro.p + (int64_t)k * m] = np_;
+          A[ro.q + (int64_t)k * m] = nq_;
+        }
       }
       cl_sync();
     }
@@ -489,8 +583,8 @@ int launch_jacobi(int nblk, const SmallDesc* d_desc, int max_m, S* A, S* Vwork, 
   if (nblk <= 0) return 0;
   const size_t smem = sizeof(Rot<S>) * (size_t)((max_m + 2) / 2);
   if (smem > 48 * 1024) PD_CK(cudaFuncSetAttribute(jacobi_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  return launch_cluster(jacobi_kernel<S>, nblk, smem, st, d_desc, A, Vwork, Vout, lam, tol, max_sweeps,
-                        sweeps_out, scratch);
+  return launch_cluster_t(jacobi_kernel<S>, nblk, smem, 512, st, d_desc, A, Vwork, Vout, lam, tol, max_sweeps,
+                          sweeps_out, scratch);
 }
 
 // ---------------------------------------------------------------------------
@@ -564,6 +658,41 @@ __global__ void small_cast_kernel(const SmallDesc* desc, const A* __restrict__ s
   }
 }
 
+// A <- A - mu I with mu = mean of Re diag(A), per block; mu saved in shift[t]
+template <typename S>
+__global__ void shift_kernel(const SmallDesc* desc, S* Aall, double* shift) {
+  const SmallDesc d = desc[blockIdx.x];
+  S* A = Aall + d.off;
+  __shared__ double red[32];
+  __shared__ double mu;
+  double sum = 0.0;
+  for (int i = threadIdx.x; i < d.m; i += blockDim.x) sum += sc<S>::re(A[i + (int64_t)i * d.m]);
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    mu = d.m > 0 ? t / d.m : 0.0;
+    shift[blockIdx.x] = mu;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < d.m; i += blockDim.x) {
+    S* a = A + i + (int64_t)i * d.m;
+    *a = sc<S>::from_re(sc<S>::re(*a) - mu);
+  }
+}
+
+__global__ void unshift_kernel(const SmallDesc* desc, double* lam, const double* shift) {
+  const SmallDesc d = desc[blockIdx.x];
+  for (int i = threadIdx.x; i < d.m; i += blockDim.x) lam[d.voff + i] += shift[blockIdx.x];
+}
+
+template <typename S>
+__global__ void identity_kernel(S* V, int m) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) V[i + (int64_t)i * m] = sc<S>::from_re(1.0);
+}
+
 // first largest-magnitude component of each column real and positive
 template <typename S>
 __global__ void phase_kernel(const SmallDesc* desc, S* Wall) {
@@ -612,20 +741,26 @@ EighScratch<S> plan_eigh_scratch(Arena& a, int64_t msq, int64_t mtot, int nblk) 
   w.sweeps = a.take<int>(nblk);
   w.jscratch = a.take<double>((size_t)nblk * 2 * 16);
   w.items = a.take<GemmItem<S>>(nblk);
+  w.dsub = a.take<SmallDesc>(2 * (size_t)nblk);
+  w.delta = a.take<double>(nblk);
+  w.shift = a.take<double>(nblk);
+  w.A64 = a.take<S>(msq);
   return w;
 }
 
 template <typename S>
-int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int max_m, S* A, double* lam, S* W,
-               const EighScratch<S>& w, cudaStream_t st, int* fp64_sweeps_out) {
-  using L = typename lowp<S>::type;
-  if (nblk <= 0) return 0;
-  const dim3 g((unsigned)std::min<int64_t>(ceil_div((int64_t)max_m * max_m, 256), 512), (unsigned)nblk);
-  small_cast_kernel<S, L><<<g, 256, 0, st>>>(d_desc, A, w.A32);
-  PD_CK_LAUNCH();
-  PD_TRY(launch_jacobi<L>(nblk, d_desc, max_m, w.A32, w.V32w, w.V32, w.lam32, 2e-6, 20, w.sweeps, w.jscratch, st));
-  small_cast_kernel<L, S><<<g, 256, 0, st>>>(d_desc, w.V32, w.Vd);
-  PD_CK_LAUNCH();
+int small_gemm(bool conjA, const std::vector<SmallDesc>& blk, int max_m, S* const* abc, int herm, int triB,
+               GemmItem<S>* d_items, cudaStream_t st) {
+  // abc = {A base, B base, C base}; every block is m x m at the block's offset
+  const int nb = (int)blk.size();
+  if (!nb) return 0;
+  std::vector<GemmItem<S>> it(nb);
+  for (int t = 0; t < nb; ++t) {
+    const int m = blk[t].m;
+    const int64_t o = blk[t].off;
+    it[t] = GemmItem<S>{abc[0] + o, abc[1] + o, abc[2] + o, m, m, m, m, m, m, 0};
+  }
+  PD_CK(cudaMemcpyAsync(d_items, it.data(), sizeof(GemmItem<S>) * nb, cudaMemcpyHostToDevice, st));
   S one, zero;
   if constexpr (std::is_same<S, double>::value) {
     one = 1.0;
@@ -634,66 +769,316 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
     one = make_double2(1.0, 0.0);
     zero = make_double2(0.0, 0.0);
   }
-  std::vector<GemmItem<S>> it(nblk);
-  // V32 is unitary only to FP32 accuracy: orthonormalise it in FP64 (one CholQR
-  // pass, its Gram matrix is I + O(1e-7)) so that V^H A V is a similarity.
-  for (int t = 0; t < nblk; ++t) {
-    const int m = h_desc[t].m;
-    const int64_t o = h_desc[t].off;
-    it[t] = GemmItem<S>{w.Vd + o, w.Vd + o, w.T + o, m, m, m, m, m, m, 0};
+  return launch_gemm<S>(conjA, nb, d_items, max_m, max_m, max_m, one, zero, 1, nullptr, 0, st, herm, triB);
+}
+
+// One refinement step of an approximate eigenvector matrix V of a Hermitian A
+// (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue
+// decomposition", 2018), given S = V^H A V and P = V^H V:
+//   R = I - P,  lambda_i = Re S_ii / (1 - Re R_ii),
+//   delta = 2 (||S - diag(lambda)||_F + max|lambda| ||R||_F),
+//   E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)  if |lambda_i - lambda_j| > delta,
+//   E_ij = R_ij / 2 otherwise (and on the diagonal);  V <- V + V E.
+// One thread block per slice; E overwrites S.  delta_out[t] = delta / max|lambda|.
+template <typename S>
+__global__ void __launch_bounds__(1024) oa_kernel(const SmallDesc* desc, S* Sall, const S* Pall, double* lamall,
+                                                  double* delta_out) {
+  const SmallDesc d = desc[blockIdx.x];
+  const int m = d.m;
+  S* Sm = Sall + d.off;
+  const S* P = Pall + d.off;
+  double* lam = lamall + d.voff;
+  __shared__ double red[3][32];
+  __shared__ double sh_delta;
+  double smax = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double l = sc<S>::re(Sm[i + (int64_t)i * m]) / sc<S>::re(P[i + (int64_t)i * m]);
+    lam[i] = l;
+    smax = fmax(smax, fabs(l));
   }
-  PD_CK(cudaMemcpyAsync(w.items, it.data(), sizeof(GemmItem<S>) * nblk, cudaMemcpyHostToDevice, st));
-  PD_TRY(launch_gemm<S>(true, nblk, w.items, max_m, max_m, max_m, one, zero, 1, nullptr, 0, st, 1, 0));
-  PD_TRY(launch_cholesky<S>(nblk, d_desc, w.T, w.sweeps, st));
-  PD_TRY(launch_triinv<S>(nblk, d_desc, w.T, w.Vw, st));
-  for (int t = 0; t < nblk; ++t) {
-    const int m = h_desc[t].m;
-    const int64_t o = h_desc[t].off;
-    it[t] = GemmItem<S>{w.Vd + o, w.Vw + o, w.W64 + o, m, m, m, m, m, m, 0};
+  __syncthreads();
+  double off = 0.0, rn = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    S r = sc<S>::scale(P[e], -1.0);
+    if (i == j) r = sc<S>::add(r, sc<S>::from_re(1.0));
+    rn += sc<S>::abs2(r);
+    S sd = Sm[e];
+    if (i == j) sd = sc<S>::sub(sd, sc<S>::from_re(lam[i]));
+    off += sc<S>::abs2(sd);
   }
-  PD_CK(cudaMemcpyAsync(w.items, it.data(), sizeof(GemmItem<S>) * nblk, cudaMemcpyHostToDevice, st));
-  PD_TRY(launch_gemm<S>(false, nblk, w.items, max_m, max_m, max_m, one, zero, 1, nullptr, 0, st, 0, 1));
-  PD_CK(cudaMemcpyAsync(w.Vd, w.W64, sizeof(S) * (size_t)(h_desc[nblk - 1].off + (int64_t)h_desc[nblk - 1].m *
-                                                                                       h_desc[nblk - 1].m),
-                        cudaMemcpyDeviceToDevice, st));
-  // T = A Vd
-  for (int t = 0; t < nblk; ++t) {
-    const int m = h_desc[t].m;
-    const int64_t o = h_desc[t].off;
-    it[t] = GemmItem<S>{A + o, w.Vd + o, w.T + o, m, m, m, m, m, m, 0};
+  for (int o = 16; o > 0; o >>= 1) {
+    off += __shfl_down_sync(0xffffffffu, off, o);
+    rn += __shfl_down_sync(0xffffffffu, rn, o);
+    smax = fmax(smax, __shfl_down_sync(0xffffffffu, smax, o));
   }
-  PD_CK(cudaMemcpyAsync(w.items, it.data(), sizeof(GemmItem<S>) * nblk, cudaMemcpyHostToDevice, st));
-  PD_TRY(launch_gemm<S>(false, nblk, w.items, max_m, max_m, max_m, one, zero, 1, nullptr, 0, st, 0, 0));
-  // H = Vd^H T (into A)
-  for (int t = 0; t < nblk; ++t) {
-    const int m = h_desc[t].m;
-    const int64_t o = h_desc[t].off;
-    it[t] = GemmItem<S>{w.Vd + o, w.T + o, A + o, m, m, m, m, m, m, 0};
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = off;
+    red[1][threadIdx.x >> 5] = rn;
+    red[2][threadIdx.x >> 5] = smax;
   }
-  PD_CK(cudaMemcpyAsync(w.items, it.data(), sizeof(GemmItem<S>) * nblk, cudaMemcpyHostToDevice, st));
-  PD_TRY(launch_gemm<S>(true, nblk, w.items, max_m, max_m, max_m, one, zero, 1, nullptr, 0, st, 1, 0));
-  PD_TRY(launch_jacobi<S>(nblk, d_desc, max_m, A, w.Vw, w.W64, lam, 1e-14, 60, w.sweeps, w.jscratch, st));
-  if (fp64_sweeps_out) PD_CK(cudaMemcpyAsync(fp64_sweeps_out, w.sweeps, sizeof(int) * nblk, cudaMemcpyDeviceToDevice, st));
-  // W = Vd W64
-  for (int t = 0; t < nblk; ++t) {
-    const int m = h_desc[t].m;
-    const int64_t o = h_desc[t].off;
-    it[t] = GemmItem<S>{w.Vd + o, w.W64 + o, W + o, m, m, m, m, m, m, 0};
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+      c = fmax(c, red[2][w]);
+    }
+    sh_delta = 2.0 * (sqrt(a) + c * sqrt(b));
+    delta_out[blockIdx.x] = c > 0.0 ? sh_delta / c : 0.0;
   }
-  PD_CK(cudaMemcpyAsync(w.items, it.data(), sizeof(GemmItem<S>) * nblk, cudaMemcpyHostToDevice, st));
-  PD_TRY(launch_gemm<S>(false, nblk, w.items, max_m, max_m, max_m, one, zero, 1, nullptr, 0, st, 0, 0));
-  phase_kernel<S><<<dim3((unsigned)ceil_div(max_m, 8), nblk), 256, 0, st>>>(d_desc, W);
+  __syncthreads();
+  const double delta = sh_delta;
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    S r = sc<S>::scale(P[e], -1.0);
+    if (i == j) r = sc<S>::add(r, sc<S>::from_re(1.0));
+    S ev;
+    const double gap = lam[j] - lam[i];
+    if (i != j && fabs(gap) > delta)
+      ev = sc<S>::scale(sc<S>::add(Sm[e], sc<S>::scale(r, lam[j])), 1.0 / gap);
+    else
+      ev = sc<S>::scale(r, 0.5);
+    Sm[e] = ev;
+  }
+}
+
+// W[:, rank(i)] = V[:, i] * phase, eigenvalues sorted ascending (rank sort, ties by index).
+template <typename S>
+__global__ void __launch_bounds__(1024) sort_phase_kernel(const SmallDesc* desc, const S* Vall, const double* lam_in,
+                                                          double* lam_out, S* Wall) {
+  const SmallDesc d = desc[blockIdx.x];
+  const int m = d.m;
+  const S* V = Vall + d.off;
+  S* Wm = Wall + d.off;
+  const double* li = lam_in + d.voff;
+  double* lo = lam_out + d.voff;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < m; i += nw) {
+    int rank = 0;
+    for (int j = lane; j < m; j += 32) rank += (li[j] < li[i]) || (li[j] == li[i] && j < i);
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_down_sync(0xffffffffu, rank, o);
+    rank = __shfl_sync(0xffffffffu, rank, 0);
+    const S* v = V + (int64_t)i * m;
+    double best = -1.0;
+    int kb = m;
+    for (int k = lane; k < m; k += 32) {
+      const double a = sc<S>::abs2(v[k]);
+      if (a > best) {
+        best = a;
+        kb = k;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int ok = __shfl_down_sync(0xffffffffu, kb, o);
+      if (ob > best || (ob == best && ok < kb)) {
+        best = ob;
+        kb = ok;
+      }
+    }
+    best = __shfl_sync(0xffffffffu, best, 0);
+    kb = __shfl_sync(0xffffffffu, kb, 0);
+    const double nb = sqrt(best);
+    S ph = sc<S>::from_re(1.0);
+    if (nb > 0.0) ph = sc<S>::scale(sc<S>::conj(v[kb]), 1.0 / nb);
+    S* w = Wm + (int64_t)rank * m;
+    for (int k = lane; k < m; k += 32) w[k] = (k == kb) ? sc<S>::from_re(nb) : sc<S>::mul(v[k], ph);
+    if (lane == 0) lo[rank] = li[i];
+  }
+}
+
+// blocks whose refined eigenvalues still contain a pair closer than delta (an
+// unresolved cluster) with delta above 1e-12 max|lambda|
+template <typename S>
+__global__ void cluster_check_kernel(const SmallDesc* desc, const double* lam, const double* delta_rel, int* flag) {
+  const SmallDesc d = desc[blockIdx.x];
+  const double* l = lam + d.voff;  // sorted
+  double lmax = 0.0;
+  for (int i = 0; i < d.m; ++i) lmax = fmax(lmax, fabs(l[i]));
+  const double del = delta_rel[blockIdx.x] * lmax;
+  int bad = 0;
+  if (delta_rel[blockIdx.x] > 1e-12)
+    for (int i = threadIdx.x; i + 1 < d.m; i += blockDim.x) bad |= (l[i + 1] - l[i]) <= del;
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) flag[blockIdx.x] = bad;
+}
+
+template <typename S>
+int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int max_m, S* A, double* lam, S* W,
+               const EighScratch<S>& w, cudaStream_t st, int* fp64_sweeps_out, const unsigned char* h_fp32,
+               int* fp32_sweeps_out) {
+  using L = typename lowp<S>::type;
+  if (nblk <= 0) return 0;
+  std::vector<SmallDesc> all(h_desc, h_desc + nblk), sub, rest;
+  for (int t = 0; t < nblk; ++t) (h_fp32 == nullptr || h_fp32[t] ? sub : rest).push_back(h_desc[t]);
+  const int ns = (int)sub.size();
+  S one, zero;
+  if constexpr (std::is_same<S, double>::value) {
+    one = 1.0;
+    zero = 0.0;
+  } else {
+    one = make_double2(1.0, 0.0);
+    zero = make_double2(0.0, 0.0);
+  }
+  const dim3 gcast((unsigned)std::min<int64_t>(ceil_div((int64_t)max_m * max_m, 256), 512), (unsigned)nblk);
+  // Shift every block by the mean of its diagonal: the projected matrices of a slice
+  // have eigenvalues clustered around an offset much larger than their spread, and
+  // the FP32 stage, the refinement's cluster threshold and the Jacobi stopping test
+  // must resolve the spread, not the offset.  The shift is added back at the end.
+  shift_kernel<S><<<nblk, 256, 0, st>>>(d_desc, A, w.shift);
   PD_CK_LAUNCH();
+  if (ns) {
+    // FP32 Jacobi on the blocks far from diagonal gives the starting eigenvectors
+    PD_CK(cudaMemcpyAsync(w.dsub, sub.data(), sizeof(SmallDesc) * ns, cudaMemcpyHostToDevice, st));
+    const dim3 g((unsigned)gcast.x, (unsigned)ns);
+    small_cast_kernel<S, L><<<g, 256, 0, st>>>(w.dsub, A, w.A32);
+    PD_CK_LAUNCH();
+    PD_TRY(launch_jacobi<L>(ns, w.dsub, max_m, w.A32, w.V32w, w.V32, w.lam32, 1e-6, 30, w.sweeps, w.jscratch, st));
+    if (fp32_sweeps_out)
+      PD_CK(cudaMemcpyAsync(fp32_sweeps_out, w.sweeps, sizeof(int) * ns, cudaMemcpyDeviceToDevice, st));
+    small_cast_kernel<L, S><<<g, 256, 0, st>>>(w.dsub, w.V32, w.Vd);
+    PD_CK_LAUNCH();
+  }
+  for (auto& b : rest) {  // nearly diagonal blocks start from the identity
+    PD_CK(cudaMemsetAsync(w.Vd + b.off, 0, sizeof(S) * (size_t)b.m * b.m, st));
+    identity_kernel<S><<<1, 256, 0, st>>>(w.Vd + b.off, b.m);
+    PD_CK_LAUNCH();
+  }
+  // FP64 refinement of V: each step roughly squares the relative error; stop after the
+  // step whose input error estimate delta/max|lambda| was below 1e-7 (at most 6 steps)
+  S* V = w.Vd;
+  S* Vn = w.Vw;
+  std::vector<double> drel(nblk);
+  for (int it = 0; it < 6; ++it) {
+    {
+      S* abc[3] = {A, V, w.T};  // T = A V
+      PD_TRY(small_gemm<S>(false, all, max_m, abc, 0, 0, w.items, st));
+    }
+    {
+      S* abc[3] = {V, w.T, w.W64};  // S = V^H A V  (in W64)
+      PD_TRY(small_gemm<S>(true, all, max_m, abc, 1, 0, w.items, st));
+    }
+    {
+      S* abc[3] = {V, V, w.T};  // P = V^H V  (in T)
+      PD_TRY(small_gemm<S>(true, all, max_m, abc, 1, 0, w.items, st));
+    }
+    oa_kernel<S><<<nblk, 1024, 0, st>>>(d_desc, w.W64, w.T, w.lam32, w.delta);
+    PD_CK_LAUNCH();
+    for (auto& b : all) PD_CK(cudaMemcpyAsync(Vn + b.off, V + b.off, sizeof(S) * (size_t)b.m * b.m,
+                                              cudaMemcpyDeviceToDevice, st));
+    {
+      // Vn = V + V E
+      std::vector<GemmItem<S>> it2(nblk);
+      for (int t = 0; t < nblk; ++t) {
+        const int m = all[t].m;
+        const int64_t o = all[t].off;
+        it2[t] = GemmItem<S>{V + o, w.W64 + o, Vn + o, m, m, m, m, m, m, 0};
+      }
+      PD_CK(cudaMemcpyAsync(w.items, it2.data(), sizeof(GemmItem<S>) * nblk, cudaMemcpyHostToDevice, st));
+      PD_TRY(launch_gemm<S>(false, nblk, w.items, max_m, max_m, max_m, one, one, 1, nullptr, 0, st, 0, 0));
+    }
+    std::swap(V, Vn);
+    PD_CK(cudaMemcpyAsync(drel.data(), w.delta, sizeof(double) * nblk, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    double dmax = 0.0;
+    for (double v : drel) dmax = std::max(dmax, v);
+    if (dmax < 1e-7) break;
+  }
+  sort_phase_kernel<S><<<nblk, 1024, 0, st>>>(d_desc, V, w.lam32, lam, W);
+  PD_CK_LAUNCH();
+  cluster_check_kernel<S><<<nblk, 256, 0, st>>>(d_desc, lam, w.delta, w.sweeps);
+  PD_CK_LAUNCH();
+  std::vector<int> flag(nblk, 0);
+  PD_CK(cudaMemcpyAsync(flag.data(), w.sweeps, sizeof(int) * nblk, cudaMemcpyDeviceToHost, st));
+  PD_CK(cudaStreamSynchronize(st));
+  // Blocks where the refinement did not converge (last input error >= 1e-7) or left
+  // an unresolved cluster are redone robustly: start vectors (V32 orthonormalised in
+  // FP64, or I), H = V^H A V, FP64 Jacobi on H, W = V W64.
+  std::vector<SmallDesc> fb, fb32;
+  std::vector<int> fbidx;
+  for (int t = 0; t < nblk; ++t) {
+    if (!(flag[t] || drel[t] >= 1e-7)) continue;
+    fb.push_back(all[t]);
+    fbidx.push_back(t);
+  }
+  const int nfb = (int)fb.size();
+  if (nfb) {
+    PD_CK(cudaMemcpyAsync(w.dsub, fb.data(), sizeof(SmallDesc) * nfb, cudaMemcpyHostToDevice, st));
+    for (int q = 0; q < nfb; ++q) {
+      const SmallDesc b = fb[q];
+      const bool had32 = h_fp32 == nullptr || h_fp32[fbidx[q]];
+      if (had32) {
+        fb32.push_back(b);
+      } else {
+        PD_CK(cudaMemsetAsync(w.Vd + b.off, 0, sizeof(S) * (size_t)b.m * b.m, st));
+        identity_kernel<S><<<1, 256, 0, st>>>(w.Vd + b.off, b.m);
+        PD_CK_LAUNCH();
+      }
+    }
+    if (!fb32.empty()) {
+      const int n32 = (int)fb32.size();
+      SmallDesc* d32 = w.dsub + nfb;  // second half of the descriptor scratch
+      PD_CK(cudaMemcpyAsync(d32, fb32.data(), sizeof(SmallDesc) * n32, cudaMemcpyHostToDevice, st));
+      small_cast_kernel<L, S><<<dim3((unsigned)gcast.x, (unsigned)n32), 256, 0, st>>>(d32, w.V32, w.Vd);
+      PD_CK_LAUNCH();
+      {
+        S* abc[3] = {w.Vd, w.Vd, w.T};
+        PD_TRY(small_gemm<S>(true, fb32, max_m, abc, 1, 0, w.items, st));
+      }
+      PD_TRY(launch_cholesky<S>(n32, d32, w.T, w.sweeps, st));
+      PD_TRY(launch_triinv<S>(n32, d32, w.T, w.Vw, st));
+      {
+        S* abc[3] = {w.Vd, w.Vw, w.W64};
+        PD_TRY(small_gemm<S>(false, fb32, max_m, abc, 0, 1, w.items, st));
+      }
+      for (auto& b : fb32)
+        PD_CK(cudaMemcpyAsync(w.Vd + b.off, w.W64 + b.off, sizeof(S) * (size_t)b.m * b.m, cudaMemcpyDeviceToDevice, st));
+    }
+    {
+      S* abc[3] = {A, w.Vd, w.T};  // T = A V
+      PD_TRY(small_gemm<S>(false, fb, max_m, abc, 0, 0, w.items, st));
+    }
+    {
+      S* abc[3] = {w.Vd, w.T, w.A64};  // H = V^H A V
+      PD_TRY(small_gemm<S>(true, fb, max_m, abc, 1, 0, w.items, st));
+    }
+    PD_TRY(launch_jacobi<S>(nfb, w.dsub, max_m, w.A64, w.Vw, w.W64, lam, 1e-13, 60, w.sweeps, w.jscratch, st));
+    {
+      S* abc[3] = {w.Vd, w.W64, W};
+      PD_TRY(small_gemm<S>(false, fb, max_m, abc, 0, 0, w.items, st));
+    }
+    phase_kernel<S><<<dim3((unsigned)ceil_div(max_m, 8), nfb), 256, 0, st>>>(w.dsub, W);
+    PD_CK_LAUNCH();
+  }
+  unshift_kernel<<<nblk, 256, 0, st>>>(d_desc, lam, w.shift);
+  PD_CK_LAUNCH();
+  if (fp64_sweeps_out) {
+    // report the fallback Jacobi's sweeps (0 for blocks that did not need it)
+    std::vector<int> sw(nblk, 0);
+    if (nfb) {
+      std::vector<int> swf(nfb);
+      PD_CK(cudaMemcpyAsync(swf.data(), w.sweeps, sizeof(int) * nfb, cudaMemcpyDeviceToHost, st));
+      PD_CK(cudaStreamSynchronize(st));
+      for (int q = 0; q < nfb; ++q) sw[fbidx[q]] = swf[q];
+    }
+    PD_CK(cudaMemcpyAsync(fp64_sweeps_out, sw.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice, st));
+  }
   return 0;
 }
 
 // explicit instantiations
+template int small_gemm<double>(bool, const std::vector<SmallDesc>&, int, double* const*, int, int,
+                                GemmItem<double>*, cudaStream_t);
+template int small_gemm<double2>(bool, const std::vector<SmallDesc>&, int, double2* const*, int, int,
+                                 GemmItem<double2>*, cudaStream_t);
 template EighScratch<double> plan_eigh_scratch<double>(Arena&, int64_t, int64_t, int);
 template EighScratch<double2> plan_eigh_scratch<double2>(Arena&, int64_t, int64_t, int);
 template int eigh_mixed<double>(int, const SmallDesc*, const SmallDesc*, int, double*, double*, double*,
-                                const EighScratch<double>&, cudaStream_t, int*);
+                                const EighScratch<double>&, cudaStream_t, int*, const unsigned char*, int*);
 template int eigh_mixed<double2>(int, const SmallDesc*, const SmallDesc*, int, double2*, double*, double2*,
-                                 const EighScratch<double2>&, cudaStream_t, int*);
+                                 const EighScratch<double2>&, cudaStream_t, int*, const unsigned char*, int*);
 template int launch_gemm<double>(bool, int, const GemmItem<double>*, int, int, int, double, double, int,
                                  double*, int64_t, cudaStream_t, int, int);
 template int launch_gemm<double2>(bool, int, const GemmItem<double2>*, int, int, int, double2, double2, int,

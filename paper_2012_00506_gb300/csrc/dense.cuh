@@ -3,6 +3,8 @@
 // CholQR: batched GEMM, small Cholesky and triangular inverse, cluster
 // parallel Jacobi eigensolver, band-times-block products, column norms.
 #pragma once
+#include <vector>
+
 #include "common.cuh"
 
 namespace pdeshep {
@@ -47,6 +49,7 @@ int launch_cholesky(int nblk, const SmallDesc* d_desc, S* G, int* info, cudaStre
                     double* diag0 = nullptr, double* minratio = nullptr);
 
 // Rinv = R^{-1} for upper triangular R (out of place, same layout).
+int cluster_ctas_used();
 template <typename S>
 int launch_triinv(int nblk, const SmallDesc* d_desc, const S* R, S* Rinv, cudaStream_t st);
 
@@ -57,9 +60,11 @@ template <typename S>
 int launch_jacobi(int nblk, const SmallDesc* d_desc, int max_m, S* A, S* Vwork, S* Vout, double* lam,
                   double tol, int max_sweeps, int* sweeps_out, double* scratch, cudaStream_t st);
 
-// Mixed-precision small Hermitian eigensolver: FP32 Jacobi gives V32; in FP64
-// H = V32^H A V32 is nearly diagonal and a few FP64 Jacobi sweeps finish it;
-// the eigenvectors are V32 W64.  Same layout and outputs as launch_jacobi.
+// Mixed-precision small Hermitian eigensolver: FP32 Jacobi gives V32 (blocks
+// already close to diagonal start from I instead), FP64 Ogita-Aishima
+// refinement steps (batched GEMMs over all SMs) bring V to FP64 accuracy, and
+// blocks left with an unresolved cluster finish with FP64 Jacobi sweeps on
+// V^H A V.  Same layout and outputs as launch_jacobi.
 template <typename S>
 struct EighScratch {
   typename lowp<S>::type* A32;
@@ -73,12 +78,24 @@ struct EighScratch {
   int* sweeps;
   double* jscratch;
   GemmItem<S>* items;
+  SmallDesc* dsub;
+  double* delta;
+  double* shift;
+  S* A64;
 };
 template <typename S>
 EighScratch<S> plan_eigh_scratch(Arena& a, int64_t msq, int64_t mtot, int nblk);
+// C_t = op(A_t) B_t for m x m blocks at each block's offset (abc = {A, B, C} bases).
+template <typename S>
+int small_gemm(bool conjA, const std::vector<SmallDesc>& blk, int max_m, S* const* abc, int herm, int triB,
+               GemmItem<S>* d_items, cudaStream_t st);
+
+// h_fp32[t] (optional, default all): run the FP32 pre-rotation on block t; blocks that are
+// already nearly diagonal skip it and go straight to the FP64 sweeps.
 template <typename S>
 int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int max_m, S* A, double* lam, S* W,
-               const EighScratch<S>& w, cudaStream_t st, int* fp64_sweeps_out = nullptr);
+               const EighScratch<S>& w, cudaStream_t st, int* fp64_sweeps_out = nullptr,
+               const unsigned char* h_fp32 = nullptr, int* fp32_sweeps_out = nullptr);
 
 // Y = B X for the Hermitian band (lower storage), X, Y n x ncols (ld n).
 template <typename S>

@@ -176,6 +176,55 @@ __global__ void symmetrize_kernel(const SmallDesc* desc, S* Aall) {
   }
 }
 
+// ratio[t] = off(A)^2 / ||A - mu I||_F^2 of each small block, mu = mean of the diagonal
+// (the eigenvalues of a slice's projected matrix cluster around mu)
+template <typename S>
+__global__ void offratio_kernel(const SmallDesc* desc, const S* Aall, double* ratio) {
+  const SmallDesc d = desc[blockIdx.x];
+  const S* A = Aall + d.off;
+  __shared__ double s1[32], s2[32], s3[32];
+  __shared__ double mu;
+  double dsum = 0.0;
+  for (int i = threadIdx.x; i < d.m; i += blockDim.x) dsum += sc<S>::re(A[i + (int64_t)i * d.m]);
+  for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+  if ((threadIdx.x & 31) == 0) s3[threadIdx.x >> 5] = dsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s3[w];
+    mu = t / d.m;
+  }
+  __syncthreads();
+  double off = 0.0, fro = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)d.m * d.m; e += blockDim.x) {
+    if (e % d.m != e / d.m) {
+      const double a = sc<S>::abs2(A[e]);
+      off += a;
+      fro += a;
+    } else {
+      const double a = sc<S>::re(A[e]) - mu;
+      fro += a * a;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    off += __shfl_down_sync(0xffffffffu, off, o);
+    fro += __shfl_down_sync(0xffffffffu, fro, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = off;
+    s2[threadIdx.x >> 5] = fro;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += s1[w];
+      b += s2[w];
+    }
+    ratio[blockIdx.x] = b > 0.0 ? a / b : 0.0;
+  }
+}
+
 // R = BX - X diag(lam) (in place on BX), res = ||R||/(bnorm ||X||), colscale = ||R|| (1 if 0)
 template <typename S>
 __global__ void residual_kernel(int64_t n, const SliceDesc* sd, const S* __restrict__ X, S* __restrict__ BX,
@@ -295,11 +344,16 @@ struct Plan {
   void* small_G;   // S sum m0^2 (Gram / R)
   void* small_I;   // S sum m0^2 (R^{-1}, Jacobi work)
   void* small_W;   // S sum m0^2 (eigenvectors)
+  void* small_A;   // S sum m0^2 (projected matrix before the basis change)
+  void* small_T;   // S sum m0^2 (temporary)
+  double* offratio;// K
+  GemmItem<double2>* d_items_small; // K
   void* part;      // S splits * sum m0^2
   int* info;       // K (Cholesky)
   double* minratio;// K (Cholesky conditioning indicator)
   double* diag0;   // M (Gram diagonal)
   int* sweeps;     // K
+  int* sweeps32;   // K
   int* nconv;      // K
   int* dest;       // M
   int* sys_status; // max systems
@@ -410,12 +464,17 @@ struct Feast {
     q.small_G = a.take<S>(Msq);
     q.small_I = a.take<S>(Msq);
     q.small_W = a.take<S>(Msq);
+    q.small_A = a.take<S>(Msq);
+    q.small_T = a.take<S>(Msq);
+    q.offratio = a.take<double>(K);
+    q.d_items_small = a.take<GemmItem<double2>>(K);
     q.splits = 8;
     q.part = a.take<S>((size_t)q.splits * Msq);
     q.info = a.take<int>(K);
     q.minratio = a.take<double>(K);
     q.diag0 = a.take<double>(M);
     q.sweeps = a.take<int>(K);
+    q.sweeps32 = a.take<int>(K);
     q.nconv = a.take<int>(K);
     q.dest = a.take<int>(M);
     q.sys_status = a.take<int>((size_t)K * ne);
@@ -546,8 +605,8 @@ struct FeastRun : Feast<S, C> {
     return this->kt.end(fl);
   }
 
-  // One CholQR pass on the active slices' blocks of p.Q (result back in p.Q).
-  int cholqr_pass() {
+  // Gram matrix, Cholesky and R^{-1} of the active slices' blocks of p.Q (Q itself unchanged).
+  int chol_factor() {
     const int na = (int)active.size();
     S* G = (S*)p.small_G;
     S* I = (S*)p.small_I;
@@ -557,15 +616,22 @@ struct FeastRun : Feast<S, C> {
     PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
     PD_TRY(launch_cholesky<S>(na, p.d_small, G, p.info, st, p.diag0, p.minratio));
     PD_TRY(launch_triinv<S>(na, p.d_small, G, I, st));
-    PD_TRY(this->kt.end(flsmall));
-    PD_TRY(gemm(1, (S*)p.Q, I, (S*)p.Q2, 1));
-    for (int s : active)
-      PD_CK(cudaMemcpyAsync((S*)p.Q + col_off[s] * n, (S*)p.Q2 + col_off[s] * n, sizeof(S) * n * m0[s],
-                            cudaMemcpyDeviceToDevice, st));
-    return 0;
+    return this->kt.end(flsmall);
   }
 
-  // Rayleigh-Ritz on Q for the active slices -> Xt, lam, BQ = residuals, res, colscale, nconv
+  int small_mm(bool conjA, S* A, S* Bm, S* Cm, int herm, int tri) {
+    S* abc[3] = {A, Bm, Cm};
+    double fl = 0.0;
+    for (int s : active) fl += this->cw() * (double)m0[s] * m0[s] * m0[s] * ((herm || tri) ? 0.5 : 1.0);
+    PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
+    PD_TRY(small_gemm<S>(conjA, this->h_small, act_max_m0(), abc, herm, tri, (GemmItem<S>*)p.d_items_small, st));
+    return this->kt.end(fl);
+  }
+
+  // Rayleigh-Ritz on span(Q) for the active slices -> Xt, lam, BQ = residuals, res, colscale, nconv.
+  // CholQR is fused: with Q^H Q = R^H R, the orthonormal basis Q R^{-1} is never formed;
+  // A~ = R^{-H} (Q^H B Q) R^{-1}, A~ W = W Lambda, X = Q (R^{-1} W).  Slices whose columns
+  // are far from orthogonal get an explicit first pass Q <- Q R1^{-1} (CholQR2).
   int rr() {
     const int na = (int)active.size();
     if (!na) return 0;
@@ -574,15 +640,15 @@ struct FeastRun : Feast<S, C> {
     S* G = (S*)p.small_G;
     S* I = (S*)p.small_I;
     S* W = (S*)p.small_W;
-    // CholQR: one pass, repeated for the slices whose columns were far from
-    // orthogonal (min_c R(c,c)^2/G(c,c) < 1/4), i.e. CholQR2 where it matters.
-    PD_TRY(cholqr_pass());
+    S* Aq = (S*)p.small_A;
+    S* T = (S*)p.small_T;
+    PD_TRY(chol_factor());
     std::vector<int> info(K, 0);
     std::vector<double> mr(K, 1.0);
     PD_CK(cudaMemcpyAsync(info.data(), p.info, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaMemcpyAsync(mr.data(), p.minratio, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
-    // per-slice kernel outputs (info, minratio, sweeps) are indexed by position in the active batch
+    // per-slice kernel outputs (info, minratio, sweeps, offratio) are indexed by position in the active batch
     for (int a = 0; a < na; ++a)
       if (info[a]) return PDESHEP_CHOLQR_BREAKDOWN;
     std::vector<int> again;
@@ -592,7 +658,11 @@ struct FeastRun : Feast<S, C> {
       std::vector<int> keep = active;
       active = again;
       PD_TRY(upload_active());
-      PD_TRY(cholqr_pass());
+      PD_TRY(gemm(1, (S*)p.Q, I, (S*)p.Q2, 1));
+      for (int s : active)
+        PD_CK(cudaMemcpyAsync((S*)p.Q + col_off[s] * n, (S*)p.Q2 + col_off[s] * n, sizeof(S) * n * m0[s],
+                              cudaMemcpyDeviceToDevice, st));
+      PD_TRY(chol_factor());
       active = keep;
       PD_TRY(upload_active());
       PD_CK(cudaMemcpyAsync(info.data(), p.info, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
@@ -601,13 +671,25 @@ struct FeastRun : Feast<S, C> {
         if (info[a]) return PDESHEP_CHOLQR_BREAKDOWN;
     }
     PD_TRY(band_mm((S*)p.Q, (S*)p.BQ));
-    PD_TRY(gemm(0, (S*)p.Q, (S*)p.BQ, G));
+    PD_TRY(gemm(0, (S*)p.Q, (S*)p.BQ, Aq));         // Q^H B Q
+    PD_TRY(small_mm(false, Aq, I, T, 0, 1));         // (Q^H B Q) R^{-1}
+    PD_TRY(small_mm(true, I, T, G, 1, 0));           // A~ = R^{-H} (Q^H B Q) R^{-1}
     PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
     symmetrize_kernel<S><<<dim3(grid1((int64_t)mm * mm), na), 256, 0, st>>>(p.d_small, G);
     PD_CK_LAUNCH();
-    PD_TRY(eigh_mixed<S>(na, p.d_small, this->h_small.data(), mm, G, p.lam, W, this->eig, st, p.sweeps));
+    offratio_kernel<S><<<na, 256, 0, st>>>(p.d_small, G, p.offratio);
+    PD_CK_LAUNCH();
+    std::vector<double> orat(K, 1.0);
+    PD_CK(cudaMemcpyAsync(orat.data(), p.offratio, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    std::vector<unsigned char> fp32(na);
+    for (int a = 0; a < na; ++a) fp32[a] = orat[a] > 1e-6 ? 1 : 0;  // off(A~) > 1e-3 ||A~||_F
+    PD_CK(cudaMemsetAsync(p.sweeps32, 0, sizeof(int) * K, st));
+    PD_TRY(eigh_mixed<S>(na, p.d_small, this->h_small.data(), mm, G, p.lam, W, this->eig, st, p.sweeps,
+                         fp32.data(), p.sweeps32));
     PD_TRY(this->kt.end(0.0));
-    PD_TRY(gemm(1, (S*)p.Q, W, (S*)p.Xt));
+    PD_TRY(small_mm(false, I, W, T, 0, 0));          // R^{-1} W
+    PD_TRY(gemm(1, (S*)p.Q, T, (S*)p.Xt));           // X = Q R^{-1} W
     PD_TRY(band_mm((S*)p.Xt, (S*)p.BQ));
     PD_TRY(this->kt.begin(PDESHEP_KG_BANDMM));
     residual_kernel<S><<<dim3(mm, na), 256, 0, st>>>(n, p.d_sd, (S*)p.Xt, (S*)p.BQ, p.lam, bnorm, p.res,
@@ -616,12 +698,20 @@ struct FeastRun : Feast<S, C> {
     PD_TRY(this->kt.end(0.0));
     nconv_kernel<<<na, 256, 0, st>>>(p.d_sd, p.lam, p.res, o->tol, p.nconv);
     PD_CK_LAUNCH();
-    std::vector<int> sw(K, 0);
+    std::vector<int> sw(K, 0), sw32(K, 0);
     PD_CK(cudaMemcpyAsync(nconv.data(), p.nconv, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaMemcpyAsync(sw.data(), p.sweeps, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaMemcpyAsync(sw32.data(), p.sweeps32, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
-    for (int a = 0; a < na; ++a)
+    int mx64 = 0, mx32 = 0;
+    for (int a = 0; a < na; ++a) {
       if (sw[a] < 0) return PDESHEP_EIG_NOT_CONVERGED;
+      mx64 = std::max(mx64, sw[a]);
+      mx32 = std::max(mx32, sw32[a] < 0 ? 20 : sw32[a]);
+    }
+    stats.jacobi_sweeps64 += mx64;
+    stats.jacobi_sweeps32 += mx32;
+    stats.rr_calls += 1;
     return this->kt.collect();
   }
 
@@ -967,6 +1057,7 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
       F.stats.kg_flops[gi] = F.kt.fl[gi];
     }
     F.stats.ms_factor = F.kt.ms[PDESHEP_KG_FACTOR];
+    F.stats.cluster_ctas = cluster_ctas_used();
     *h_stats = F.stats;
   }
   return status;
