@@ -280,6 +280,92 @@ int pdeshep_band_slice(int64_t n, int32_t b, int32_t is_complex, const void* d_b
                        const pdeshep_opts* opts, double* d_evals, void* d_evecs, int32_t* h_counts,
                        int32_t* h_nfound, pdeshep_stats* h_stats);
 
+/* ======================================================================== */
+/* Slice proposal.  The paper slices the spectrum by inertia counts          */
+/* (Section 3.2) and, with no earlier spectrum to go by, points to density- */
+/* of-states estimates (Section 3.1); one of its partition objectives is an  */
+/* equal eigenvalue count per slice (Section 3.1).  The network below is not */
+/* in the paper: it predicts equal-count boundaries from cheap statistics of */
+/* the band, and every count the proposer returns is an exact inertia count. */
+/* ======================================================================== */
+
+/* Number of FP32 parameters of the proposal network 98 -> 256 -> 256 -> 256  */
+/* -> 64 (ReLU hidden layers, softmax head).  Parameter vector layout: for   */
+/* each of the four layers W (out x in, row-major) then its bias (out).      */
+int64_t pdeshep_mlp_param_count(void);
+
+/* ------------------------------------------------------------------------ */
+/* 98 FP32 features of one band into d_features[98] (asynchronous):         */
+/*  [0,64)  histogram of diag(B) over the Gershgorin interval [lo, hi]: bin  */
+/*          k = clamp(floor((d - lo) / ((hi - lo)/64)), 0, 63) computed in   */
+/*          FP64, as fractions of n;                                        */
+/*  64, 65  (lo + hi)/2 / s and (hi - lo)/2 / s with s = max(|lo|, |hi|);    */
+/*  [66,98) Chebyshev moments mu_k = (1/(8n)) sum_p z_p^H T_k(Bs) z_p,       */
+/*          k = 0..31, of Bs = (B - c I)/r (c, r the interval's centre and   */
+/*          half-width), accumulated in FP64 (kernel polynomial method).     */
+/* Probe p (p = 0..7), entry i: +1 if splitmix64(seed + p*n + i) is even,    */
+/* else -1 (splitmix64: Vigna's 64-bit mixer with increment                 */
+/* 0x9e3779b97f4a7c15).  d_work: pdeshep_slice_features_workspace_size      */
+/* bytes (5 * 8 * n scalars of the band's type plus a few KiB).             */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_slice_features_workspace_size(int64_t n, int32_t is_complex);
+int pdeshep_slice_features(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                           uint64_t seed, float* d_features, void* d_work, size_t work_bytes,
+                           void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Network evaluation on a batch (asynchronous, FP32).  d_x: batch x 98      */
+/* row-major features; d_bounds: batch x 63 row-major outputs, the cumulative */
+/* sums of the softmax of the 64 logits = predicted equal-count boundaries   */
+/* k/64 (k = 1..63) in normalised [0, 1] coordinates of the Gershgorin       */
+/* interval.  pdeshep_mlp_grad also takes targets (batch x 63) and writes    */
+/* the loss L = mean over batch and the 63 boundaries of the squared error  */
+/* to d_loss[0] and dL/dparams to d_grad (param_count floats).              */
+/* pdeshep_mlp_train_step does that and one Adam step (beta1 0.9, beta2      */
+/* 0.999, eps 1e-8, bias correction with the 1-based `step`) on d_params,    */
+/* d_adam_m, d_adam_v (param_count floats each, moments start at zero).      */
+/* batch in [1, 65535]; d_work: pdeshep_mlp_workspace_size(batch) bytes.     */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_mlp_workspace_size(int32_t batch);
+int pdeshep_mlp_forward(const float* d_params, int32_t batch, const float* d_x, float* d_bounds,
+                        void* d_work, size_t work_bytes, void* stream);
+int pdeshep_mlp_grad(const float* d_params, int32_t batch, const float* d_x, const float* d_target,
+                     float* d_grad, float* d_loss, void* d_work, size_t work_bytes, void* stream);
+int pdeshep_mlp_train_step(float* d_params, float* d_adam_m, float* d_adam_v, int32_t step, float lr,
+                           int32_t batch, const float* d_x, const float* d_target, float* d_loss,
+                           void* d_work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Propose nslices slices holding equal shares of the eigenvalues with       */
+/* ascending indices in [frac_lo n, frac_hi n):  target count of boundary k  */
+/* is t_k = round(n (frac_lo + (frac_hi - frac_lo) k / nslices)).            */
+/*  1. Proposal: with d_params, features -> network -> the predicted         */
+/*     counting function, inverted piecewise linearly at t_k / n; with       */
+/*     d_params == NULL, equal widths over the Gershgorin interval (uniform  */
+/*     density; the "no network" baseline).  Boundaries with t_k = 0 or n sit */
+/*     just outside the Gershgorin interval (exact counts 0 and n).          */
+/*  2. Validation: exact inertia counts at every other boundary, all in one  */
+/*     batched launch; a boundary is accepted if |count - t_k| <= count_tol. */
+/*  3. Fall-back: the rejected boundaries are re-placed together by          */
+/*     multisection on inertia (`fanout` points per boundary per launch)     */
+/*     inside brackets taken from every count evaluated so far, until each   */
+/*     count is within count_tol (or the bracket is a cluster narrower than  */
+/*     rounding, where the closest count is kept).                          */
+/* Outputs: h_bounds[nslices+1] ascending, h_counts[nslices] exact inertia   */
+/* counts of [h_bounds[k], h_bounds[k+1]); optional h_used_fallback = number */
+/* of boundaries rejected in step 2, h_inertia_evals = shifts evaluated.     */
+/* n >= 1, nslices in [1, 1024], fanout in [1, 64].  Synchronous.            */
+/* d_work: pdeshep_propose_workspace_size bytes.  NONFINITE_INPUT if the     */
+/* band holds NaN/Inf.                                                       */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_propose_workspace_size(int64_t n, int32_t b, int32_t is_complex, int32_t nslices,
+                                      int32_t fanout);
+int pdeshep_propose_slices(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                           const float* d_params, uint64_t seed, double frac_lo, double frac_hi,
+                           int32_t nslices, int32_t count_tol, int32_t fanout, double* h_bounds,
+                           int32_t* h_counts, int32_t* h_used_fallback, int64_t* h_inertia_evals,
+                           void* d_work, size_t work_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,6 +42,9 @@ EXPORTED = [
     "pdeshep_shifted_solve_workspace_size", "pdeshep_shifted_solve", "pdeshep_band_matmul",
     "pdeshep_cholqr_workspace_size", "pdeshep_cholqr", "pdeshep_eigh_workspace_size",
     "pdeshep_eigh", "pdeshep_workspace_size", "pdeshep_band_slice",
+    "pdeshep_mlp_param_count", "pdeshep_slice_features_workspace_size", "pdeshep_slice_features",
+    "pdeshep_mlp_workspace_size", "pdeshep_mlp_forward", "pdeshep_mlp_grad", "pdeshep_mlp_train_step",
+    "pdeshep_propose_workspace_size", "pdeshep_propose_slices",
 ]
 
 
@@ -124,6 +127,16 @@ def load(path: str = LIB_PATH):
         "pdeshep_workspace_size": (sz, [i64, i32, i32, i32, P, i32, C.POINTER(Opts)]),
         "pdeshep_band_slice": (C.c_int, [i64, i32, i32, P, i64, i32, P, i32, P, P, P, P, P, sz,
                                          C.POINTER(Opts), P, P, P, P, C.POINTER(Stats)]),
+        "pdeshep_mlp_param_count": (i64, []),
+        "pdeshep_slice_features_workspace_size": (sz, [i64, i32]),
+        "pdeshep_slice_features": (C.c_int, [i64, i32, i32, P, i64, C.c_uint64, P, P, sz, P]),
+        "pdeshep_mlp_workspace_size": (sz, [i32]),
+        "pdeshep_mlp_forward": (C.c_int, [P, i32, P, P, P, sz, P]),
+        "pdeshep_mlp_grad": (C.c_int, [P, i32, P, P, P, P, P, sz, P]),
+        "pdeshep_mlp_train_step": (C.c_int, [P, P, P, i32, C.c_float, i32, P, P, P, P, sz, P]),
+        "pdeshep_propose_workspace_size": (sz, [i64, i32, i32, i32, i32]),
+        "pdeshep_propose_slices": (C.c_int, [i64, i32, i32, P, i64, P, C.c_uint64, dbl, dbl, i32, i32, i32,
+                                             P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
