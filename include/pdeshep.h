@@ -338,7 +338,7 @@ int pdeshep_mlp_train_step(float* d_params, float* d_adam_m, float* d_adam_v, in
 /* ------------------------------------------------------------------------ */
 /* Propose nslices slices holding equal shares of the eigenvalues with       */
 /* ascending indices in [frac_lo n, frac_hi n):  target count of boundary k  */
-/* is t_k = round(n (frac_lo + (frac_hi - frac_lo) k / nslices)).            */
+/* is t_k = floor(n (frac_lo + (frac_hi - frac_lo) k / nslices) + 1/2).     */
 /*  1. Proposal: with d_params, features -> network -> the predicted         */
 /*     counting function, inverted piecewise linearly at t_k / n; with       */
 /*     d_params == NULL, equal widths over the Gershgorin interval (uniform  */
@@ -353,7 +353,12 @@ int pdeshep_mlp_train_step(float* d_params, float* d_adam_m, float* d_adam_v, in
 /*     rounding, where the closest count is kept).                          */
 /* Outputs: h_bounds[nslices+1] ascending, h_counts[nslices] exact inertia   */
 /* counts of [h_bounds[k], h_bounds[k+1]); optional h_used_fallback = number */
-/* of boundaries rejected in step 2, h_inertia_evals = shifts evaluated.     */
+/* of boundaries rejected in step 2, h_inertia_evals = shifts evaluated,     */
+/* h_proposed_counts[nslices+1] = exact count below each boundary of step 1 */
+/* (before the fall-back; it measures the proposal's quality).  In step 3    */
+/* one point per boundary and launch is the regula-falsi estimate on the     */
+/* counting function, the other fanout-1 split the bracket evenly (fanout 1: */
+/* plain bisection).                                                         */
 /* n >= 1, nslices in [1, 1024], fanout in [1, 64].  Synchronous.            */
 /* d_work: pdeshep_propose_workspace_size bytes.  NONFINITE_INPUT if the     */
 /* band holds NaN/Inf.                                                       */
@@ -364,7 +369,7 @@ int pdeshep_propose_slices(int64_t n, int32_t b, int32_t is_complex, const void*
                            const float* d_params, uint64_t seed, double frac_lo, double frac_hi,
                            int32_t nslices, int32_t count_tol, int32_t fanout, double* h_bounds,
                            int32_t* h_counts, int32_t* h_used_fallback, int64_t* h_inertia_evals,
-                           void* d_work, size_t work_bytes, void* stream);
+                           int64_t* h_proposed_counts, void* d_work, size_t work_bytes, void* stream);
 
 #ifdef __cplusplus
 }

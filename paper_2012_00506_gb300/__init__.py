@@ -136,7 +136,7 @@ def load(path: str = LIB_PATH):
         "pdeshep_mlp_train_step": (C.c_int, [P, P, P, i32, C.c_float, i32, P, P, P, P, sz, P]),
         "pdeshep_propose_workspace_size": (sz, [i64, i32, i32, i32, i32]),
         "pdeshep_propose_slices": (C.c_int, [i64, i32, i32, P, i64, P, C.c_uint64, dbl, dbl, i32, i32, i32,
-                                             P, P, P, P, P, sz, P]),
+                                             P, P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -510,8 +510,8 @@ struct Probe {
 
 static int propose(int64_t n, int b, int cplx, const void* band, int64_t ldab, const float* c63, double lo,
                    double hi, double f0, double f1, int K, int count_tol, int fanout, double* bounds,
-                   int32_t* counts, int32_t* used_fallback, int64_t* evals_out, void* iw, size_t iws,
-                   cudaStream_t st) {
+                   int32_t* counts, int32_t* used_fallback, int64_t* evals_out, int64_t* proposed_counts,
+                   void* iw, size_t iws, cudaStream_t st) {
   const double span = hi - lo;
   const double pad = 1e-3 * (span > 0 ? span : 1.0) + 1e-300;
   const double below = lo - pad, above = hi + pad;  // count 0 and n by the Gershgorin theorem
@@ -520,7 +520,7 @@ static int propose(int64_t n, int b, int cplx, const void* band, int64_t ldab, c
   std::vector<int64_t> neg(K + 1, -1);
   for (int k = 0; k <= K; ++k) {
     const double f = f0 + (f1 - f0) * k / K;
-    tgt[k] = std::min<int64_t>(n, std::max<int64_t>(0, (int64_t)llround(f * (double)n)));
+    tgt[k] = std::min<int64_t>(n, std::max<int64_t>(0, (int64_t)floor(f * (double)n + 0.5)));
     if (tgt[k] == 0) {
       sig[k] = below;
       neg[k] = 0;
@@ -560,6 +560,8 @@ static int propose(int64_t n, int b, int cplx, const void* band, int64_t ldab, c
   for (int k = 0; k <= K; ++k)
     if (!ok(k)) todo.push_back(k);
   if (used_fallback) *used_fallback = (int32_t)todo.size();
+  if (proposed_counts)
+    for (int k = 0; k <= K; ++k) proposed_counts[k] = neg[k];
   // 2. multisection on the failed boundaries.  Every count evaluated so far
   // (for any boundary) is reused: a point inside a boundary's window is taken
   // at once, the others bracket it as [a, c] with count(a) < target - tol and
@@ -582,19 +584,35 @@ static int propose(int64_t n, int b, int cplx, const void* band, int64_t ldab, c
         continue;
       }
       double a = below, c = above;
+      int64_t na = 0, nc = n;
       for (const Probe& q : seen) {
-        if (q.neg < tgt[k] - count_tol && q.sigma > a) a = q.sigma;
-        if (q.neg > tgt[k] + count_tol && q.sigma < c) c = q.sigma;
+        if (q.neg < tgt[k] - count_tol && q.sigma > a) {
+          a = q.sigma;
+          na = q.neg;
+        }
+        if (q.neg > tgt[k] + count_tol && q.sigma < c) {
+          c = q.sigma;
+          nc = q.neg;
+        }
       }
       const double w = c - a;
       next.push_back(k);
       if (!(w > 4e-16 * std::max(1.0, std::max(fabs(a), fabs(c))))) continue;  // unsplittable cluster
-      for (int f = 1; f <= fanout; ++f) {
-        const double x = a + w * f / (fanout + 1);
+      auto add = [&](double x) {
         if (x > a && x < c) {
           s.push_back(x);
           owner.push_back(k);
         }
+      };
+      if (fanout == 1) {
+        add(a + 0.5 * w);  // plain bisection
+      } else {
+        // one point where the straight line through (a, count(a)) and
+        // (c, count(c)) reaches the target (regula falsi on the counting
+        // function), the others split [a, c] evenly so that the bracket
+        // shrinks by fanout whatever the interpolation is worth
+        add(a + w * ((double)(tgt[k] - na) / (double)(nc - na)));
+        for (int f = 1; f < fanout; ++f) add(a + w * f / fanout);
       }
     }
     todo.swap(next);
@@ -747,7 +765,8 @@ extern "C" int pdeshep_propose_slices(int64_t n, int32_t b, int32_t is_complex, 
                                       const float* d_params, uint64_t seed, double frac_lo, double frac_hi,
                                       int32_t nslices, int32_t count_tol, int32_t fanout, double* h_bounds,
                                       int32_t* h_counts, int32_t* h_used_fallback, int64_t* h_inertia_evals,
-                                      void* d_work, size_t work_bytes, void* stream) {
+                                      int64_t* h_proposed_counts, void* d_work, size_t work_bytes,
+                                      void* stream) {
   if (n <= 0) return -1;
   if (b < 0) return -2;
   if (!d_band) return -4;
@@ -759,7 +778,7 @@ extern "C" int pdeshep_propose_slices(int64_t n, int32_t b, int32_t is_complex, 
   if (fanout < 1 || fanout > 64) return -12;
   if (!h_bounds) return -13;
   if (!h_counts) return -14;
-  if (!d_work) return -17;
+  if (!d_work) return -18;
   const int cplx = is_complex ? 1 : 0;
   cudaStream_t st = (cudaStream_t)stream;
   Arena a(d_work, work_bytes);
@@ -790,7 +809,7 @@ extern "C" int pdeshep_propose_slices(int64_t n, int32_t b, int32_t is_complex, 
   int32_t used = 0;
   int64_t evals = 0;
   PD_TRY(propose(n, b, cplx, d_band, ldab, d_params ? c63 : nullptr, lohi[0], lohi[1], frac_lo, frac_hi, nslices,
-                 count_tol, fanout, h_bounds, h_counts, &used, &evals, iw, iws, st));
+                 count_tol, fanout, h_bounds, h_counts, &used, &evals, h_proposed_counts, iw, iws, st));
   if (h_used_fallback) *h_used_fallback = used;
   if (h_inertia_evals) *h_inertia_evals = evals;
   return 0;

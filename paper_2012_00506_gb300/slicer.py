@@ -135,14 +135,14 @@ class Trainer:
         return self.loss
 
 
-def equal_count_targets(band, nslices: int = N_OUT, rtol: float = 1e-9, b=None, stream=None):
+def equal_count_targets(band, nslices: int = N_OUT, rtol: float = 1e-7, b=None, stream=None):
     """Training labels: the equal-count boundaries k n / nslices (k = 1..nslices-1),
     each the midpoint of the enclosures of eigenvalues t-1 and t (t = round(k n / nslices)),
     found by inertia bisection and normalised to the Gershgorin interval."""
     from . import bisect, gershgorin
     n = band.shape[0]
     lo, hi = gershgorin(band, b=b, stream=stream)
-    t = np.array([int(round(k * n / nslices)) for k in range(1, nslices)], dtype=np.int64)
+    t = np.array([(2 * k * n + nslices) // (2 * nslices) for k in range(1, nslices)], dtype=np.int64)
     t = np.clip(t, 1, n - 1)
     idx = np.unique(np.concatenate([t - 1, t]))
     elo, ehi = bisect(band, idx, rtol=rtol, fanout=8, b=b, stream=stream)
@@ -178,6 +178,7 @@ class Proposal:
     counts: np.ndarray        # exact eigenvalue count per slice
     used_fallback: int        # boundaries whose proposed count missed the target
     inertia_evals: int        # shifts evaluated (validation + fix-up)
+    proposed_counts: np.ndarray = None  # exact count below each proposed boundary, before the fix-up
 
 
 def propose_slices(band, params=None, nslices: int = N_OUT, frac=(0.0, 1.0), count_tol: int = 0,
@@ -190,13 +191,15 @@ def propose_slices(band, params=None, nslices: int = N_OUT, frac=(0.0, 1.0), cou
     counts = np.zeros(nslices, dtype=np.int32)
     used = C.c_int32()
     evals = C.c_int64()
+    proposed = np.zeros(nslices + 1, dtype=np.int64)
     ws = _workspace(lib.pdeshep_propose_workspace_size(n, b, cplx, nslices, fanout), band.device)
     st = lib.pdeshep_propose_slices(n, b, cplx, _ptr(band), ldab, _ptr(params),
                                     C.c_uint64(int(seed) & (2**64 - 1)), float(frac[0]), float(frac[1]),
                                     int(nslices), int(count_tol), int(fanout), _np_ptr(bounds), _np_ptr(counts),
-                                    C.byref(used), C.byref(evals), _ptr(ws), ws.numel(), _stream(stream))
+                                    C.byref(used), C.byref(evals), _np_ptr(proposed), _ptr(ws), ws.numel(),
+                                    _stream(stream))
     _check("pdeshep_propose_slices", st)
-    return Proposal(bounds, counts, int(used.value), int(evals.value))
+    return Proposal(bounds, counts, int(used.value), int(evals.value), proposed)
 
 
 def save_params(path: str, params, meta: dict | None = None):

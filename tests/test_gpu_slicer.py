@@ -94,7 +94,7 @@ def _check_counts(ab, pr, frac, nslices, tol, exact_targets=True):
     assert np.all(np.diff(bd) >= 0)
     neg = [oracle.inertia(ab, s) for s in bd]
     assert np.array_equal(np.diff(neg), pr.counts), (np.diff(neg), pr.counts)
-    tgt = np.round(n * (frac[0] + (frac[1] - frac[0]) * np.arange(nslices + 1) / nslices)).astype(int)
+    tgt = np.floor(n * (frac[0] + (frac[1] - frac[0]) * np.arange(nslices + 1) / nslices) + 0.5).astype(int)
     if exact_targets:
         assert np.all(np.abs(np.array(neg) - tgt) <= tol), (neg, tgt)
     return np.array(neg), tgt
@@ -139,35 +139,40 @@ def _family(seed, n, b):
 @pytest.fixture(scope="module")
 def trained(device):
     from paper_2012_00506_gb300 import slicer
-    bands = [to_dev(_family(1000 + s, 1024, 8), device) for s in range(192)]
-    params, losses, _ = slicer.train(bands, steps=1500, batch=64, lr=1e-3, seed=0, log_every=100)
+    bands = [to_dev(_family(1000 + s, 1024, 8), device) for s in range(1024)]
+    params, losses, _ = slicer.train(bands, steps=3000, batch=64, lr=1e-3, seed=0, log_every=250)
     return params, losses
 
 
 def test_training_reduces_loss(trained):
     _, losses = trained
-    assert losses[-1][1] < 0.2 * losses[0][1], losses
+    assert losses[-1][1] < 0.1 * losses[0][1], losses
 
 
 @pytest.mark.parametrize("tol", [4, 16])
 def test_network_gain_over_equal_widths(device, trained, tol):
-    """Held-out spectra of the same family: the trained proposal misses fewer boundaries
-    and needs fewer inertia evaluations than equal widths; counts are exact either way."""
+    """Held-out spectra of the same family: the trained network's boundaries are much
+    closer in count to the equal-count targets than equal widths, and the proposal
+    needs fewer inertia evaluations in all; counts are exact either way."""
     from paper_2012_00506_gb300 import slicer
     params, _ = trained
-    miss = {"mlp": 0, "none": 0}
+    err = {"mlp": [], "none": []}
     evals = {"mlp": 0, "none": 0}
     for s in range(16):
         ab = _family(50000 + s, 1024, 8)
         band = to_dev(ab, device)
+        tgt = np.floor(1024 * np.arange(17) / 16 + 0.5).astype(int)
         for name, p in (("mlp", params), ("none", None)):
             pr = slicer.propose_slices(band, p, nslices=16, count_tol=tol)
             if s < 4:
                 _check_counts(ab, pr, (0.0, 1.0), 16, tol)
-            miss[name] += pr.used_fallback
+            err[name] += list(np.abs(pr.proposed_counts - tgt)[1:-1])
             evals[name] += pr.inertia_evals
-    assert miss["mlp"] < 0.5 * miss["none"], (miss, evals)
-    assert evals["mlp"] < evals["none"], (miss, evals)
+    e_m, e_u = np.mean(err["mlp"]), np.mean(err["none"])
+    print(f"\nproposal count error (tol {tol}): network {e_m:.1f}, equal widths {e_u:.1f}; "
+          f"inertia evaluations: network {evals['mlp']}, equal widths {evals['none']}")
+    assert e_m < 0.33 * e_u, (e_m, e_u, evals)
+    assert evals["mlp"] < evals["none"], (e_m, e_u, evals)
 
 
 def test_weights_roundtrip(device, trained, tmp_path):
@@ -190,4 +195,4 @@ def test_proposal_full_size_complex(device, trained):
     cum = np.concatenate([[0], np.cumsum(pr.counts)])
     for k in (1, 20, 47, 63):
         assert oracle.inertia(ab, pr.bounds[k]) == cum[k]
-        assert abs(cum[k] - round(16384 * k / 64)) <= 16
+        assert abs(cum[k] - 16384 * k // 64) <= 16
