@@ -230,7 +230,7 @@ def run_gpu(args):
     kg_ms = {g: 0.0 for g in pk.KERNEL_GROUPS}
     kg_fl = {g: 0.0 for g in pk.KERNEL_GROUPS}
     kg_n = {g: 0 for g in pk.KERNEL_GROUPS}
-    iters, statuses, sweeps = [], [], []
+    iters, statuses, sweeps, eig_rep = [], [], [], []
     for k in range(W, W + K):
         inputs.append((k, x0, bounds))
         r = seq.step(k, x0, bounds, pk.MIXED)
@@ -239,6 +239,8 @@ def run_gpu(args):
         iters.append(r.stats["iterations"])
         cluster_ctas = r.stats["cluster_ctas"]
         sweeps.append((r.stats["rr_calls"], r.stats["jacobi_sweeps32"], r.stats["jacobi_sweeps64"]))
+        eig_rep.append({key: r.stats[key] for key in ("eig_refine_steps", "eig_clusters", "eig_max_cluster",
+                                                    "eig_fallback_unconverged", "eig_fallback_wide")})
         for g in pk.KERNEL_GROUPS:
             kg_ms[g] += r.stats["kg_ms"][g]
             kg_fl[g] += r.stats["kg_flops"][g]
@@ -286,6 +288,7 @@ def run_gpu(args):
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "iterations_per_step": iters, "status_per_step": statuses, "cluster_ctas": cluster_ctas,
            "rr_calls_sweeps32_sweeps64": sweeps,
+           "eigensolver": eig_rep,
            "kernel_groups": groups, "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
 
     if rank == 0 and not args.no_plain and args.plain_steps > 0:

@@ -109,6 +109,15 @@ typedef struct {
   int32_t jacobi_sweeps64; /* FP64 Jacobi sweeps, summed over Rayleigh-Ritz calls (max over slices) */
   int32_t jacobi_sweeps32; /* FP32 Jacobi sweeps, same accounting */
   int32_t rr_calls;        /* Rayleigh-Ritz calls */
+  /* small dense eigensolver, summed over Rayleigh-Ritz calls: FP64 refinement
+     steps, clusters resolved by their own Rayleigh-Ritz step (and the widest),
+     and blocks sent to the FP64 Jacobi path because the refinement had not
+     converged or left a cluster wider than 64 */
+  int32_t eig_refine_steps;
+  int32_t eig_clusters;
+  int32_t eig_max_cluster;
+  int32_t eig_fallback_unconverged;
+  int32_t eig_fallback_wide;
 } pdeshep_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -73,6 +73,8 @@ class Stats(C.Structure):
         ("kg_ms", C.c_double * 7), ("kg_launches", C.c_int64 * 7), ("kg_flops", C.c_double * 7),
         ("rhs_columns", C.c_int64), ("cluster_ctas", C.c_int32), ("jacobi_sweeps64", C.c_int32),
         ("jacobi_sweeps32", C.c_int32), ("rr_calls", C.c_int32),
+        ("eig_refine_steps", C.c_int32), ("eig_clusters", C.c_int32), ("eig_max_cluster", C.c_int32),
+        ("eig_fallback_unconverged", C.c_int32), ("eig_fallback_wide", C.c_int32),
     ]
 
     def as_dict(self):

@@ -188,6 +188,7 @@ struct sc<double> {
   // acc += conj(a) b
   static __device__ __forceinline__ void fmacj(double& acc, double a, double b) { acc = fma(a, b, acc); }
   static __device__ __forceinline__ double abs2(double a) { return a * a; }
+  static __device__ __forceinline__ double absv(double a) { return fabs(a); }
   static __device__ __forceinline__ double re(double a) { return a; }
   static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
   static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
@@ -202,6 +203,7 @@ struct sc<double2> {
   static __device__ __forceinline__ void fma_(double2& acc, double2 a, double2 b) { cfma(acc, a, b); }
   static __device__ __forceinline__ void fmacj(double2& acc, double2 a, double2 b) { cfmacj(acc, a, b); }
   static __device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }
+  static __device__ __forceinline__ double absv(double2 a) { return hypot(a.x, a.y); }
   static __device__ __forceinline__ double re(double2 a) { return a.x; }
   static __device__ __forceinline__ double2 mul(double2 a, double2 b) { return cmul(a, b); }
   static __device__ __forceinline__ double2 sub(double2 a, double2 b) { return csub(a, b); }
@@ -216,6 +218,7 @@ struct sc<float> {
   static __device__ __forceinline__ float conj(float a) { return a; }
   static __device__ __forceinline__ void fma_(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
   static __device__ __forceinline__ float abs2(float a) { return a * a; }
+  static __device__ __forceinline__ float absv(float a) { return fabsf(a); }
   static __device__ __forceinline__ float re(float a) { return a; }
   static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
   static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
@@ -229,6 +232,7 @@ struct sc<float2> {
   static __device__ __forceinline__ float2 conj(float2 a) { return make_float2(a.x, -a.y); }
   static __device__ __forceinline__ void fma_(float2& acc, float2 a, float2 b) { cfma(acc, a, b); }
   static __device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+  static __device__ __forceinline__ float absv(float2 a) { return hypotf(a.x, a.y); }
   static __device__ __forceinline__ float re(float2 a) { return a.x; }
   static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return cmul(a, b); }
   static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return csub(a, b); }

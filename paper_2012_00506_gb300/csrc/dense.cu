@@ -380,8 +380,10 @@ __device__ __forceinline__ void make_rot(const S* A, int m, int p, int q, Rot<S>
     return;
   }
   const S apq = A[p + (int64_t)q * m];
-  const R g = sqrt(sc<S>::abs2(apq));
-  const R tiny = sizeof(R) == 8 ? R(1e-300) : R(1e-35);
+  // |A(p,q)| without squaring: in FP32 the square of an element below ~1e-19
+  // is subnormal, and a modulus taken from it makes the rotation non-unitary
+  const R g = sc<S>::absv(apq);
+  const R tiny = sizeof(R) == 8 ? R(1e-290) : R(1e-30);
   if (!(g > tiny)) {
     r.p = -1;
     return;
@@ -745,6 +747,13 @@ EighScratch<S> plan_eigh_scratch(Arena& a, int64_t msq, int64_t mtot, int nblk) 
   w.delta = a.take<double>(nblk);
   w.shift = a.take<double>(nblk);
   w.A64 = a.take<S>(msq);
+  w.reach = a.take<double>(mtot);
+  w.reach_sorted = a.take<double>(mtot);
+  w.ccap = (int)(mtot / 2 + 1);
+  w.citems = a.take<GemmItem<S>>(w.ccap);
+  w.cdesc = a.take<SmallDesc>(w.ccap);
+  w.csweeps = a.take<int>(w.ccap);
+  w.cjscratch = a.take<double>((size_t)w.ccap * 2 * 16);
   return w;
 }
 
@@ -782,72 +791,101 @@ int small_gemm(bool conjA, const std::vector<SmallDesc>& blk, int max_m, S* cons
 // One thread block per slice; E overwrites S.  delta_out[t] = delta / max|lambda|.
 template <typename S>
 __global__ void __launch_bounds__(1024) oa_kernel(const SmallDesc* desc, S* Sall, const S* Pall, double* lamall,
-                                                  double* delta_out) {
+                                                  double* est_out, double* reach_all) {
+  // One refinement step (Ogita and Aishima, 2018) for block t, given S = V^H A V
+  // and P = V^H V of the current approximate eigenvectors V:
+  //   lambda_i = S_ii / P_ii, R = I - P, c_ij = S_ij + lambda_j R_ij,
+  //   E_ij = c_ij / (lambda_j - lambda_i)   for a separated pair (|gap| > 4 max(|c_ij|, |c_ji|)),
+  //   E_ij = R_ij / 2                       otherwise (and on the diagonal),
+  // and V <- V (I + E) (done by the caller).  A separated pair gets |E_ij| < 1/4
+  // and converges quadratically.  A pair that is not separated although it is
+  // coupled (|c_ij| > 1e-14 max|lambda|) belongs to a cluster: its coupling is
+  // left alone here and resolved by the caller.  Outputs: est = max(|E_ij| over
+  // separated pairs, |R_ij|), the size of the correction, and per column j
+  // reach_j = the largest lambda_i >= lambda_j (i != j) coupled to j without
+  // being separated, or -inf.
   const SmallDesc d = desc[blockIdx.x];
   const int m = d.m;
   S* Sm = Sall + d.off;
   const S* P = Pall + d.off;
   double* lam = lamall + d.voff;
-  __shared__ double red[3][32];
-  __shared__ double sh_delta;
-  double smax = 0.0;
+  double* reach = reach_all + d.voff;
+  __shared__ double red[2][32];
+  __shared__ double sh_l;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double lmax = 0.0;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     const double l = sc<S>::re(Sm[i + (int64_t)i * m]) / sc<S>::re(P[i + (int64_t)i * m]);
     lam[i] = l;
-    smax = fmax(smax, fabs(l));
+    lmax = fmax(lmax, fabs(l));
+  }
+  for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_down_sync(0xffffffffu, lmax, o));
+  if (lane == 0) red[0][warp] = lmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < nw; ++w) a = fmax(a, red[0][w]);
+    sh_l = a;
   }
   __syncthreads();
-  double off = 0.0, rn = 0.0;
-  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
-    const int i = (int)(e % m), j = (int)(e / m);
-    S r = sc<S>::scale(P[e], -1.0);
-    if (i == j) r = sc<S>::add(r, sc<S>::from_re(1.0));
-    rn += sc<S>::abs2(r);
-    S sd = Sm[e];
-    if (i == j) sd = sc<S>::sub(sd, sc<S>::from_re(lam[i]));
-    off += sc<S>::abs2(sd);
+  const double tiny = 1e-14 * sh_l;
+  double emax = 0.0, rmax = 0.0;
+  for (int j = warp; j < m; j += nw) {
+    const double lj = lam[j];
+    double rj = -INFINITY;
+    for (int i = lane; i < m; i += 32) {
+      const int64_t e = i + (int64_t)j * m;
+      S r = sc<S>::scale(P[e], -1.0);
+      if (i == j) r = sc<S>::add(r, sc<S>::from_re(1.0));
+      rmax = fmax(rmax, sqrt(sc<S>::abs2(r)));
+      S ev = sc<S>::scale(r, 0.5);
+      if (i != j) {
+        // c_ij and |c_ji| = |S_ij + lambda_i R_ij|: the pair is classified on the
+        // larger of the two so that (i,j) and (j,i) always get the same treatment
+        // (E + E^H then equals R, which keeps the orthogonality correction exact)
+        const double li = lam[i];
+        const S c = sc<S>::add(Sm[e], sc<S>::scale(r, lj));
+        const double ca = fmax(sc<S>::absv(c), sc<S>::absv(sc<S>::add(Sm[e], sc<S>::scale(r, li))));
+        const double gap = lj - li;
+        if (ca > tiny) {
+          if (fabs(gap) > 4.0 * ca) {
+            ev = sc<S>::scale(c, 1.0 / gap);
+            emax = fmax(emax, sqrt(sc<S>::abs2(ev)));
+          } else if (li >= lj) {
+            rj = fmax(rj, li);
+          }
+        }
+      }
+      Sm[e] = ev;
+    }
+    for (int o = 16; o > 0; o >>= 1) rj = fmax(rj, __shfl_down_sync(0xffffffffu, rj, o));
+    if (lane == 0) reach[j] = rj;
   }
   for (int o = 16; o > 0; o >>= 1) {
-    off += __shfl_down_sync(0xffffffffu, off, o);
-    rn += __shfl_down_sync(0xffffffffu, rn, o);
-    smax = fmax(smax, __shfl_down_sync(0xffffffffu, smax, o));
+    emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, o));
+    rmax = fmax(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
   }
-  if ((threadIdx.x & 31) == 0) {
-    red[0][threadIdx.x >> 5] = off;
-    red[1][threadIdx.x >> 5] = rn;
-    red[2][threadIdx.x >> 5] = smax;
+  __syncthreads();
+  if (lane == 0) {
+    red[0][warp] = emax;
+    red[1][warp] = rmax;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a += red[0][w];
-      b += red[1][w];
-      c = fmax(c, red[2][w]);
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      a = fmax(a, red[0][w]);
+      b = fmax(b, red[1][w]);
     }
-    sh_delta = 2.0 * (sqrt(a) + c * sqrt(b));
-    delta_out[blockIdx.x] = c > 0.0 ? sh_delta / c : 0.0;
-  }
-  __syncthreads();
-  const double delta = sh_delta;
-  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
-    const int i = (int)(e % m), j = (int)(e / m);
-    S r = sc<S>::scale(P[e], -1.0);
-    if (i == j) r = sc<S>::add(r, sc<S>::from_re(1.0));
-    S ev;
-    const double gap = lam[j] - lam[i];
-    if (i != j && fabs(gap) > delta)
-      ev = sc<S>::scale(sc<S>::add(Sm[e], sc<S>::scale(r, lam[j])), 1.0 / gap);
-    else
-      ev = sc<S>::scale(r, 0.5);
-    Sm[e] = ev;
+    est_out[blockIdx.x] = fmax(a, b);
   }
 }
 
 // W[:, rank(i)] = V[:, i] * phase, eigenvalues sorted ascending (rank sort, ties by index).
 template <typename S>
 __global__ void __launch_bounds__(1024) sort_phase_kernel(const SmallDesc* desc, const S* Vall, const double* lam_in,
-                                                          double* lam_out, S* Wall) {
+                                                          double* lam_out, S* Wall, const double* aux_in = nullptr,
+                                                          double* aux_out = nullptr) {
   const SmallDesc d = desc[blockIdx.x];
   const int m = d.m;
   const S* V = Vall + d.off;
@@ -885,30 +923,79 @@ __global__ void __launch_bounds__(1024) sort_phase_kernel(const SmallDesc* desc,
     if (nb > 0.0) ph = sc<S>::scale(sc<S>::conj(v[kb]), 1.0 / nb);
     S* w = Wm + (int64_t)rank * m;
     for (int k = lane; k < m; k += 32) w[k] = (k == kb) ? sc<S>::from_re(nb) : sc<S>::mul(v[k], ph);
-    if (lane == 0) lo[rank] = li[i];
+    if (lane == 0) {
+      lo[rank] = li[i];
+      if (aux_in) aux_out[d.voff + rank] = aux_in[d.voff + i];
+    }
   }
 }
 
-// blocks whose refined eigenvalues still contain a pair closer than delta (an
-// unresolved cluster) with delta above 1e-12 max|lambda|
+// Rayleigh-Ritz on clusters of eigenvector columns.  Cluster q covers the c
+// columns i0..i0+c-1 of an m x m block at element offset `off` (eigenvalues at
+// voff): H = Vc^H A Vc (c x c, FP64), FP64 Jacobi H = Wc diag(mu) Wc^H,
+// Vc <- Vc Wc, lambda(i0..) <- mu (ascending).  All clusters are batched.
 template <typename S>
-__global__ void cluster_check_kernel(const SmallDesc* desc, const double* lam, const double* delta_rel, int* flag) {
-  const SmallDesc d = desc[blockIdx.x];
-  const double* l = lam + d.voff;  // sorted
-  double lmax = 0.0;
-  for (int i = 0; i < d.m; ++i) lmax = fmax(lmax, fabs(l[i]));
-  const double del = delta_rel[blockIdx.x] * lmax;
-  int bad = 0;
-  if (delta_rel[blockIdx.x] > 1e-12)
-    for (int i = threadIdx.x; i + 1 < d.m; i += blockDim.x) bad |= (l[i + 1] - l[i]) <= del;
-  bad = __syncthreads_or(bad);
-  if (threadIdx.x == 0) flag[blockIdx.x] = bad;
+static int resolve_clusters(const std::vector<ClusterRef>& cl, const S* A, double* lam, S* W,
+                            const EighScratch<S>& w, cudaStream_t st) {
+  const int nq = (int)cl.size();
+  if (nq > w.ccap) return PDESHEP_WORKSPACE_TOO_SMALL;
+  S one, zero;
+  if constexpr (std::is_same<S, double>::value) {
+    one = 1.0;
+    zero = 0.0;
+  } else {
+    one = make_double2(1.0, 0.0);
+    zero = make_double2(0.0, 0.0);
+  }
+  int mx_m = 0, mx_c = 0;
+  for (const ClusterRef& q : cl) {
+    mx_m = std::max(mx_m, q.m);
+    mx_c = std::max(mx_c, q.c);
+  }
+  std::vector<GemmItem<S>> it(nq);
+  auto col = [&](const ClusterRef& q) { return q.off + (int64_t)q.i0 * q.m; };
+  // T = A Vc  (m x c at the cluster's columns of T)
+  for (int q = 0; q < nq; ++q) {
+    const ClusterRef& c = cl[q];
+    it[q] = GemmItem<S>{A + c.off, W + col(c), w.T + col(c), c.m, c.c, c.m, c.m, c.m, c.m, 0};
+  }
+  PD_CK(cudaMemcpyAsync(w.citems, it.data(), sizeof(GemmItem<S>) * nq, cudaMemcpyHostToDevice, st));
+  PD_TRY(launch_gemm<S>(false, nq, w.citems, mx_m, mx_c, mx_m, one, zero, 1, nullptr, 0, st, 0, 0));
+  // H = Vc^H T  (c x c, leading dimension c, in A64 at the cluster's offset)
+  for (int q = 0; q < nq; ++q) {
+    const ClusterRef& c = cl[q];
+    it[q] = GemmItem<S>{W + col(c), w.T + col(c), w.A64 + col(c), c.c, c.c, c.m, c.m, c.m, c.c, 0};
+  }
+  PD_CK(cudaMemcpyAsync(w.citems, it.data(), sizeof(GemmItem<S>) * nq, cudaMemcpyHostToDevice, st));
+  PD_TRY(launch_gemm<S>(true, nq, w.citems, mx_c, mx_c, mx_m, one, zero, 1, nullptr, 0, st, 1, 0));
+  std::vector<SmallDesc> cd(nq);
+  for (int q = 0; q < nq; ++q) cd[q] = SmallDesc{col(cl[q]), cl[q].voff + cl[q].i0, cl[q].c, 0};
+  PD_CK(cudaMemcpyAsync(w.cdesc, cd.data(), sizeof(SmallDesc) * nq, cudaMemcpyHostToDevice, st));
+  PD_TRY(launch_jacobi<S>(nq, w.cdesc, mx_c, w.A64, w.Vw, w.W64, w.lam32, 1e-14, 60, w.csweeps, w.cjscratch, st));
+  // Vc Wc -> Vd, then back into W; eigenvalues back into lam
+  for (int q = 0; q < nq; ++q) {
+    const ClusterRef& c = cl[q];
+    it[q] = GemmItem<S>{W + col(c), w.W64 + col(c), w.Vd + col(c), c.m, c.c, c.c, c.m, c.c, c.m, 0};
+  }
+  PD_CK(cudaMemcpyAsync(w.citems, it.data(), sizeof(GemmItem<S>) * nq, cudaMemcpyHostToDevice, st));
+  PD_TRY(launch_gemm<S>(false, nq, w.citems, mx_m, mx_c, mx_c, one, zero, 1, nullptr, 0, st, 0, 0));
+  for (const ClusterRef& c : cl) {
+    PD_CK(cudaMemcpyAsync(W + col(c), w.Vd + col(c), sizeof(S) * (size_t)c.m * c.c, cudaMemcpyDeviceToDevice, st));
+    PD_CK(cudaMemcpyAsync(lam + c.voff + c.i0, w.lam32 + c.voff + c.i0, sizeof(double) * c.c,
+                          cudaMemcpyDeviceToDevice, st));
+  }
+  std::vector<int> sw(nq);
+  PD_CK(cudaMemcpyAsync(sw.data(), w.csweeps, sizeof(int) * nq, cudaMemcpyDeviceToHost, st));
+  PD_CK(cudaStreamSynchronize(st));
+  for (int v : sw)
+    if (v < 0) return PDESHEP_EIG_NOT_CONVERGED;
+  return 0;
 }
 
 template <typename S>
 int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int max_m, S* A, double* lam, S* W,
                const EighScratch<S>& w, cudaStream_t st, int* fp64_sweeps_out, const unsigned char* h_fp32,
-               int* fp32_sweeps_out) {
+               int* fp32_sweeps_out, EighReport* rep) {
   using L = typename lowp<S>::type;
   if (nblk <= 0) return 0;
   std::vector<SmallDesc> all(h_desc, h_desc + nblk), sub, rest;
@@ -946,62 +1033,121 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
     identity_kernel<S><<<1, 256, 0, st>>>(w.Vd + b.off, b.m);
     PD_CK_LAUNCH();
   }
-  // FP64 refinement of V: each step roughly squares the relative error; stop after the
-  // step whose input error estimate delta/max|lambda| was below 1e-7 (at most 6 steps)
+  // FP64 refinement of V (kept in Vd): each step roughly squares the error of the
+  // separated pairs.  A block leaves the batch after the step whose correction was
+  // below kRefineTol (what remains is of the order of its square); at most
+  // kRefineSteps steps.
   S* V = w.Vd;
   S* Vn = w.Vw;
-  std::vector<double> drel(nblk);
-  for (int it = 0; it < 6; ++it) {
+  std::vector<double> drel(nblk, 1.0), est(nblk);
+  std::vector<int> act(nblk);
+  for (int t = 0; t < nblk; ++t) act[t] = t;
+  for (int it = 0; it < kRefineSteps && !act.empty(); ++it) {
+    const int na = (int)act.size();
+    std::vector<SmallDesc> sub_d(na);
+    for (int q = 0; q < na; ++q) sub_d[q] = all[act[q]];
+    const SmallDesc* dd = d_desc;
+    if (na != nblk) {
+      PD_CK(cudaMemcpyAsync(w.dsub, sub_d.data(), sizeof(SmallDesc) * na, cudaMemcpyHostToDevice, st));
+      dd = w.dsub;
+    }
     {
       S* abc[3] = {A, V, w.T};  // T = A V
-      PD_TRY(small_gemm<S>(false, all, max_m, abc, 0, 0, w.items, st));
+      PD_TRY(small_gemm<S>(false, sub_d, max_m, abc, 0, 0, w.items, st));
     }
     {
       S* abc[3] = {V, w.T, w.W64};  // S = V^H A V  (in W64)
-      PD_TRY(small_gemm<S>(true, all, max_m, abc, 1, 0, w.items, st));
+      PD_TRY(small_gemm<S>(true, sub_d, max_m, abc, 1, 0, w.items, st));
     }
     {
       S* abc[3] = {V, V, w.T};  // P = V^H V  (in T)
-      PD_TRY(small_gemm<S>(true, all, max_m, abc, 1, 0, w.items, st));
+      PD_TRY(small_gemm<S>(true, sub_d, max_m, abc, 1, 0, w.items, st));
     }
-    oa_kernel<S><<<nblk, 1024, 0, st>>>(d_desc, w.W64, w.T, w.lam32, w.delta);
+    oa_kernel<S><<<na, 1024, 0, st>>>(dd, w.W64, w.T, w.lam32, w.delta, w.reach);
     PD_CK_LAUNCH();
-    for (auto& b : all) PD_CK(cudaMemcpyAsync(Vn + b.off, V + b.off, sizeof(S) * (size_t)b.m * b.m,
-                                              cudaMemcpyDeviceToDevice, st));
+    for (auto& b : sub_d)
+      PD_CK(cudaMemcpyAsync(Vn + b.off, V + b.off, sizeof(S) * (size_t)b.m * b.m, cudaMemcpyDeviceToDevice, st));
     {
-      // Vn = V + V E
-      std::vector<GemmItem<S>> it2(nblk);
-      for (int t = 0; t < nblk; ++t) {
-        const int m = all[t].m;
-        const int64_t o = all[t].off;
-        it2[t] = GemmItem<S>{V + o, w.W64 + o, Vn + o, m, m, m, m, m, m, 0};
+      // Vn = V + V E, then back into V
+      std::vector<GemmItem<S>> it2(na);
+      for (int q = 0; q < na; ++q) {
+        const int m = sub_d[q].m;
+        const int64_t o = sub_d[q].off;
+        it2[q] = GemmItem<S>{V + o, w.W64 + o, Vn + o, m, m, m, m, m, m, 0};
       }
-      PD_CK(cudaMemcpyAsync(w.items, it2.data(), sizeof(GemmItem<S>) * nblk, cudaMemcpyHostToDevice, st));
-      PD_TRY(launch_gemm<S>(false, nblk, w.items, max_m, max_m, max_m, one, one, 1, nullptr, 0, st, 0, 0));
+      PD_CK(cudaMemcpyAsync(w.items, it2.data(), sizeof(GemmItem<S>) * na, cudaMemcpyHostToDevice, st));
+      PD_TRY(launch_gemm<S>(false, na, w.items, max_m, max_m, max_m, one, one, 1, nullptr, 0, st, 0, 0));
     }
-    std::swap(V, Vn);
-    PD_CK(cudaMemcpyAsync(drel.data(), w.delta, sizeof(double) * nblk, cudaMemcpyDeviceToHost, st));
+    for (auto& b : sub_d)
+      PD_CK(cudaMemcpyAsync(V + b.off, Vn + b.off, sizeof(S) * (size_t)b.m * b.m, cudaMemcpyDeviceToDevice, st));
+    PD_CK(cudaMemcpyAsync(est.data(), w.delta, sizeof(double) * na, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
-    double dmax = 0.0;
-    for (double v : drel) dmax = std::max(dmax, v);
-    if (dmax < 1e-7) break;
+    if (rep) rep->refine_steps += 1;
+    std::vector<int> next;
+    for (int q = 0; q < na; ++q) {
+      drel[act[q]] = est[q];
+      if (!(est[q] < kRefineTol)) next.push_back(act[q]);
+    }
+    act.swap(next);
   }
-  sort_phase_kernel<S><<<nblk, 1024, 0, st>>>(d_desc, V, w.lam32, lam, W);
+  sort_phase_kernel<S><<<nblk, 1024, 0, st>>>(d_desc, V, w.lam32, lam, W, w.reach, w.reach_sorted);
   PD_CK_LAUNCH();
-  cluster_check_kernel<S><<<nblk, 256, 0, st>>>(d_desc, lam, w.delta, w.sweeps);
-  PD_CK_LAUNCH();
-  std::vector<int> flag(nblk, 0);
-  PD_CK(cudaMemcpyAsync(flag.data(), w.sweeps, sizeof(int) * nblk, cudaMemcpyDeviceToHost, st));
+  // Clusters: runs of sorted eigenvalues tied together by pairs that the
+  // refinement could not separate (a run extends while the next eigenvalue is
+  // within the reach of the run).  Their mutual couplings were left alone; a
+  // Rayleigh-Ritz step on each run's own columns resolves them (the cluster
+  // treatment of Ogita and Aishima's refinement for clustered eigenvalues):
+  // H = Vc^H A Vc, H = Wc diag(mu) Wc^H by FP64 Jacobi, Vc <- Vc Wc, lambda <- mu.
+  // Blocks whose refinement did not converge, or with a run wider than
+  // kMaxCluster columns, are redone by the robust path below.
+  int64_t lam_len = 0;
+  for (auto& b : all) lam_len = std::max<int64_t>(lam_len, b.voff + b.m);
+  std::vector<double> lam_h(lam_len), reach_h(lam_len);
+  PD_CK(cudaMemcpyAsync(lam_h.data(), lam, sizeof(double) * lam_len, cudaMemcpyDeviceToHost, st));
+  PD_CK(cudaMemcpyAsync(reach_h.data(), w.reach_sorted, sizeof(double) * lam_len, cudaMemcpyDeviceToHost, st));
   PD_CK(cudaStreamSynchronize(st));
-  // Blocks where the refinement did not converge (last input error >= 1e-7) or left
-  // an unresolved cluster are redone robustly: start vectors (V32 orthonormalised in
-  // FP64, or I), H = V^H A V, FP64 Jacobi on H, W = V W64.
+  struct Cl {
+    int t, i0, c;
+  };
+  std::vector<Cl> cl;
   std::vector<SmallDesc> fb, fb32;
   std::vector<int> fbidx;
   for (int t = 0; t < nblk; ++t) {
-    if (!(flag[t] || drel[t] >= 1e-7)) continue;
-    fb.push_back(all[t]);
-    fbidx.push_back(t);
+    const SmallDesc& b = all[t];
+    bool bad = !(drel[t] < kRefineTol);
+    if (bad && rep) rep->fallback_unconverged += 1;
+    std::vector<Cl> mine;
+    for (int i = 0; i < b.m && !bad;) {
+      int j = i + 1;
+      double r = reach_h[b.voff + i];
+      while (j < b.m && lam_h[b.voff + j] <= r) {
+        r = std::max(r, reach_h[b.voff + j]);
+        ++j;
+      }
+      if (j - i > kMaxCluster) {
+        bad = true;
+        if (rep) rep->fallback_wide += 1;
+      } else if (j - i > 1) {
+        mine.push_back({t, i, j - i});
+      }
+      i = j;
+    }
+    if (!bad && rep)
+      for (const Cl& q : mine) {
+        rep->clusters += 1;
+        rep->max_cluster = std::max(rep->max_cluster, q.c);
+      }
+    if (bad) {
+      fb.push_back(b);
+      fbidx.push_back(t);
+    } else {
+      cl.insert(cl.end(), mine.begin(), mine.end());
+    }
+  }
+  if (!cl.empty()) {
+    std::vector<ClusterRef> refs;
+    for (const Cl& q : cl) refs.push_back({all[q.t].off, all[q.t].voff, all[q.t].m, q.i0, q.c});
+    PD_TRY(resolve_clusters<S>(refs, A, lam, W, w, st));
   }
   const int nfb = (int)fb.size();
   if (nfb) {
@@ -1076,9 +1222,11 @@ template int small_gemm<double2>(bool, const std::vector<SmallDesc>&, int, doubl
 template EighScratch<double> plan_eigh_scratch<double>(Arena&, int64_t, int64_t, int);
 template EighScratch<double2> plan_eigh_scratch<double2>(Arena&, int64_t, int64_t, int);
 template int eigh_mixed<double>(int, const SmallDesc*, const SmallDesc*, int, double*, double*, double*,
-                                const EighScratch<double>&, cudaStream_t, int*, const unsigned char*, int*);
+                                const EighScratch<double>&, cudaStream_t, int*, const unsigned char*, int*,
+                                EighReport*);
 template int eigh_mixed<double2>(int, const SmallDesc*, const SmallDesc*, int, double2*, double*, double2*,
-                                 const EighScratch<double2>&, cudaStream_t, int*, const unsigned char*, int*);
+                                 const EighScratch<double2>&, cudaStream_t, int*, const unsigned char*, int*,
+                                 EighReport*);
 template int launch_gemm<double>(bool, int, const GemmItem<double>*, int, int, int, double, double, int,
                                  double*, int64_t, cudaStream_t, int, int);
 template int launch_gemm<double2>(bool, int, const GemmItem<double2>*, int, int, int, double2, double2, int,

@@ -82,7 +82,22 @@ struct EighScratch {
   double* delta;
   double* shift;
   S* A64;
+  double* reach;            // per column: reach of the refinement's unseparated couplings
+  double* reach_sorted;     // the same in ascending eigenvalue order
+  int ccap;                 // capacity of the cluster arrays below
+  GemmItem<S>* citems;
+  SmallDesc* cdesc;
+  int* csweeps;
+  double* cjscratch;
 };
+// columns i0..i0+c-1 of the m x m block at element offset off (eigenvalues at voff)
+struct ClusterRef {
+  int64_t off, voff;
+  int m, i0, c;
+};
+constexpr int kMaxCluster = 64;
+constexpr int kRefineSteps = 10;
+constexpr double kRefineTol = 1e-8;
 template <typename S>
 EighScratch<S> plan_eigh_scratch(Arena& a, int64_t msq, int64_t mtot, int nblk);
 // C_t = op(A_t) B_t for m x m blocks at each block's offset (abc = {A, B, C} bases).
@@ -92,10 +107,14 @@ int small_gemm(bool conjA, const std::vector<SmallDesc>& blk, int max_m, S* cons
 
 // h_fp32[t] (optional, default all): run the FP32 pre-rotation on block t; blocks that are
 // already nearly diagonal skip it and go straight to the FP64 sweeps.
+// what the mixed eigensolver did (accumulated by the caller)
+struct EighReport {
+  int refine_steps = 0, clusters = 0, max_cluster = 0, fallback_unconverged = 0, fallback_wide = 0;
+};
 template <typename S>
 int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int max_m, S* A, double* lam, S* W,
                const EighScratch<S>& w, cudaStream_t st, int* fp64_sweeps_out = nullptr,
-               const unsigned char* h_fp32 = nullptr, int* fp32_sweeps_out = nullptr);
+               const unsigned char* h_fp32 = nullptr, int* fp32_sweeps_out = nullptr, EighReport* rep = nullptr);
 
 // Y = B X for the Hermitian band (lower storage), X, Y n x ncols (ld n).
 template <typename S>

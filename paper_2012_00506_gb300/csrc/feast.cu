@@ -32,6 +32,9 @@ namespace pdeshep {
 
 // from other translation units
 size_t inertia_ws_bytes(int b, int cplx, int nsigma);
+int inertia_counts_async(int64_t n, int b, int cplx, const void* band, int64_t ldab, int nsigma,
+                         const double* h_sigma, void* work, size_t wbytes, cudaStream_t st,
+                         const int64_t** d_neg, const int** d_bad);
 int inertia_counts(int64_t n, int b, int cplx, const void* band, int64_t ldab, int nsigma,
                    const double* h_sigma, int64_t* h_neg, double* d_piv, void* work, size_t wbytes,
                    cudaStream_t st, bool* nonfinite_out);
@@ -415,8 +418,44 @@ struct KTimer {
     grp.clear();
     return 0;
   }
+  // an interval measured elsewhere (e.g. on a side stream)
+  void add(int g, double t_ms, long long launches, double flops) {
+    if (!on) return;
+    ms[g] += t_ms;
+    nl[g] += launches;
+    fl[g] += flops;
+  }
   ~KTimer() {
     for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+// A non-blocking stream forked from the caller's stream by an event; `done`
+// marks the end of the work enqueued on it.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t forked = nullptr, done = nullptr, t0 = nullptr, t1 = nullptr;
+  int fork(cudaStream_t st) {
+    PD_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    PD_CK(cudaEventCreateWithFlags(&forked, cudaEventDisableTiming));
+    PD_CK(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    PD_CK(cudaEventCreate(&t0));
+    PD_CK(cudaEventCreate(&t1));
+    PD_CK(cudaEventRecord(forked, st));
+    PD_CK(cudaStreamWaitEvent(s, forked, 0));
+    return 0;
+  }
+  int join(cudaStream_t) {
+    PD_CK(cudaEventRecord(done, s));
+    return 0;
+  }
+  ~SideStream() {
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+    for (cudaEvent_t e : {forked, done, t0, t1})
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -685,8 +724,14 @@ struct FeastRun : Feast<S, C> {
     std::vector<unsigned char> fp32(na);
     for (int a = 0; a < na; ++a) fp32[a] = orat[a] > 1e-6 ? 1 : 0;  // off(A~) > 1e-3 ||A~||_F
     PD_CK(cudaMemsetAsync(p.sweeps32, 0, sizeof(int) * K, st));
+    EighReport rep;
     PD_TRY(eigh_mixed<S>(na, p.d_small, this->h_small.data(), mm, G, p.lam, W, this->eig, st, p.sweeps,
-                         fp32.data(), p.sweeps32));
+                         fp32.data(), p.sweeps32, &rep));
+    stats.eig_refine_steps += rep.refine_steps;
+    stats.eig_clusters += rep.clusters;
+    stats.eig_max_cluster = std::max(stats.eig_max_cluster, rep.max_cluster);
+    stats.eig_fallback_unconverged += rep.fallback_unconverged;
+    stats.eig_fallback_wide += rep.fallback_wide;
     PD_TRY(this->kt.end(0.0));
     PD_TRY(small_mm(false, I, W, T, 0, 0));          // R^{-1} W
     PD_TRY(gemm(1, (S*)p.Q, T, (S*)p.Xt));           // X = Q R^{-1} W
@@ -924,35 +969,51 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   PD_CK(cudaEventCreate(&e0));
   PD_CK(cudaEventCreate(&e1));
   PD_CK(cudaEventRecord(e0, st));
-  // exact counts by inertia at every boundary
   F.bounds.assign(h_bounds, h_bounds + K + 1);
-  std::vector<int64_t> neg(K + 1);
-  bool bad = false;
-  PD_TRY(F.kt.begin(PDESHEP_KG_INERTIA));
-  PD_TRY(inertia_counts(n, b, cplx, band, ldab, K + 1, h_bounds, neg.data(), nullptr, F.p.inertia_ws,
-                        F.p.inertia_bytes, st, &bad));
-  PD_TRY(F.kt.end((K + 1) * (double)n * b * b * (cplx ? 4.0 : 1.0)));
-  if (bad) return PDESHEP_NONFINITE_INPUT;
-  F.counts.assign(K, 0);
-  F.nconv.assign(K, 0);
-  F.iters.assign(K, 0);
-  for (int s = 0; s < K; ++s) {
-    F.counts[s] = (int)(neg[s + 1] - neg[s]);
-    if (h_counts) h_counts[s] = F.counts[s];
-  }
-  for (int s = 0; s < K; ++s)
-    if (F.m0[s] < F.counts[s]) return PDESHEP_COUNT_MISMATCH;
-  {
-    float ms = 0;
-    PD_CK(cudaEventRecord(e1, st));
-    PD_CK(cudaEventSynchronize(e1));
-    PD_CK(cudaEventElapsedTime(&ms, e0, e1));
-    F.stats.ms_inertia = ms;
-  }
-  // ||B||_2
+  // ||B||_2 (synchronous; uses the inertia workspace before the counts do)
   F.bnorm = o->bnorm;
   if (!(F.bnorm > 0.0))
     PD_TRY(spectral_norm(n, b, cplx, band, ldab, 1e-6, &F.bnorm, F.p.inertia_ws, F.p.inertia_bytes, st));
+  // Exact counts by inertia at every boundary (Section 3.2).  The LDL^T sweeps
+  // occupy one SM per boundary, so they run on a side stream next to the first
+  // filter pass and are read back with the first Rayleigh-Ritz results; a slice
+  // whose subspace is smaller than its count is reported after that pass.
+  SideStream side;
+  PD_TRY(side.fork(st));
+  const int64_t* d_neg = nullptr;
+  const int* d_bad = nullptr;
+  PD_CK(cudaEventRecord(side.t0, side.s));
+  PD_TRY(inertia_counts_async(n, b, cplx, band, ldab, K + 1, h_bounds, F.p.inertia_ws, F.p.inertia_bytes, side.s,
+                              &d_neg, &d_bad));
+  PD_CK(cudaEventRecord(side.t1, side.s));
+  PD_TRY(side.join(st));
+  const long long inertia_launches = 2;
+  F.counts.assign(K, 0);
+  F.nconv.assign(K, 0);
+  F.iters.assign(K, 0);
+  bool counts_ready = false;
+  auto read_counts = [&]() -> int {
+    if (counts_ready) return 0;
+    std::vector<int64_t> neg(K + 1);
+    int bad = 0;
+    PD_CK(cudaStreamWaitEvent(st, side.done, 0));
+    PD_CK(cudaMemcpyAsync(neg.data(), d_neg, sizeof(int64_t) * (K + 1), cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaStreamSynchronize(st));
+    counts_ready = true;
+    float ms = 0;
+    PD_CK(cudaEventElapsedTime(&ms, side.t0, side.t1));
+    F.stats.ms_inertia = ms;
+    F.kt.add(PDESHEP_KG_INERTIA, ms, inertia_launches, (K + 1) * (double)n * b * b * (cplx ? 4.0 : 1.0));
+    if (bad) return PDESHEP_NONFINITE_INPUT;
+    for (int s = 0; s < K; ++s) {
+      F.counts[s] = (int)(neg[s + 1] - neg[s]);
+      if (h_counts) h_counts[s] = F.counts[s];
+    }
+    for (int s = 0; s < K; ++s)
+      if (F.m0[s] < F.counts[s]) return PDESHEP_COUNT_MISMATCH;
+    return 0;
+  };
   // quadrature per slice
   F.zh.resize((size_t)K * ne);
   F.wh.resize((size_t)K * ne);
@@ -1011,10 +1072,18 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   int it = 1;
   for (; it <= o->max_iter && !F.active.empty(); ++it) {
     F.mode = (refine && it > 1) ? 1 : 0;
-    PD_TRY(timed(ms_filter, [&]() { return F.filter(); }));
-    PD_TRY(timed(ms_rr, [&]() { return F.rr(); }));
+    // a failure of the counts (non-finite band, subspace too small) takes precedence
+    auto first_error = [&](int r) -> int {
+      if (!r) return 0;
+      const int rc = read_counts();
+      return rc ? rc : r;
+    };
+    PD_TRY(first_error(timed(ms_filter, [&]() { return F.filter(); })));
+    PD_TRY(first_error(timed(ms_rr, [&]() { return F.rr(); })));
+    PD_TRY(read_counts());
     update_active(it);
   }
+  PD_TRY(read_counts());
   if (!F.active.empty()) status = PDESHEP_NOT_CONVERGED;
   // outputs for every slice
   F.active.clear();
@@ -1048,7 +1117,7 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
     for (int s = 0; s < K; ++s) F.stats.iterations = std::max(F.stats.iterations, F.iters[s]);
     F.stats.ms_solve = ms_filter;
     F.stats.ms_rr = ms_rr;
-    F.stats.ms_total = F.stats.ms_inertia + ms_filter + ms_rr;
+    F.stats.ms_total = ms_filter + ms_rr;  // the counts overlap the first filter pass
     F.stats.max_residual = maxres;
     PD_TRY(F.kt.collect());
     for (int gi = 0; gi < PDESHEP_KG_COUNT; ++gi) {

@@ -265,6 +265,23 @@ size_t inertia_ws_bytes(int b, int cplx, int nsigma) {
   return a.used();
 }
 
+// Asynchronous counts: everything is enqueued on st; the counts (nsigma int64)
+// and the non-finite flag (int) stay in the workspace at *d_neg / *d_bad.
+int inertia_counts_async(int64_t n, int b, int cplx, const void* band, int64_t ldab, int nsigma,
+                         const double* h_sigma, void* work, size_t wbytes, cudaStream_t st,
+                         const int64_t** d_neg, const int** d_bad) {
+  Arena a(work, wbytes);
+  InertiaWs w = plan_inertia(a, b, cplx, nsigma);
+  if (!a.fits()) return PDESHEP_WORKSPACE_TOO_SMALL;
+  PD_TRY(launch_band_amax(n, b, cplx, band, ldab, w.amax, w.nonfinite, st));
+  PD_CK(cudaMemcpyAsync(w.sigma, h_sigma, sizeof(double) * nsigma, cudaMemcpyHostToDevice, st));
+  PD_TRY(launch_inertia(n, b, cplx, band, ldab, nsigma, w.sigma, w.amax, w.neg, nullptr, w.gwin,
+                        w.gwin_stride, st));
+  *d_neg = w.neg;
+  *d_bad = w.nonfinite;
+  return 0;
+}
+
 // Synchronous helper used by the host-side drivers (bisection, slicing).
 int inertia_counts(int64_t n, int b, int cplx, const void* band, int64_t ldab, int nsigma,
                    const double* h_sigma, int64_t* h_neg, double* d_piv, void* work, size_t wbytes,

@@ -115,3 +115,25 @@ def test_streaming_waves_match_resident(device):
     assert r1.status == r2.status == 0
     assert r2.stats["waves"] > r1.stats["waves"]
     assert np.max(np.abs(r1.evals.cpu().numpy() - r2.evals.cpu().numpy())[:15]) < 1e-12
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_mixed_eigensolver_needs_no_fallback(device, cplx):
+    """The FP32 Jacobi start plus FP64 refinement of the Rayleigh-Ritz eigenproblems
+    converges on its own on a random band (every block refined, none sent to the FP64
+    Jacobi path), and the slices still match the exact counts."""
+    import paper_2012_00506_gb300 as pk
+    n, b = 1500, 12
+    ab = synth.random_band(n, b, 8080 + cplx, cplx)
+    ks = [100, 260, 420]
+    bounds = _bounds(ab, ks)
+    m0 = [oracle.m0_rule(ks[i + 1] - ks[i]) for i in range(2)]
+    X0 = synth.random_subspace(n, int(sum(m0)), 3, cplx)
+    r = pk.band_slice(to_dev(ab, device), bounds, m0, block_to_dev(X0, device), precision=pk.MIXED,
+                      bnorm=oracle.spectral_norm(ab), max_iter=30)
+    assert r.status == 0
+    assert list(r.nfound) == [ks[1] - ks[0], ks[2] - ks[1]]
+    st = r.stats
+    assert st["eig_refine_steps"] > 0
+    assert st["eig_fallback_unconverged"] == 0 and st["eig_fallback_wide"] == 0, st
+    assert st["jacobi_sweeps64"] == 0
