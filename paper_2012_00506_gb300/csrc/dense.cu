@@ -103,6 +103,158 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmItem<S>* items, S a
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same products in float-float arithmetic on the FP32 pipes.  GB300 runs
+// FP32 at 64 times its FP64 rate, so an FP64 operand is split into a pair of
+// floats (hi = fl(v), lo = fl(v - hi): about 48 significant bits) and every
+// product is accumulated error-free (exact product by an FMA, exact sum by
+// Knuth's two-sum) into a (hi, lo) accumulator; the cross terms hi*lo enter
+// the low word and lo*lo is dropped.  Relative accuracy of a length-K dot
+// product is about 2^-48 sqrt(K) in practice, far inside the 1e-10 residual
+// target; the exponent range is FP32's (operands above ~1e-19 in magnitude
+// keep full precision).  Tiles: 64 x 64 outputs per CTA, 4 x 4 per thread,
+// k-steps of 16 staged in shared memory as (hi, lo) pairs.
+// ---------------------------------------------------------------------------
+constexpr int FBM = 64, FBN = 64, FBK = 16;
+
+template <typename S>
+struct ffv;  // a split operand in shared memory
+template <>
+struct ffv<double> {
+  using type = float2;  // (hi, lo)
+};
+template <>
+struct ffv<double2> {
+  using type = float4;  // (re hi, re lo, im hi, im lo)
+};
+
+__device__ __forceinline__ float2 ff_split(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+__device__ __forceinline__ void ff_load(double v, bool conj, float2& o) {
+  (void)conj;
+  o = ff_split(v);
+}
+__device__ __forceinline__ void ff_load(double2 v, bool conj, float4& o) {
+  const float2 a = ff_split(v.x), b = ff_split(conj ? -v.y : v.y);
+  o = make_float4(a.x, a.y, b.x, b.y);
+}
+
+// (h, l) += x * y exactly up to the dropped x_lo * y_lo and the rounding of l
+__device__ __forceinline__ void ff_mac(float& h, float& l, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  const float e = fmaf(xh, yh, -p);
+  const float c = fmaf(xh, yl, xl * yh);
+  const float s = h + p;
+  const float bb = s - h;
+  const float t = (h - (s - bb)) + (p - bb);
+  h = s;
+  l += t + (e + c);
+}
+
+struct ffacc1 {
+  float h, l;
+};
+struct ffacc2 {
+  float rh, rl, ih, il;
+};
+__device__ __forceinline__ void ff_fma(ffacc1& a, float2 x, float2 y) { ff_mac(a.h, a.l, x.x, x.y, y.x, y.y); }
+__device__ __forceinline__ void ff_fma(ffacc2& a, float4 x, float4 y) {
+  // (xr + i xi)(yr + i yi) = (xr yr - xi yi) + i (xr yi + xi yr)
+  ff_mac(a.rh, a.rl, x.x, x.y, y.x, y.y);
+  ff_mac(a.rh, a.rl, -x.z, -x.w, y.z, y.w);
+  ff_mac(a.ih, a.il, x.x, x.y, y.z, y.w);
+  ff_mac(a.ih, a.il, x.z, x.w, y.x, y.y);
+}
+__device__ __forceinline__ double ff_val(const ffacc1& a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ double2 ff_val(const ffacc2& a) {
+  return make_double2((double)a.rh + (double)a.rl, (double)a.ih + (double)a.il);
+}
+
+template <typename S, bool CA>
+__global__ void __launch_bounds__(256) ffgemm_kernel(const GemmItem<S>* items, S alpha, S beta, int splits,
+                                                    S* part, int64_t part_stride, int herm, int triB) {
+  using V = typename ffv<S>::type;
+  using ACC = typename std::conditional<std::is_same<S, double2>::value, ffacc2, ffacc1>::type;
+  __shared__ V As[FBK][FBM];
+  __shared__ V Bs[FBK][FBN];
+  const GemmItem<S> it = items[blockIdx.y];
+  const int tm = (it.m + FBM - 1) / FBM, tn = (it.n + FBN - 1) / FBN;
+  if ((int)blockIdx.x >= tm * tn) return;
+  const int ti = blockIdx.x % tm, tj = blockIdx.x / tm;
+  if (herm && ti > tj) return;
+  const int i0 = ti * FBM, j0 = tj * FBN;
+  const int split = blockIdx.z;
+  const int klim = triB ? min(it.k, j0 + FBN) : it.k;
+  const int kper = ((klim + splits - 1) / splits + FBK - 1) / FBK * FBK;
+  const int kb = split * kper, ke = min(klim, kb + kper);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  ACC acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = ACC{};
+  for (int k0 = kb; k0 < ke; k0 += FBK) {
+#pragma unroll
+    for (int q = 0; q < (FBM * FBK) / 256; ++q) {
+      const int e = tid + q * 256;
+      int i, kk;
+      S v = sc<S>::zero();
+      if (CA) {  // A stored k x m: read along k
+        kk = e % FBK;
+        i = e / FBK;
+        if (i0 + i < it.m && k0 + kk < ke) v = it.A[(k0 + kk) + (int64_t)(i0 + i) * it.lda];
+      } else {   // A stored m x k: read along m
+        i = e % FBM;
+        kk = e / FBM;
+        if (i0 + i < it.m && k0 + kk < ke) v = it.A[(i0 + i) + (int64_t)(k0 + kk) * it.lda];
+      }
+      ff_load(v, CA, As[kk][i]);
+    }
+#pragma unroll
+    for (int q = 0; q < (FBN * FBK) / 256; ++q) {
+      const int e = tid + q * 256;
+      const int kk = e % FBK, j = e / FBK;
+      S v = sc<S>::zero();
+      if (j0 + j < it.n && k0 + kk < ke) v = it.B[(k0 + kk) + (int64_t)(j0 + j) * it.ldb];
+      ff_load(v, false, Bs[kk][j]);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < FBK; ++kk) {
+      V a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[kk][ty + 16 * q];
+        b[q] = Bs[kk][tx + 16 * q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) ff_fma(acc[q][r], a[q], b[r]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + ty + 16 * q, j = j0 + tx + 16 * r;
+      if (i >= it.m || j >= it.n) continue;
+      const S val = ff_val(acc[q][r]);
+      if (splits > 1) {
+        part[split * part_stride + it.part_off + i + (int64_t)j * it.m] = val;
+      } else {
+        S* cp = it.C + i + (int64_t)j * it.ldc;
+        S v = sc<S>::mul(alpha, val);
+        if (sc<S>::re(beta) != 0.0 || sc<S>::abs2(beta) != 0.0) v = sc<S>::add(v, sc<S>::mul(beta, *cp));
+        *cp = v;
+        if (herm && ti < tj) it.C[j + (int64_t)i * it.ldc] = sc<S>::conj(v);
+      }
+    }
+}
+
 template <typename S>
 __global__ void gemm_reduce_kernel(const GemmItem<S>* items, S alpha, S beta, int splits, const S* part,
                                    int64_t part_stride, int herm) {
@@ -125,15 +277,23 @@ __global__ void gemm_reduce_kernel(const GemmItem<S>* items, S alpha, S beta, in
 
 template <typename S>
 int launch_gemm(bool conjA, int nitems, const GemmItem<S>* d_items, int max_m, int max_n, int max_k, S alpha,
-                S beta, int splits, S* part, int64_t part_stride, cudaStream_t st, int herm, int triB) {
+                S beta, int splits, S* part, int64_t part_stride, cudaStream_t st, int herm, int triB, int ff) {
   if (nitems <= 0 || max_m <= 0 || max_n <= 0) return 0;
   if (max_k <= 0) splits = 1;
   if (splits < 1) splits = 1;
-  dim3 grid((unsigned)(ceil_div(max_m, GBM) * ceil_div(max_n, GBN)), (unsigned)nitems, (unsigned)splits);
-  if (conjA)
-    gemm_kernel<S, true><<<grid, 256, 0, st>>>(d_items, alpha, beta, splits, part, part_stride, herm, triB);
-  else
-    gemm_kernel<S, false><<<grid, 256, 0, st>>>(d_items, alpha, beta, splits, part, part_stride, herm, triB);
+  if (ff) {
+    dim3 grid((unsigned)(ceil_div(max_m, FBM) * ceil_div(max_n, FBN)), (unsigned)nitems, (unsigned)splits);
+    if (conjA)
+      ffgemm_kernel<S, true><<<grid, 256, 0, st>>>(d_items, alpha, beta, splits, part, part_stride, herm, triB);
+    else
+      ffgemm_kernel<S, false><<<grid, 256, 0, st>>>(d_items, alpha, beta, splits, part, part_stride, herm, triB);
+  } else {
+    dim3 grid((unsigned)(ceil_div(max_m, GBM) * ceil_div(max_n, GBN)), (unsigned)nitems, (unsigned)splits);
+    if (conjA)
+      gemm_kernel<S, true><<<grid, 256, 0, st>>>(d_items, alpha, beta, splits, part, part_stride, herm, triB);
+    else
+      gemm_kernel<S, false><<<grid, 256, 0, st>>>(d_items, alpha, beta, splits, part, part_stride, herm, triB);
+  }
   PD_CK_LAUNCH();
   if (splits > 1) {
     int blocks = (int)ceil_div((int64_t)max_m * max_n, 256);
@@ -627,6 +787,94 @@ __global__ void __launch_bounds__(256) band_matmul_kernel(int64_t n, int b, cons
   Y[i + (int64_t)c * n] = acc;
 }
 
+// Band entries split once into float-float pairs, layout [j * (b+1) + d] for
+// B(j+d, j) (the compact lower band, leading dimension b+1).
+template <typename S>
+__global__ void band_split_kernel(int64_t n, int b, const double* __restrict__ band, int64_t ldab,
+                                  typename ffv<S>::type* __restrict__ out) {
+  const int64_t total = n * (int64_t)(b + 1);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / (b + 1);
+    const int d = (int)(e % (b + 1));
+    if constexpr (std::is_same<S, double2>::value) {
+      const double* p = band + 2 * (d + j * ldab);
+      const double im = d == 0 ? 0.0 : p[1];
+      ff_load(make_double2(p[0], im), false, out[e]);
+    } else {
+      ff_load(band[d + j * ldab], false, out[e]);
+    }
+  }
+}
+
+// Y = B X in float-float arithmetic.  Block: 32 rows x 8 columns, one warp per
+// column; the warp stages the column's x(i0-b .. i0+31+b) in shared memory as
+// float-float pairs (each x entry is split once for its 2b+1 uses), the band
+// comes pre-split and is shared by the 8 warps through L1.
+template <typename S>
+__global__ void __launch_bounds__(256) band_matmul_ff_kernel(int64_t n, int b,
+                                                            const typename ffv<S>::type* __restrict__ bs,
+                                                            int ncols, const S* __restrict__ X, S* __restrict__ Y) {
+  using V = typename ffv<S>::type;
+  using ACC = typename std::conditional<std::is_same<S, double2>::value, ffacc2, ffacc1>::type;
+  extern __shared__ __align__(16) unsigned char ffsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int W = 32 + 2 * b;
+  V* xs = (V*)ffsm + (size_t)warp * W;
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int c = blockIdx.y * 8 + warp;
+  if (c >= ncols) return;  // whole warp leaves; no block-wide barrier follows
+  const S* x = X + (int64_t)c * n;
+  for (int t = lane; t < W; t += 32) {
+    const int64_t j = i0 - b + t;
+    S v = sc<S>::zero();
+    if (j >= 0 && j < n) v = x[j];
+    ff_load(v, false, xs[t]);
+  }
+  __syncwarp();
+  const int64_t i = i0 + lane;
+  if (i >= n) return;
+  ACC acc{};
+  const int64_t j0 = i - b < 0 ? 0 : i - b, j1 = i + b > n - 1 ? n - 1 : i + b;
+  for (int64_t j = j0; j <= j1; ++j) {
+    V bij;
+    if (j <= i) {
+      bij = bs[(i - j) + j * (int64_t)(b + 1)];
+    } else {
+      bij = bs[(j - i) + i * (int64_t)(b + 1)];
+      if constexpr (std::is_same<S, double2>::value) {
+        bij.z = -bij.z;
+        bij.w = -bij.w;
+      }
+    }
+    ff_fma(acc, bij, xs[j - (i0 - b)]);
+  }
+  Y[i + (int64_t)c * n] = ff_val(acc);
+}
+
+template <typename S>
+int launch_band_split(int64_t n, int b, const void* band, int64_t ldab, void* out, cudaStream_t st) {
+  band_split_kernel<S><<<1024, 256, 0, st>>>(n, b, (const double*)band, ldab, (typename ffv<S>::type*)out);
+  PD_CK_LAUNCH();
+  return 0;
+}
+
+size_t band_split_bytes(int64_t n, int b, int cplx) {
+  return (size_t)n * (size_t)(b + 1) * (cplx ? sizeof(float4) : sizeof(float2));
+}
+
+template <typename S>
+int launch_band_matmul_ff(int64_t n, int b, const void* band_split, int ncols, const S* X, S* Y, cudaStream_t st) {
+  if (n <= 0 || ncols <= 0) return 0;
+  using V = typename ffv<S>::type;
+  const size_t smem = (size_t)8 * (32 + 2 * b) * sizeof(V);
+  if (smem > 48 * 1024)
+    PD_CK(cudaFuncSetAttribute(band_matmul_ff_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)ceil_div(n, 32), (unsigned)ceil_div(ncols, 8));
+  band_matmul_ff_kernel<S><<<grid, 256, smem, st>>>(n, b, (const V*)band_split, ncols, X, Y);
+  PD_CK_LAUNCH();
+  return 0;
+}
+
 template <typename S>
 int launch_band_matmul(int64_t n, int b, const void* band, int64_t ldab, int ncols, const S* X, S* Y,
                        cudaStream_t st) {
@@ -759,7 +1007,7 @@ EighScratch<S> plan_eigh_scratch(Arena& a, int64_t msq, int64_t mtot, int nblk) 
 
 template <typename S>
 int small_gemm(bool conjA, const std::vector<SmallDesc>& blk, int max_m, S* const* abc, int herm, int triB,
-               GemmItem<S>* d_items, cudaStream_t st) {
+               GemmItem<S>* d_items, cudaStream_t st, int ff) {
   // abc = {A base, B base, C base}; every block is m x m at the block's offset
   const int nb = (int)blk.size();
   if (!nb) return 0;
@@ -778,7 +1026,7 @@ int small_gemm(bool conjA, const std::vector<SmallDesc>& blk, int max_m, S* cons
     one = make_double2(1.0, 0.0);
     zero = make_double2(0.0, 0.0);
   }
-  return launch_gemm<S>(conjA, nb, d_items, max_m, max_m, max_m, one, zero, 1, nullptr, 0, st, herm, triB);
+  return launch_gemm<S>(conjA, nb, d_items, max_m, max_m, max_m, one, zero, 1, nullptr, 0, st, herm, triB, ff);
 }
 
 // One refinement step of an approximate eigenvector matrix V of a Hermitian A
@@ -1053,15 +1301,15 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
     }
     {
       S* abc[3] = {A, V, w.T};  // T = A V
-      PD_TRY(small_gemm<S>(false, sub_d, max_m, abc, 0, 0, w.items, st));
+      PD_TRY(small_gemm<S>(false, sub_d, max_m, abc, 0, 0, w.items, st, w.ff));
     }
     {
       S* abc[3] = {V, w.T, w.W64};  // S = V^H A V  (in W64)
-      PD_TRY(small_gemm<S>(true, sub_d, max_m, abc, 1, 0, w.items, st));
+      PD_TRY(small_gemm<S>(true, sub_d, max_m, abc, 1, 0, w.items, st, w.ff));
     }
     {
       S* abc[3] = {V, V, w.T};  // P = V^H V  (in T)
-      PD_TRY(small_gemm<S>(true, sub_d, max_m, abc, 1, 0, w.items, st));
+      PD_TRY(small_gemm<S>(true, sub_d, max_m, abc, 1, 0, w.items, st, w.ff));
     }
     oa_kernel<S><<<na, 1024, 0, st>>>(dd, w.W64, w.T, w.lam32, w.delta, w.reach);
     PD_CK_LAUNCH();
@@ -1076,7 +1324,7 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
         it2[q] = GemmItem<S>{V + o, w.W64 + o, Vn + o, m, m, m, m, m, m, 0};
       }
       PD_CK(cudaMemcpyAsync(w.items, it2.data(), sizeof(GemmItem<S>) * na, cudaMemcpyHostToDevice, st));
-      PD_TRY(launch_gemm<S>(false, na, w.items, max_m, max_m, max_m, one, one, 1, nullptr, 0, st, 0, 0));
+      PD_TRY(launch_gemm<S>(false, na, w.items, max_m, max_m, max_m, one, one, 1, nullptr, 0, st, 0, 0, w.ff));
     }
     for (auto& b : sub_d)
       PD_CK(cudaMemcpyAsync(V + b.off, Vn + b.off, sizeof(S) * (size_t)b.m * b.m, cudaMemcpyDeviceToDevice, st));
@@ -1216,9 +1464,9 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
 
 // explicit instantiations
 template int small_gemm<double>(bool, const std::vector<SmallDesc>&, int, double* const*, int, int,
-                                GemmItem<double>*, cudaStream_t);
+                                GemmItem<double>*, cudaStream_t, int);
 template int small_gemm<double2>(bool, const std::vector<SmallDesc>&, int, double2* const*, int, int,
-                                 GemmItem<double2>*, cudaStream_t);
+                                 GemmItem<double2>*, cudaStream_t, int);
 template EighScratch<double> plan_eigh_scratch<double>(Arena&, int64_t, int64_t, int);
 template EighScratch<double2> plan_eigh_scratch<double2>(Arena&, int64_t, int64_t, int);
 template int eigh_mixed<double>(int, const SmallDesc*, const SmallDesc*, int, double*, double*, double*,
@@ -1228,9 +1476,9 @@ template int eigh_mixed<double2>(int, const SmallDesc*, const SmallDesc*, int, d
                                  const EighScratch<double2>&, cudaStream_t, int*, const unsigned char*, int*,
                                  EighReport*);
 template int launch_gemm<double>(bool, int, const GemmItem<double>*, int, int, int, double, double, int,
-                                 double*, int64_t, cudaStream_t, int, int);
+                                 double*, int64_t, cudaStream_t, int, int, int);
 template int launch_gemm<double2>(bool, int, const GemmItem<double2>*, int, int, int, double2, double2, int,
-                                  double2*, int64_t, cudaStream_t, int, int);
+                                  double2*, int64_t, cudaStream_t, int, int, int);
 template int launch_cholesky<double>(int, const SmallDesc*, double*, int*, cudaStream_t, double*, double*);
 template int launch_cholesky<double2>(int, const SmallDesc*, double2*, int*, cudaStream_t, double*, double*);
 template int launch_triinv<double>(int, const SmallDesc*, const double*, double*, cudaStream_t);
@@ -1243,6 +1491,11 @@ template int launch_jacobi<float>(int, const SmallDesc*, int, float*, float*, fl
                                   int*, double*, cudaStream_t);
 template int launch_jacobi<float2>(int, const SmallDesc*, int, float2*, float2*, float2*, double*, double,
                                    int, int*, double*, cudaStream_t);
+template int launch_band_split<double>(int64_t, int, const void*, int64_t, void*, cudaStream_t);
+template int launch_band_split<double2>(int64_t, int, const void*, int64_t, void*, cudaStream_t);
+template int launch_band_matmul_ff<double>(int64_t, int, const void*, int, const double*, double*, cudaStream_t);
+template int launch_band_matmul_ff<double2>(int64_t, int, const void*, int, const double2*, double2*,
+                                            cudaStream_t);
 template int launch_band_matmul<double>(int64_t, int, const void*, int64_t, int, const double*, double*,
                                         cudaStream_t);
 template int launch_band_matmul<double2>(int64_t, int, const void*, int64_t, int, const double2*,

@@ -25,10 +25,12 @@ struct GemmItem {
 // Launch a batch of products.  splits > 1 splits the k dimension; then `part`
 // must hold splits * sum_i(m_i * n_i) elements (deterministic reduction).
 // herm: output Hermitian (only upper tiles computed, lower mirrored); triB: B upper triangular.
+// ff: float-float arithmetic on the FP32 pipes (about 48-bit products, FP32 exponent range)
+// instead of FP64.
 template <typename S>
 int launch_gemm(bool conjA, int nitems, const GemmItem<S>* d_items, int max_m, int max_n, int max_k,
                 S alpha, S beta, int splits, S* part, int64_t part_stride, cudaStream_t st, int herm = 0,
-                int triB = 0);
+                int triB = 0, int ff = 0);
 
 // Per-slice small dense kernels.  Blocks of slice t start at offset off[t]
 // (elements) with order m[t]; one thread-block cluster per slice.
@@ -89,6 +91,7 @@ struct EighScratch {
   SmallDesc* cdesc;
   int* csweeps;
   double* cjscratch;
+  int ff = 0;               // float-float products in the refinement (set by the caller)
 };
 // columns i0..i0+c-1 of the m x m block at element offset off (eigenvalues at voff)
 struct ClusterRef {
@@ -103,7 +106,7 @@ EighScratch<S> plan_eigh_scratch(Arena& a, int64_t msq, int64_t mtot, int nblk);
 // C_t = op(A_t) B_t for m x m blocks at each block's offset (abc = {A, B, C} bases).
 template <typename S>
 int small_gemm(bool conjA, const std::vector<SmallDesc>& blk, int max_m, S* const* abc, int herm, int triB,
-               GemmItem<S>* d_items, cudaStream_t st);
+               GemmItem<S>* d_items, cudaStream_t st, int ff = 0);
 
 // h_fp32[t] (optional, default all): run the FP32 pre-rotation on block t; blocks that are
 // already nearly diagonal skip it and go straight to the FP64 sweeps.
@@ -117,6 +120,13 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
                const unsigned char* h_fp32 = nullptr, int* fp32_sweeps_out = nullptr, EighReport* rep = nullptr);
 
 // Y = B X for the Hermitian band (lower storage), X, Y n x ncols (ld n).
+// Float-float band product: the band is split once (launch_band_split into
+// band_split_bytes of scratch), then Y = B X runs on the FP32 pipes.
+size_t band_split_bytes(int64_t n, int b, int cplx);
+template <typename S>
+int launch_band_split(int64_t n, int b, const void* band, int64_t ldab, void* out, cudaStream_t st);
+template <typename S>
+int launch_band_matmul_ff(int64_t n, int b, const void* band_split, int ncols, const S* X, S* Y, cudaStream_t st);
 template <typename S>
 int launch_band_matmul(int64_t n, int b, const void* band, int64_t ldab, int ncols, const S* X, S* Y,
                        cudaStream_t st);

@@ -368,6 +368,7 @@ struct Plan {
   SysDesc* d_sys;  // K * ne
   char* inertia_ws;
   size_t inertia_bytes;
+  void* band_ff;   // float-float copy of the band (mixed precision only)
   // wave area
   char* wave_base;
   size_t wave_bytes;
@@ -529,9 +530,17 @@ struct Feast {
     }
     q.inertia_bytes = std::max(inertia_ws_bytes(b, cplx, K + 1), bisect_ws_bytes(b, cplx, 2, 16));
     q.inertia_ws = a.take<char>(q.inertia_bytes);
-    if (carve) p = q;
+    q.band_ff = ff() ? (void*)a.take<char>(band_split_bytes(n, b, cplx)) : nullptr;
+    if (carve) {
+      p = q;
+      eig.ff = ff();
+    }
     return a.used();
   }
+
+  // Mixed precision runs the FP64-class products of the Rayleigh-Ritz step in
+  // float-float arithmetic on the FP32 pipes; plain FEAST keeps them in FP64.
+  int ff() const { return o->precision == PDESHEP_MIXED ? 1 : 0; }
 
   size_t per_system_bytes(int s) const {
     return fb + (((size_t)n * m0[s] * (cplx ? 2 : 1) * es + 255) & ~size_t(255));
@@ -616,14 +625,15 @@ struct FeastRun : Feast<S, C> {
     double fl = 0.0;  // algorithmic: Hermitian or triangular products count half
     for (int s : active) fl += this->cw() * (double)n * m0[s] * m0[s] * ((kind == 0 || tri) ? 0.5 : 1.0);
     PD_TRY(this->kt.begin(PDESHEP_KG_GEMM));
+    const int ff = this->ff();
     if (kind == 0) {
-      const int64_t t1 = ceil_div(mm, 32);
+      const int64_t t1 = ceil_div(mm, ff ? 64 : 32);
       const int64_t tiles = (int64_t)na * t1 * (t1 + 1) / 2;
       int splits = (int)std::min<int64_t>(p.splits, std::max<int64_t>(1, ceil_div(8 * 152, tiles)));
       splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, n / 512));
-      PD_TRY(launch_gemm<S>(true, na, d_it, mm, mm, (int)n, one, zero, splits, (S*)p.part, Msq, st, 1, 0));
+      PD_TRY(launch_gemm<S>(true, na, d_it, mm, mm, (int)n, one, zero, splits, (S*)p.part, Msq, st, 1, 0, ff));
     } else {
-      PD_TRY(launch_gemm<S>(false, na, d_it, (int)n, mm, mm, one, zero, 1, (S*)p.part, Msq, st, 0, tri));
+      PD_TRY(launch_gemm<S>(false, na, d_it, (int)n, mm, mm, one, zero, 1, (S*)p.part, Msq, st, 0, tri, ff));
     }
     return this->kt.end(fl);
   }
@@ -639,8 +649,12 @@ struct FeastRun : Feast<S, C> {
     double fl = 0.0;
     for (int s : active) fl += this->cw() * (2.0 * b + 1.0) * (double)n * m0[s];
     PD_TRY(this->kt.begin(PDESHEP_KG_BANDMM));
-    for (int s : active)
-      PD_TRY(launch_band_matmul<S>(n, b, band, ldab, m0[s], X + col_off[s] * n, Y + col_off[s] * n, st));
+    for (int s : active) {
+      if (this->ff())
+        PD_TRY(launch_band_matmul_ff<S>(n, b, p.band_ff, m0[s], X + col_off[s] * n, Y + col_off[s] * n, st));
+      else
+        PD_TRY(launch_band_matmul<S>(n, b, band, ldab, m0[s], X + col_off[s] * n, Y + col_off[s] * n, st));
+    }
     return this->kt.end(fl);
   }
 
@@ -663,7 +677,8 @@ struct FeastRun : Feast<S, C> {
     double fl = 0.0;
     for (int s : active) fl += this->cw() * (double)m0[s] * m0[s] * m0[s] * ((herm || tri) ? 0.5 : 1.0);
     PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
-    PD_TRY(small_gemm<S>(conjA, this->h_small, act_max_m0(), abc, herm, tri, (GemmItem<S>*)p.d_items_small, st));
+    PD_TRY(small_gemm<S>(conjA, this->h_small, act_max_m0(), abc, herm, tri, (GemmItem<S>*)p.d_items_small, st,
+                         this->ff()));
     return this->kt.end(fl);
   }
 
@@ -988,6 +1003,11 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   PD_CK(cudaEventRecord(side.t1, side.s));
   PD_TRY(side.join(st));
   const long long inertia_launches = 2;
+  if (F.ff()) {
+    PD_TRY(F.kt.begin(PDESHEP_KG_BANDMM));
+    PD_TRY(launch_band_split<S>(n, b, band, ldab, F.p.band_ff, st));
+    PD_TRY(F.kt.end(0.0));
+  }
   F.counts.assign(K, 0);
   F.nconv.assign(K, 0);
   F.iters.assign(K, 0);
