@@ -112,10 +112,10 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmItem<S>* items, S a
 // the low word and lo*lo is dropped.  Relative accuracy of a length-K dot
 // product is about 2^-48 sqrt(K) in practice, far inside the 1e-10 residual
 // target; the exponent range is FP32's (operands above ~1e-19 in magnitude
-// keep full precision).  Tiles: 64 x 64 outputs per CTA, 4 x 4 per thread,
-// k-steps of 16 staged in shared memory as (hi, lo) pairs.
+// keep full precision).  Tiles: 64 x 64 outputs per CTA of 512 threads, 4 x 2
+// per thread, k-steps of 16 staged in shared memory as (hi, lo) pairs.
 // ---------------------------------------------------------------------------
-constexpr int FBM = 64, FBN = 64, FBK = 16;
+constexpr int FBM = 64, FBN = 64, FBK = 16, FFT = 512;
 
 template <typename S>
 struct ffv;  // a split operand in shared memory
@@ -173,12 +173,16 @@ __device__ __forceinline__ double2 ff_val(const ffacc2& a) {
 }
 
 template <typename S, bool CA>
-__global__ void __launch_bounds__(256) ffgemm_kernel(const GemmItem<S>* items, S alpha, S beta, int splits,
+__global__ void __launch_bounds__(FFT) ffgemm_kernel(const GemmItem<S>* items, S alpha, S beta, int splits,
                                                     S* part, int64_t part_stride, int herm, int triB) {
   using V = typename ffv<S>::type;
   using ACC = typename std::conditional<std::is_same<S, double2>::value, ffacc2, ffacc1>::type;
-  __shared__ V As[FBK][FBM];
-  __shared__ V Bs[FBK][FBN];
+  // two stages of the (hi, lo) tiles: the next k-step's operands are fetched
+  // into registers before the current step's products and split into the other
+  // stage after them, so the FP64-pipe splitting overlaps other warps' FMAs
+  extern __shared__ __align__(16) unsigned char ffsm[];
+  V(*As)[FBK][FBM] = reinterpret_cast<V(*)[FBK][FBM]>(ffsm);
+  V(*Bs)[FBK][FBN] = reinterpret_cast<V(*)[FBK][FBN]>(ffsm + 2 * sizeof(V) * FBK * FBM);
   const GemmItem<S> it = items[blockIdx.y];
   const int tm = (it.m + FBM - 1) / FBM, tn = (it.n + FBN - 1) / FBN;
   if ((int)blockIdx.x >= tm * tn) return;
@@ -189,58 +193,79 @@ __global__ void __launch_bounds__(256) ffgemm_kernel(const GemmItem<S>* items, S
   const int klim = triB ? min(it.k, j0 + FBN) : it.k;
   const int kper = ((klim + splits - 1) / splits + FBK - 1) / FBK * FBK;
   const int kb = split * kper, ke = min(klim, kb + kper);
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  ACC acc[4][4];
+  // 512 threads: thread (tx, ty) owns rows ty + 16 q (q < 4) and columns tx + 32 r (r < 2)
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  constexpr int NA = (FBM * FBK) / FFT, NB = (FBN * FBK) / FFT;
+  S ra[NA], rb[NB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = tid + q * FFT;
+      ra[q] = sc<S>::zero();
+      if (CA) {  // A stored k x m: read along k
+        const int kk = e % FBK, i = e / FBK;
+        if (i0 + i < it.m && k0 + kk < ke) ra[q] = it.A[(k0 + kk) + (int64_t)(i0 + i) * it.lda];
+      } else {   // A stored m x k: read along m
+        const int i = e % FBM, kk = e / FBM;
+        if (i0 + i < it.m && k0 + kk < ke) ra[q] = it.A[(i0 + i) + (int64_t)(k0 + kk) * it.lda];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + q * FFT;
+      const int kk = e % FBK, j = e / FBK;
+      rb[q] = sc<S>::zero();
+      if (j0 + j < it.n && k0 + kk < ke) rb[q] = it.B[(k0 + kk) + (int64_t)(j0 + j) * it.ldb];
+    }
+  };
+  auto stash = [&](int stg) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = tid + q * FFT;
+      const int kk = CA ? e % FBK : e / FBM, i = CA ? e / FBK : e % FBM;
+      ff_load(ra[q], CA, As[stg][kk][i]);
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + q * FFT;
+      ff_load(rb[q], false, Bs[stg][e % FBK][e / FBK]);
+    }
+  };
+  ACC acc[4][2];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = ACC{};
+    for (int c = 0; c < 2; ++c) acc[a][c] = ACC{};
+  int stg = 0;
+  if (kb < ke) {
+    fetch(kb);
+    stash(0);
+  }
+  __syncthreads();
   for (int k0 = kb; k0 < ke; k0 += FBK) {
-#pragma unroll
-    for (int q = 0; q < (FBM * FBK) / 256; ++q) {
-      const int e = tid + q * 256;
-      int i, kk;
-      S v = sc<S>::zero();
-      if (CA) {  // A stored k x m: read along k
-        kk = e % FBK;
-        i = e / FBK;
-        if (i0 + i < it.m && k0 + kk < ke) v = it.A[(k0 + kk) + (int64_t)(i0 + i) * it.lda];
-      } else {   // A stored m x k: read along m
-        i = e % FBM;
-        kk = e / FBM;
-        if (i0 + i < it.m && k0 + kk < ke) v = it.A[(i0 + i) + (int64_t)(k0 + kk) * it.lda];
-      }
-      ff_load(v, CA, As[kk][i]);
-    }
-#pragma unroll
-    for (int q = 0; q < (FBN * FBK) / 256; ++q) {
-      const int e = tid + q * 256;
-      const int kk = e % FBK, j = e / FBK;
-      S v = sc<S>::zero();
-      if (j0 + j < it.n && k0 + kk < ke) v = it.B[(k0 + kk) + (int64_t)(j0 + j) * it.ldb];
-      ff_load(v, false, Bs[kk][j]);
-    }
-    __syncthreads();
+    const bool more = k0 + FBK < ke;
+    if (more) fetch(k0 + FBK);
 #pragma unroll 4
     for (int kk = 0; kk < FBK; ++kk) {
-      V a[4], b[4];
+      V a[4], b[2];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[kk][ty + 16 * q];
-        b[q] = Bs[kk][tx + 16 * q];
-      }
+      for (int q = 0; q < 4; ++q) a[q] = As[stg][kk][ty + 16 * q];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) b[r] = Bs[stg][kk][tx + 32 * r];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) ff_fma(acc[q][r], a[q], b[r]);
+        for (int r = 0; r < 2; ++r) ff_fma(acc[q][r], a[q], b[r]);
     }
+    if (more) stash(stg ^ 1);
     __syncthreads();
+    stg ^= 1;
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int i = i0 + ty + 16 * q, j = j0 + tx + 16 * r;
+    for (int r = 0; r < 2; ++r) {
+      const int i = i0 + ty + 16 * q, j = j0 + tx + 32 * r;
       if (i >= it.m || j >= it.n) continue;
       const S val = ff_val(acc[q][r]);
       if (splits > 1) {
@@ -283,10 +308,14 @@ int launch_gemm(bool conjA, int nitems, const GemmItem<S>* d_items, int max_m, i
   if (splits < 1) splits = 1;
   if (ff) {
     dim3 grid((unsigned)(ceil_div(max_m, FBM) * ceil_div(max_n, FBN)), (unsigned)nitems, (unsigned)splits);
-    if (conjA)
-      ffgemm_kernel<S, true><<<grid, 256, 0, st>>>(d_items, alpha, beta, splits, part, part_stride, herm, triB);
-    else
-      ffgemm_kernel<S, false><<<grid, 256, 0, st>>>(d_items, alpha, beta, splits, part, part_stride, herm, triB);
+    const size_t smem = 2 * sizeof(typename ffv<S>::type) * FBK * (FBM + FBN);
+    if (conjA) {
+      PD_CK(cudaFuncSetAttribute(ffgemm_kernel<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ffgemm_kernel<S, true><<<grid, FFT, smem, st>>>(d_items, alpha, beta, splits, part, part_stride, herm, triB);
+    } else {
+      PD_CK(cudaFuncSetAttribute(ffgemm_kernel<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ffgemm_kernel<S, false><<<grid, FFT, smem, st>>>(d_items, alpha, beta, splits, part, part_stride, herm, triB);
+    }
   } else {
     dim3 grid((unsigned)(ceil_div(max_m, GBM) * ceil_div(max_n, GBN)), (unsigned)nitems, (unsigned)splits);
     if (conjA)
@@ -992,7 +1021,7 @@ EighScratch<S> plan_eigh_scratch(Arena& a, int64_t msq, int64_t mtot, int nblk) 
   w.jscratch = a.take<double>((size_t)nblk * 2 * 16);
   w.items = a.take<GemmItem<S>>(nblk);
   w.dsub = a.take<SmallDesc>(2 * (size_t)nblk);
-  w.delta = a.take<double>(nblk);
+  w.delta = a.take<double>((size_t)nblk * kOaSplit);
   w.shift = a.take<double>(nblk);
   w.A64 = a.take<S>(msq);
   w.reach = a.take<double>(mtot);
@@ -1031,14 +1060,12 @@ int small_gemm(bool conjA, const std::vector<SmallDesc>& blk, int max_m, S* cons
 
 // One refinement step of an approximate eigenvector matrix V of a Hermitian A
 // (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue
-// decomposition", 2018), given S = V^H A V and P = V^H V:
-//   R = I - P,  lambda_i = Re S_ii / (1 - Re R_ii),
-//   delta = 2 (||S - diag(lambda)||_F + max|lambda| ||R||_F),
-//   E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)  if |lambda_i - lambda_j| > delta,
-//   E_ij = R_ij / 2 otherwise (and on the diagonal);  V <- V + V E.
-// One thread block per slice; E overwrites S.  delta_out[t] = delta / max|lambda|.
+// decomposition", 2018); E overwrites S.  Their separation test uses one
+// Frobenius-norm bound for all pairs; here each pair is tested on its own
+// coupling, which keeps the step quadratic on the separated pairs while the
+// others are left to the cluster treatment.
 template <typename S>
-__global__ void __launch_bounds__(1024) oa_kernel(const SmallDesc* desc, S* Sall, const S* Pall, double* lamall,
+__global__ void __launch_bounds__(256) oa_kernel(const SmallDesc* desc, S* Sall, const S* Pall, double* lamall,
                                                   double* est_out, double* reach_all) {
   // One refinement step (Ogita and Aishima, 2018) for block t, given S = V^H A V
   // and P = V^H V of the current approximate eigenvectors V:
@@ -1051,7 +1078,9 @@ __global__ void __launch_bounds__(1024) oa_kernel(const SmallDesc* desc, S* Sall
   // left alone here and resolved by the caller.  Outputs: est = max(|E_ij| over
   // separated pairs, |R_ij|), the size of the correction, and per column j
   // reach_j = the largest lambda_i >= lambda_j (i != j) coupled to j without
-  // being separated, or -inf.
+  // being separated, or -inf.  Grid (blocks, kOaSplit): CTA y of a block handles
+  // columns y*nw + warp (stride kOaSplit*nw); est_out[block * kOaSplit + y] is its
+  // partial maximum.  Every CTA computes the (identical) lambda itself.
   const SmallDesc d = desc[blockIdx.x];
   const int m = d.m;
   S* Sm = Sall + d.off;
@@ -1078,7 +1107,7 @@ __global__ void __launch_bounds__(1024) oa_kernel(const SmallDesc* desc, S* Sall
   __syncthreads();
   const double tiny = 1e-14 * sh_l;
   double emax = 0.0, rmax = 0.0;
-  for (int j = warp; j < m; j += nw) {
+  for (int j = blockIdx.y * nw + warp; j < m; j += gridDim.y * nw) {
     const double lj = lam[j];
     double rj = -INFINITY;
     for (int i = lane; i < m; i += 32) {
@@ -1125,7 +1154,7 @@ __global__ void __launch_bounds__(1024) oa_kernel(const SmallDesc* desc, S* Sall
       a = fmax(a, red[0][w]);
       b = fmax(b, red[1][w]);
     }
-    est_out[blockIdx.x] = fmax(a, b);
+    est_out[blockIdx.x * gridDim.y + blockIdx.y] = fmax(a, b);
   }
 }
 
@@ -1287,7 +1316,7 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
   // kRefineSteps steps.
   S* V = w.Vd;
   S* Vn = w.Vw;
-  std::vector<double> drel(nblk, 1.0), est(nblk);
+  std::vector<double> drel(nblk, 1.0), est(nblk), estp((size_t)nblk * kOaSplit);
   std::vector<int> act(nblk);
   for (int t = 0; t < nblk; ++t) act[t] = t;
   for (int it = 0; it < kRefineSteps && !act.empty(); ++it) {
@@ -1311,7 +1340,7 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
       S* abc[3] = {V, V, w.T};  // P = V^H V  (in T)
       PD_TRY(small_gemm<S>(true, sub_d, max_m, abc, 1, 0, w.items, st, w.ff));
     }
-    oa_kernel<S><<<na, 1024, 0, st>>>(dd, w.W64, w.T, w.lam32, w.delta, w.reach);
+    oa_kernel<S><<<dim3(na, kOaSplit), 256, 0, st>>>(dd, w.W64, w.T, w.lam32, w.delta, w.reach);
     PD_CK_LAUNCH();
     for (auto& b : sub_d)
       PD_CK(cudaMemcpyAsync(Vn + b.off, V + b.off, sizeof(S) * (size_t)b.m * b.m, cudaMemcpyDeviceToDevice, st));
@@ -1328,8 +1357,12 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
     }
     for (auto& b : sub_d)
       PD_CK(cudaMemcpyAsync(V + b.off, Vn + b.off, sizeof(S) * (size_t)b.m * b.m, cudaMemcpyDeviceToDevice, st));
-    PD_CK(cudaMemcpyAsync(est.data(), w.delta, sizeof(double) * na, cudaMemcpyDeviceToHost, st));
+    PD_CK(cudaMemcpyAsync(estp.data(), w.delta, sizeof(double) * na * kOaSplit, cudaMemcpyDeviceToHost, st));
     PD_CK(cudaStreamSynchronize(st));
+    for (int q = 0; q < na; ++q) {
+      est[q] = 0.0;
+      for (int c = 0; c < kOaSplit; ++c) est[q] = std::max(est[q], estp[(size_t)q * kOaSplit + c]);
+    }
     if (rep) rep->refine_steps += 1;
     std::vector<int> next;
     for (int q = 0; q < na; ++q) {

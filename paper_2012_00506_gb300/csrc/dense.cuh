@@ -101,6 +101,7 @@ struct ClusterRef {
 constexpr int kMaxCluster = 64;
 constexpr int kRefineSteps = 10;
 constexpr double kRefineTol = 1e-8;
+constexpr int kOaSplit = 16;  // CTAs per block in one refinement step
 template <typename S>
 EighScratch<S> plan_eigh_scratch(Arena& a, int64_t msq, int64_t mtot, int nblk);
 // C_t = op(A_t) B_t for m x m blocks at each block's offset (abc = {A, B, C} bases).
