@@ -67,15 +67,30 @@ typedef struct {
   int32_t max_iter;        /* FEAST iterations per slice; default 20 */
   int32_t precision;       /* PDESHEP_FP64 or PDESHEP_MIXED; default PDESHEP_MIXED */
   int32_t refine_policy;   /* PDESHEP_REFINE_*; default PDESHEP_REFINE_RESIDUAL */
-  int32_t rhs_chunk;       /* right-hand sides per solve block (0 = autotuned) */
+  int32_t rhs_chunk;       /* right-hand sides per solve work item: 16, 32 or 64; 0 = 32, or the
+                              autotuned width when autotune is on */
   double ellipse_ratio;    /* vertical / horizontal semi-axis of the contour; default 0.3 */
   double bnorm;            /* ||B||_2 for the residual; <= 0: computed by the library */
   uint64_t seed;           /* reserved for library-drawn start vectors */
   size_t hbm_cap_bytes;    /* cap on factor storage per wave; 0 = whole workspace */
-  int32_t autotune;        /* 0 off, 1 on (tile/chunk choice from measured timings) */
+  int32_t autotune;        /* 0 off; 1 use the tuned choice for this problem shape, measuring
+                              it on first use; 2 measure again.  Tuned: the solve column block
+                              (16/32/64, unless rhs_chunk is set) and the split count of the
+                              tall Gram products (2/4/8) */
   int32_t verbose;         /* 0 quiet */
   void* stream;            /* cudaStream_t */
+  int32_t rr_arith;        /* PDESHEP_MIXED only: PDESHEP_RR_FLOATFLOAT (default) or PDESHEP_RR_FP64 */
+  int32_t pad0;
+  const char* tune_cache;  /* file that keeps tuned choices across processes; NULL = in-process */
 } pdeshep_opts;
+
+/* Arithmetic of the Rayleigh-Ritz products (Gram, projection, basis update,   */
+/* band product, eigenvector refinement) in mixed precision.  FLOATFLOAT runs  */
+/* them as float-float (FP32 pairs, ~48-bit products, FP32 exponent range) on  */
+/* the FP32 pipes, which GB300 has 64x more of than FP64; FP64 keeps them in   */
+/* FP64 arithmetic.  Counts and residual tests are the same either way.       */
+#define PDESHEP_RR_FLOATFLOAT 0
+#define PDESHEP_RR_FP64 1
 
 /* Kernel groups timed separately (CUDA events around each launch). */
 #define PDESHEP_KG_INERTIA 0     /* LDL^T inertia (and the band amax reduction) */
@@ -118,7 +133,13 @@ typedef struct {
   int32_t eig_max_cluster;
   int32_t eig_fallback_unconverged;
   int32_t eig_fallback_wide;
+  int32_t rhs_chunk_used;  /* solve column block of the last filter pass */
+  int32_t gram_splits_used;/* split count of the last tall Gram product */
+  int32_t tuned;           /* number of choices measured by the autotuner in this call */
 } pdeshep_stats;
+
+/* Forget every tuned choice held in this process (cache files are kept). */
+void pdeshep_tune_reset(void);
 
 /* Fill *o with the defaults listed above. */
 void pdeshep_opts_default(pdeshep_opts* o);

@@ -24,6 +24,8 @@ LIB_PATH = os.path.join(_HERE, "libpdeshep.so")
 
 FP64 = 0
 MIXED = 1
+RR_FLOATFLOAT = 0
+RR_FP64 = 1
 REFINE_NONE = 0
 REFINE_RESIDUAL = 1
 
@@ -44,7 +46,7 @@ EXPORTED = [
     "pdeshep_eigh", "pdeshep_workspace_size", "pdeshep_band_slice",
     "pdeshep_mlp_param_count", "pdeshep_slice_features_workspace_size", "pdeshep_slice_features",
     "pdeshep_mlp_workspace_size", "pdeshep_mlp_forward", "pdeshep_mlp_grad", "pdeshep_mlp_train_step",
-    "pdeshep_propose_workspace_size", "pdeshep_propose_slices",
+    "pdeshep_propose_workspace_size", "pdeshep_propose_slices", "pdeshep_tune_reset",
 ]
 
 
@@ -58,6 +60,7 @@ class Opts(C.Structure):
         ("refine_policy", C.c_int32), ("rhs_chunk", C.c_int32), ("ellipse_ratio", C.c_double),
         ("bnorm", C.c_double), ("seed", C.c_uint64), ("hbm_cap_bytes", C.c_size_t),
         ("autotune", C.c_int32), ("verbose", C.c_int32), ("stream", C.c_void_p),
+        ("rr_arith", C.c_int32), ("pad0", C.c_int32), ("tune_cache", C.c_char_p),
     ]
 
 
@@ -75,6 +78,7 @@ class Stats(C.Structure):
         ("jacobi_sweeps32", C.c_int32), ("rr_calls", C.c_int32),
         ("eig_refine_steps", C.c_int32), ("eig_clusters", C.c_int32), ("eig_max_cluster", C.c_int32),
         ("eig_fallback_unconverged", C.c_int32), ("eig_fallback_wide", C.c_int32),
+        ("rhs_chunk_used", C.c_int32), ("gram_splits_used", C.c_int32), ("tuned", C.c_int32),
     ]
 
     def as_dict(self):
@@ -137,6 +141,7 @@ def load(path: str = LIB_PATH):
         "pdeshep_mlp_grad": (C.c_int, [P, i32, P, P, P, P, P, sz, P]),
         "pdeshep_mlp_train_step": (C.c_int, [P, P, P, i32, C.c_float, i32, P, P, P, P, sz, P]),
         "pdeshep_propose_workspace_size": (sz, [i64, i32, i32, i32, i32]),
+        "pdeshep_tune_reset": (None, []),
         "pdeshep_propose_slices": (C.c_int, [i64, i32, i32, P, i64, P, C.c_uint64, dbl, dbl, i32, i32, i32,
                                              P, P, P, P, P, P, sz, P]),
     }
@@ -344,6 +349,8 @@ def default_opts(**kw) -> Opts:
     o = Opts()
     load().pdeshep_opts_default(C.byref(o))
     for k, v in kw.items():
+        if k == "tune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 

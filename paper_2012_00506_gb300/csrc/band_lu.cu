@@ -22,12 +22,14 @@
 //   L^H and the inverse permutation (trans = 1, the conjugate node conj(z)
 //   of a Hermitian band).  Factor tiles stream from L2/HBM through shared
 //   memory; each is reused by the 32 right-hand sides of the block.
+#include <algorithm>
+#include <vector>
+
 #include "band_lu.cuh"
 
 namespace pdeshep {
 
 constexpr int kThreads = 256;
-constexpr int kCW = 32;  // right-hand sides per solve thread block
 constexpr int kLdt = kTile + 1;
 
 // ---------------------------------------------------------------------------
@@ -277,7 +279,8 @@ __global__ void __launch_bounds__(kThreads) factor_kernel(FactorGeom g, const Sy
 }
 
 // ---------------------------------------------------------------------------
-// solve helpers
+// solve helpers.  A solve block covers CW right-hand sides with 8 warps: lane
+// = row of a tile, warp w owns columns w + 8 jj, jj < NJ = CW / 8.
 // ---------------------------------------------------------------------------
 // Load one T x T tile into Tb (ld kLdt); conjugate-transposed if CT.
 template <typename C, bool CT>
@@ -293,14 +296,14 @@ __device__ __forceinline__ void load_tile(C* Tb, const C* __restrict__ src) {
 }
 
 // acc[jj] += / -= Tb(lane, :) * Bm(:, col_jj), Bm with leading dimension ldb.
-template <typename C, bool SUB>
-__device__ __forceinline__ void tile_mul(C acc[4], const C* Tb, const C* Bm, int ldb) {
+template <typename C, int NJ, bool SUB>
+__device__ __forceinline__ void tile_mul(C acc[NJ], const C* Tb, const C* Bm, int ldb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll 8
   for (int k = 0; k < kTile; ++k) {
     const C a = Tb[lane + k * kLdt];
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
+    for (int jj = 0; jj < NJ; ++jj) {
       const C bv = Bm[k + (warp + 8 * jj) * ldb];
       if (SUB)
         cfms(acc[jj], a, bv);
@@ -310,12 +313,12 @@ __device__ __forceinline__ void tile_mul(C acc[4], const C* Tb, const C* Bm, int
   }
 }
 
-template <typename C>
+template <typename C, int NJ>
 __device__ __forceinline__ void load_rhs_block(C* dst, int ldd, const C* __restrict__ Y, int64_t n,
                                                int64_t row0, int col0, int ncols) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
+  for (int jj = 0; jj < NJ; ++jj) {
     const int c = warp + 8 * jj;
     const int64_t i = row0 + lane;
     C v = cmk<C>(0, 0);
@@ -324,57 +327,60 @@ __device__ __forceinline__ void load_rhs_block(C* dst, int ldd, const C* __restr
   }
 }
 
-template <typename C>
+template <typename C, int NJ>
 __device__ __forceinline__ void store_rows(C* __restrict__ X, int64_t n, int64_t row0, int col0,
-                                           int ncols, const C acc[4]) {
+                                           int ncols, const C acc[NJ]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
+  for (int jj = 0; jj < NJ; ++jj) {
     const int c = warp + 8 * jj;
     const int64_t i = row0 + lane;
     if (i < n && col0 + c < ncols) X[i + (int64_t)(col0 + c) * n] = acc[jj];
   }
 }
 
-template <typename C>
-__device__ __forceinline__ void load_acc(C acc[4], const C* __restrict__ X, int64_t n, int64_t row0,
+template <typename C, int NJ>
+__device__ __forceinline__ void load_acc(C acc[NJ], const C* __restrict__ X, int64_t n, int64_t row0,
                                          int col0, int ncols) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
+  for (int jj = 0; jj < NJ; ++jj) {
     const int c = warp + 8 * jj;
     const int64_t i = row0 + lane;
     acc[jj] = (i < n && col0 + c < ncols) ? X[i + (int64_t)(col0 + c) * n] : cmk<C>(0, 0);
   }
 }
 
-template <typename C>
-__device__ __forceinline__ void put_acc(C* dst, int ldd, const C acc[4]) {
+template <typename C, int NJ>
+__device__ __forceinline__ void put_acc(C* dst, int ldd, const C acc[NJ]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) dst[lane + (warp + 8 * jj) * ldd] = acc[jj];
+  for (int jj = 0; jj < NJ; ++jj) dst[lane + (warp + 8 * jj) * ldd] = acc[jj];
 }
 
-template <typename C>
-__device__ __forceinline__ void get_acc(C acc[4], const C* src, int lds) {
+template <typename C, int NJ>
+__device__ __forceinline__ void get_acc(C acc[NJ], const C* src, int lds) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) acc[jj] = src[lane + (warp + 8 * jj) * lds];
+  for (int jj = 0; jj < NJ; ++jj) acc[jj] = src[lane + (warp + 8 * jj) * lds];
+}
+
+template <typename C, int NJ>
+__device__ __forceinline__ void zero_acc(C acc[NJ]) {
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj) acc[jj] = cmk<C>(0, 0);
 }
 
 // ---------------------------------------------------------------------------
-// trans = 0: forward (P, L) then backward (U)
+// trans = 0: forward (P, L) then backward (U), for columns col0 .. col0+CW-1
 // ---------------------------------------------------------------------------
-template <typename C>
-__global__ void __launch_bounds__(kThreads) solve_n_kernel(FactorGeom g, const SysDesc* sys,
-                                                          const char* arena, const C* rhs, C* out) {
-  extern __shared__ __align__(16) char smem[];
+template <typename C, int CW>
+__device__ void solve_n_body(const FactorGeom& g, const SysDesc& d, int col0, const char* arena, const C* rhs,
+                             C* out, char* smem) {
+  constexpr int NJ = CW / 8;
   const int T = kTile, bt = g.bt;
   const int Pmax = (bt + 1) * T;
   const int ldw = Pmax;
-  const SysDesc d = sys[blockIdx.y];
-  const int col0 = blockIdx.x * kCW;
-  if (col0 >= d.ncols) return;
   const FactorPtr<C> f = factor_ptr<C>(g, (char*)arena + d.factor_off);
   const C* Y = rhs + d.rhs_off;
   C* X = out + d.out_off;
@@ -383,50 +389,50 @@ __global__ void __launch_bounds__(kThreads) solve_n_kernel(FactorGeom g, const S
   const int tid = threadIdx.x;
 
   C* Tb = (C*)smem;                    // T x kLdt
-  C* tS = Tb + T * kLdt;               // T x kCW
-  C* U0 = tS + T * kCW;                // union area
-  C* Wn = U0;                          // Pmax x kCW
-  C* G = U0 + (size_t)Pmax * kCW;      // Pmax x kCW
-  C* xwin = U0;                        // 2bt slots of T x kCW
+  C* tS = Tb + T * kLdt;               // T x CW
+  C* U0 = tS + T * CW;                 // union area
+  C* Wn = U0;                          // Pmax x CW
+  C* G = U0 + (size_t)Pmax * CW;       // Pmax x CW
+  C* xwin = U0;                        // 2bt slots of T x CW
 
   // ---------------- forward ----------------
   {
     const int nbb0 = min(bt, g.Nb - 1);
-    for (int q = 0; q <= nbb0; ++q) load_rhs_block(Wn + q * T, ldw, Y, n, (int64_t)q * T, col0, ncols);
+    for (int q = 0; q <= nbb0; ++q) load_rhs_block<C, NJ>(Wn + q * T, ldw, Y, n, (int64_t)q * T, col0, ncols);
     __syncthreads();
     for (int K = 0; K < g.Nb; ++K) {
       const int nbb = min(bt, g.Nb - 1 - K);
       const int P = (nbb + 1) * T;
       const int16_t* pm = f.perm + (int64_t)K * Pmax;
-      for (int e = tid; e < P * kCW; e += blockDim.x) {
+      for (int e = tid; e < P * CW; e += blockDim.x) {
         const int r = e % P, c = e / P;
         G[r + c * ldw] = Wn[pm[r] + c * ldw];
       }
       load_tile<C, false>(Tb, f.inv + (int64_t)(2 * K) * g.tile_elems);
       __syncthreads();
-      C acc[4];
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) acc[jj] = cmk<C>(0, 0);
-      tile_mul<C, false>(acc, Tb, G, ldw);
+      C acc[NJ];
+      zero_acc<C, NJ>(acc);
+      tile_mul<C, NJ, false>(acc, Tb, G, ldw);
       __syncthreads();
-      put_acc(G, ldw, acc);
-      store_rows(X, n, (int64_t)K * T, col0, ncols, acc);
+      put_acc<C, NJ>(G, ldw, acc);
+      store_rows<C, NJ>(X, n, (int64_t)K * T, col0, ncols, acc);
       __syncthreads();
       for (int q = 1; q <= nbb; ++q) {
         load_tile<C, false>(Tb, f.tiles + g.tile_index(K + q, K) * g.tile_elems);
         __syncthreads();
-        get_acc(acc, G + q * T, ldw);
-        tile_mul<C, true>(acc, Tb, G, ldw);
-        put_acc(G + q * T, ldw, acc);
+        get_acc<C, NJ>(acc, G + q * T, ldw);
+        tile_mul<C, NJ, true>(acc, Tb, G, ldw);
+        put_acc<C, NJ>(G + q * T, ldw, acc);
         __syncthreads();
       }
       if (K + 1 < g.Nb) {
-        for (int e = tid; e < nbb * T * kCW; e += blockDim.x) {
+        for (int e = tid; e < nbb * T * CW; e += blockDim.x) {
           const int r = e % (nbb * T), c = e / (nbb * T);
           Wn[r + c * ldw] = G[T + r + c * ldw];
         }
         const int nbn = min(bt, g.Nb - 2 - K);
-        if (nbn == nbb) load_rhs_block(Wn + nbb * T, ldw, Y, n, (int64_t)(K + bt + 1) * T, col0, ncols);
+        if (nbn == nbb)
+          load_rhs_block<C, NJ>(Wn + nbb * T, ldw, Y, n, (int64_t)(K + bt + 1) * T, col0, ncols);
         __syncthreads();
       }
     }
@@ -436,22 +442,21 @@ __global__ void __launch_bounds__(kThreads) solve_n_kernel(FactorGeom g, const S
     const int ns = 2 * bt;
     for (int K = g.Nb - 1; K >= 0; --K) {
       const int nbr = min(2 * bt, g.Nb - 1 - K);
-      C acc[4];
-      load_acc(acc, X, n, (int64_t)K * T, col0, ncols);
+      C acc[NJ];
+      load_acc<C, NJ>(acc, X, n, (int64_t)K * T, col0, ncols);
       for (int q = 1; q <= nbr; ++q) {
         load_tile<C, false>(Tb, f.tiles + g.tile_index(K, K + q) * g.tile_elems);
         __syncthreads();
-        tile_mul<C, true>(acc, Tb, xwin + ((K + q) % ns) * T * kCW, T);
+        tile_mul<C, NJ, true>(acc, Tb, xwin + ((K + q) % ns) * T * CW, T);
         __syncthreads();
       }
-      put_acc(tS, T, acc);
+      put_acc<C, NJ>(tS, T, acc);
       load_tile<C, false>(Tb, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
       __syncthreads();
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) acc[jj] = cmk<C>(0, 0);
-      tile_mul<C, false>(acc, Tb, tS, T);
-      put_acc(xwin + (K % ns) * T * kCW, T, acc);
-      store_rows(X, n, (int64_t)K * T, col0, ncols, acc);
+      zero_acc<C, NJ>(acc);
+      tile_mul<C, NJ, false>(acc, Tb, tS, T);
+      put_acc<C, NJ>(xwin + (K % ns) * T * CW, T, acc);
+      store_rows<C, NJ>(X, n, (int64_t)K * T, col0, ncols, acc);
       __syncthreads();
     }
   }
@@ -460,16 +465,13 @@ __global__ void __launch_bounds__(kThreads) solve_n_kernel(FactorGeom g, const S
 // ---------------------------------------------------------------------------
 // trans = 1: forward U^H, backward L^H then P^T
 // ---------------------------------------------------------------------------
-template <typename C>
-__global__ void __launch_bounds__(kThreads) solve_c_kernel(FactorGeom g, const SysDesc* sys,
-                                                          const char* arena, const C* rhs, C* out) {
-  extern __shared__ __align__(16) char smem[];
+template <typename C, int CW>
+__device__ void solve_c_body(const FactorGeom& g, const SysDesc& d, int col0, const char* arena, const C* rhs,
+                             C* out, char* smem) {
+  constexpr int NJ = CW / 8;
   const int T = kTile, bt = g.bt;
   const int Pmax = (bt + 1) * T;
   const int ldw = Pmax;
-  const SysDesc d = sys[blockIdx.y];
-  const int col0 = blockIdx.x * kCW;
-  if (col0 >= d.ncols) return;
   const FactorPtr<C> f = factor_ptr<C>(g, (char*)arena + d.factor_off);
   const C* Y = rhs + d.rhs_off;
   C* X = out + d.out2_off;
@@ -479,32 +481,31 @@ __global__ void __launch_bounds__(kThreads) solve_c_kernel(FactorGeom g, const S
 
   C* Tb = (C*)smem;
   C* tS = Tb + T * kLdt;
-  C* U0 = tS + T * kCW;
-  C* wwin = U0;                        // 2bt slots of T x kCW
-  C* V = U0;                           // Pmax x kCW
-  C* Vn = U0 + (size_t)Pmax * kCW;     // Pmax x kCW
+  C* U0 = tS + T * CW;
+  C* wwin = U0;                        // 2bt slots of T x CW
+  C* V = U0;                           // Pmax x CW
+  C* Vn = U0 + (size_t)Pmax * CW;      // Pmax x CW
 
   // ---------------- forward: U^H w = y ----------------
   {
     const int ns = 2 * bt;
     for (int K = 0; K < g.Nb; ++K) {
-      C acc[4];
-      load_acc(acc, Y, n, (int64_t)K * T, col0, ncols);
+      C acc[NJ];
+      load_acc<C, NJ>(acc, Y, n, (int64_t)K * T, col0, ncols);
       const int nq = min(2 * bt, K);
       for (int q = 1; q <= nq; ++q) {
         load_tile<C, true>(Tb, f.tiles + g.tile_index(K - q, K) * g.tile_elems);
         __syncthreads();
-        tile_mul<C, true>(acc, Tb, wwin + ((K - q) % ns) * T * kCW, T);
+        tile_mul<C, NJ, true>(acc, Tb, wwin + ((K - q) % ns) * T * CW, T);
         __syncthreads();
       }
-      put_acc(tS, T, acc);
+      put_acc<C, NJ>(tS, T, acc);
       load_tile<C, true>(Tb, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
       __syncthreads();
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) acc[jj] = cmk<C>(0, 0);
-      tile_mul<C, false>(acc, Tb, tS, T);
-      put_acc(wwin + (K % ns) * T * kCW, T, acc);
-      store_rows(X, n, (int64_t)K * T, col0, ncols, acc);
+      zero_acc<C, NJ>(acc);
+      tile_mul<C, NJ, false>(acc, Tb, tS, T);
+      put_acc<C, NJ>(wwin + (K % ns) * T * CW, T, acc);
+      store_rows<C, NJ>(X, n, (int64_t)K * T, col0, ncols, acc);
       __syncthreads();
     }
   }
@@ -513,24 +514,23 @@ __global__ void __launch_bounds__(kThreads) solve_c_kernel(FactorGeom g, const S
     for (int K = g.Nb - 1; K >= 0; --K) {
       const int nbb = min(bt, g.Nb - 1 - K);
       const int P = (nbb + 1) * T;
-      C acc[4];
-      load_acc(acc, X, n, (int64_t)K * T, col0, ncols);
+      C acc[NJ];
+      load_acc<C, NJ>(acc, X, n, (int64_t)K * T, col0, ncols);
       for (int q = 1; q <= nbb; ++q) {
         load_tile<C, true>(Tb, f.tiles + g.tile_index(K + q, K) * g.tile_elems);
         __syncthreads();
-        tile_mul<C, true>(acc, Tb, V + q * T, ldw);
+        tile_mul<C, NJ, true>(acc, Tb, V + q * T, ldw);
         __syncthreads();
       }
-      put_acc(tS, T, acc);
+      put_acc<C, NJ>(tS, T, acc);
       load_tile<C, true>(Tb, f.inv + (int64_t)(2 * K) * g.tile_elems);
       __syncthreads();
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) acc[jj] = cmk<C>(0, 0);
-      tile_mul<C, false>(acc, Tb, tS, T);
-      put_acc(V, ldw, acc);
+      zero_acc<C, NJ>(acc);
+      tile_mul<C, NJ, false>(acc, Tb, tS, T);
+      put_acc<C, NJ>(V, ldw, acc);
       __syncthreads();
       const int16_t* pm = f.perm + (int64_t)K * Pmax;
-      for (int e = tid; e < P * kCW; e += blockDim.x) {
+      for (int e = tid; e < P * CW; e += blockDim.x) {
         const int r = e % P, c = e / P;
         Vn[pm[r] + c * ldw] = V[r + c * ldw];
       }
@@ -538,11 +538,11 @@ __global__ void __launch_bounds__(kThreads) solve_c_kernel(FactorGeom g, const S
       if (nbb == bt) {
         // block K+bt is final
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) acc[jj] = Vn[bt * T + (tid & 31) + ((tid >> 5) + 8 * jj) * ldw];
-        store_rows(X, n, (int64_t)(K + bt) * T, col0, ncols, acc);
+        for (int jj = 0; jj < NJ; ++jj) acc[jj] = Vn[bt * T + (tid & 31) + ((tid >> 5) + 8 * jj) * ldw];
+        store_rows<C, NJ>(X, n, (int64_t)(K + bt) * T, col0, ncols, acc);
       }
       const int nbn = min(bt, g.Nb - K);  // window blocks kept for step K-1 (beyond its top block)
-      for (int e = tid; e < nbn * T * kCW; e += blockDim.x) {
+      for (int e = tid; e < nbn * T * CW; e += blockDim.x) {
         const int r = e % (nbn * T), c = e / (nbn * T);
         V[T + r + c * ldw] = Vn[r + c * ldw];
       }
@@ -551,23 +551,47 @@ __global__ void __launch_bounds__(kThreads) solve_c_kernel(FactorGeom g, const S
     // remaining window blocks 0 .. min(bt, Nb)-1 sit in V[T : ...]
     const int nrem = min(bt, g.Nb);
     for (int q = 0; q < nrem; ++q) {
-      C acc[4];
+      C acc[NJ];
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) acc[jj] = V[T + q * T + (tid & 31) + ((tid >> 5) + 8 * jj) * ldw];
-      store_rows(X, n, (int64_t)q * T, col0, ncols, acc);
+      for (int jj = 0; jj < NJ; ++jj) acc[jj] = V[T + q * T + (tid & 31) + ((tid >> 5) + 8 * jj) * ldw];
+      store_rows<C, NJ>(X, n, (int64_t)q * T, col0, ncols, acc);
     }
+  }
+}
+
+// Persistent solve: the grid holds as many blocks as fit on the GPU at once;
+// each block takes (system, column block) items from a shared counter until
+// the list is exhausted, so systems of uneven m0 keep every SM busy.
+template <typename C, int CW, int TRANS>
+__global__ void __launch_bounds__(kThreads) solve_kernel(FactorGeom g, const SysDesc* sys, const char* arena,
+                                                        const C* rhs, C* out, const int2* items, int nitems,
+                                                        int* counter) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ int sh_item;
+  for (;;) {
+    if (threadIdx.x == 0) sh_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = sh_item;
+    __syncthreads();  // every thread has its item before thread 0 fetches the next one
+    if (item >= nitems) return;
+    const int2 w = items[item];
+    const SysDesc d = sys[w.x];
+    if (TRANS == 0)
+      solve_n_body<C, CW>(g, d, w.y, arena, rhs, out, smem);
+    else
+      solve_c_body<C, CW>(g, d, w.y, arena, rhs, out, smem);
+    __syncthreads();
   }
 }
 
 size_t solve_smem_bytes(const FactorGeom& g, int chunk, size_t es, int trans) {
   (void)trans;
-  (void)chunk;
   const int T = kTile;
   const size_t Pmax = (size_t)(g.bt + 1) * T;
-  size_t uni = 2 * Pmax * kCW;
-  size_t win = (size_t)2 * g.bt * T * kCW;
+  size_t uni = 2 * Pmax * (size_t)chunk;
+  size_t win = (size_t)2 * g.bt * T * chunk;
   if (win > uni) uni = win;
-  return es * ((size_t)T * kLdt + (size_t)T * kCW + uni);
+  return es * ((size_t)T * kLdt + (size_t)T * chunk + uni);
 }
 
 static size_t factor_smem_bytes(const FactorGeom& g, size_t es) {
@@ -595,36 +619,73 @@ int launch_factor(const FactorGeom& g, int cplx, const void* band, int64_t ldab,
   return 0;
 }
 
-template <typename C>
-int launch_solve(const FactorGeom& g, int trans, int nsys, int max_cols, const SysDesc* d_sys,
-                 const char* factor_arena, const C* rhs_arena, C* out_arena, int chunk,
-                 cudaStream_t st) {
-  (void)chunk;
-  if (nsys <= 0 || max_cols <= 0) return 0;
-  const size_t smem = solve_smem_bytes(g, kCW, sizeof(C), trans);
+// Scratch of the solve work queue for nsys systems of at most max_cols
+// right-hand sides (enough for the narrowest column block, 16).
+size_t solve_queue_bytes(int nsys, int max_cols) {
+  Arena a;
+  a.take<int>(1);
+  a.take<int2>((size_t)nsys * ceil_div(max_cols, 16));
+  return a.used();
+}
+
+template <typename C, int CW, int TRANS>
+static int launch_solve_cw(const FactorGeom& g, int nsys, const SysDesc* h_sys, const SysDesc* d_sys,
+                           const char* factor_arena, const C* rhs_arena, C* out_arena, void* queue,
+                           cudaStream_t st) {
+  const size_t smem = solve_smem_bytes(g, CW, sizeof(C), TRANS);
   if (smem > 227 * 1024) {
-    set_last_error_msg("band too wide for the solve kernel's shared memory");
+    set_last_error_msg("band too wide for the solve kernel's shared memory at this column block");
     return PDESHEP_CUDA_ERROR;
   }
-  dim3 grid((unsigned)ceil_div(max_cols, kCW), (unsigned)nsys);
-  if (trans == 0) {
-    PD_CK(cudaFuncSetAttribute(solve_n_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    solve_n_kernel<C><<<grid, kThreads, smem, st>>>(g, d_sys, factor_arena, rhs_arena, out_arena);
-  } else {
-    PD_CK(cudaFuncSetAttribute(solve_c_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    solve_c_kernel<C><<<grid, kThreads, smem, st>>>(g, d_sys, factor_arena, rhs_arena, out_arena);
-  }
+  // queue layout: the counter, then the (system, first column) items
+  std::vector<int2> it;
+  for (int s = 0; s < nsys; ++s)
+    for (int c = 0; c < h_sys[s].ncols; c += CW) it.push_back(make_int2(s, c));
+  const int nitems = (int)it.size();
+  if (!nitems) return 0;
+  Arena qa(queue, ~size_t(0));
+  int* counter = qa.take<int>(1);
+  int2* d_items = qa.take<int2>((size_t)nitems);
+  PD_CK(cudaMemsetAsync(counter, 0, sizeof(int), st));
+  PD_CK(cudaMemcpyAsync(d_items, it.data(), sizeof(int2) * nitems, cudaMemcpyHostToDevice, st));
+  auto kern = solve_kernel<C, CW, TRANS>;
+  PD_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, dev = 0, sms = 0;
+  PD_CK(cudaGetDevice(&dev));
+  PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+  const int grid = std::max(1, std::min(nitems, sms * std::max(1, per_sm)));
+  kern<<<grid, kThreads, smem, st>>>(g, d_sys, factor_arena, rhs_arena, out_arena, d_items, nitems, counter);
   PD_CK_LAUNCH();
   return 0;
+}
+
+template <typename C>
+int launch_solve(const FactorGeom& g, int trans, int nsys, const SysDesc* h_sys, const SysDesc* d_sys,
+                 const char* factor_arena, const C* rhs_arena, C* out_arena, int chunk, void* queue,
+                 cudaStream_t st) {
+  if (nsys <= 0) return 0;
+  if (chunk <= 0) chunk = 32;
+  switch (chunk * 2 + (trans ? 1 : 0)) {
+    case 32: return launch_solve_cw<C, 16, 0>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    case 33: return launch_solve_cw<C, 16, 1>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    case 64: return launch_solve_cw<C, 32, 0>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    case 65: return launch_solve_cw<C, 32, 1>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    case 128: return launch_solve_cw<C, 64, 0>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    case 129: return launch_solve_cw<C, 64, 1>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    default:
+      set_last_error_msg("right-hand-side block width must be 16, 32 or 64");
+      return PDESHEP_CUDA_ERROR;
+  }
 }
 
 template int launch_factor<float2>(const FactorGeom&, int, const void*, int64_t, int, const SysDesc*,
                                    char*, int*, int32_t*, cudaStream_t);
 template int launch_factor<double2>(const FactorGeom&, int, const void*, int64_t, int, const SysDesc*,
                                     char*, int*, int32_t*, cudaStream_t);
-template int launch_solve<float2>(const FactorGeom&, int, int, int, const SysDesc*, const char*,
-                                  const float2*, float2*, int, cudaStream_t);
-template int launch_solve<double2>(const FactorGeom&, int, int, int, const SysDesc*, const char*,
-                                   const double2*, double2*, int, cudaStream_t);
+template int launch_solve<float2>(const FactorGeom&, int, int, const SysDesc*, const SysDesc*, const char*,
+                                  const float2*, float2*, int, void*, cudaStream_t);
+template int launch_solve<double2>(const FactorGeom&, int, int, const SysDesc*, const SysDesc*, const char*,
+                                   const double2*, double2*, int, void*, cudaStream_t);
 
 }  // namespace pdeshep

@@ -86,11 +86,15 @@ int launch_factor(const FactorGeom& g, int cplx, const void* band, int64_t ldab,
                   cudaStream_t st);
 
 // trans = 0: X = (zI-B)^{-1} Y;  trans = 1: X = (zI-B)^{-H} Y.  Y and X hold C.
+// h_sys: the same descriptors on the host (their column counts build the work
+// list).  chunk: right-hand sides per work item (16, 32 or 64; 0 = 32).
+// queue: device scratch of solve_queue_bytes(nsys, max columns).
 template <typename C>
-int launch_solve(const FactorGeom& g, int trans, int nsys, int max_cols, const SysDesc* d_sys,
-                 const char* factor_arena, const C* rhs_arena, C* out_arena, int chunk,
+int launch_solve(const FactorGeom& g, int trans, int nsys, const SysDesc* h_sys, const SysDesc* d_sys,
+                 const char* factor_arena, const C* rhs_arena, C* out_arena, int chunk, void* queue,
                  cudaStream_t st);
 
 size_t solve_smem_bytes(const FactorGeom& g, int chunk, size_t es, int trans);
+size_t solve_queue_bytes(int nsys, int max_cols);
 
 }  // namespace pdeshep

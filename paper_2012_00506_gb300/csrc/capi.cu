@@ -38,6 +38,7 @@ struct ShiftedWs {
   void* out;
   SysDesc* sys;
   int* status;
+  void* queue;
 };
 
 static ShiftedWs plan_shifted(Arena& a, const FactorGeom& g, int nshift, int nrhs, size_t es) {
@@ -48,6 +49,7 @@ static ShiftedWs plan_shifted(Arena& a, const FactorGeom& g, int nshift, int nrh
   w.out = a.take<char>((size_t)g.n * nrhs * nshift * es);
   w.sys = a.take<SysDesc>(nshift);
   w.status = a.take<int>(nshift);
+  w.queue = a.take<char>(solve_queue_bytes(nshift, nrhs));
   return w;
 }
 
@@ -74,7 +76,8 @@ static int shifted_solve(int64_t n, int b, int cplx, const void* band, int64_t l
   PD_CK(cudaMemcpyAsync(w.sys, sd.data(), sizeof(SysDesc) * nshift, cudaMemcpyHostToDevice, st));
   PD_TRY(launch_cast<double2, C>(n * nrhs, d_rhs, (C*)w.rhs, st));
   PD_TRY(launch_factor<C>(g, cplx, band, ldab, nshift, w.sys, w.factors, w.status, d_ipiv, st));
-  PD_TRY(launch_solve<C>(g, trans, nshift, nrhs, w.sys, w.factors, (const C*)w.rhs, (C*)w.out, 0, st));
+  PD_TRY(launch_solve<C>(g, trans, nshift, sd.data(), w.sys, w.factors, (const C*)w.rhs, (C*)w.out, 0, w.queue,
+                         st));
   PD_TRY(launch_cast<C, double2>(n * nrhs * nshift, (const C*)w.out, d_x, st));
   std::vector<int> status(nshift);
   PD_CK(cudaMemcpyAsync(status.data(), w.status, sizeof(int) * nshift, cudaMemcpyDeviceToHost, st));

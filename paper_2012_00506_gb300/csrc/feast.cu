@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "band_lu.cuh"
@@ -32,6 +33,9 @@ namespace pdeshep {
 
 // from other translation units
 size_t inertia_ws_bytes(int b, int cplx, int nsigma);
+std::string tune_key(const char* what, int64_t n, int b, int cplx, int precision, int nsys, int max_cols);
+int tune_lookup(const char* path, const std::string& key, int* value);
+void tune_store(const char* path, const std::string& key, int value);
 int inertia_counts_async(int64_t n, int b, int cplx, const void* band, int64_t ldab, int nsigma,
                          const double* h_sigma, void* work, size_t wbytes, cudaStream_t st,
                          const int64_t** d_neg, const int** d_bad);
@@ -369,6 +373,7 @@ struct Plan {
   char* inertia_ws;
   size_t inertia_bytes;
   void* band_ff;   // float-float copy of the band (mixed precision only)
+  void* solve_queue; // work list of the persistent solves
   // wave area
   char* wave_base;
   size_t wave_bytes;
@@ -531,6 +536,7 @@ struct Feast {
     q.inertia_bytes = std::max(inertia_ws_bytes(b, cplx, K + 1), bisect_ws_bytes(b, cplx, 2, 16));
     q.inertia_ws = a.take<char>(q.inertia_bytes);
     q.band_ff = ff() ? (void*)a.take<char>(band_split_bytes(n, b, cplx)) : nullptr;
+    q.solve_queue = a.take<char>(solve_queue_bytes(K * ne, max_m0));
     if (carve) {
       p = q;
       eig.ff = ff();
@@ -540,7 +546,30 @@ struct Feast {
 
   // Mixed precision runs the FP64-class products of the Rayleigh-Ritz step in
   // float-float arithmetic on the FP32 pipes; plain FEAST keeps them in FP64.
-  int ff() const { return o->precision == PDESHEP_MIXED ? 1 : 0; }
+  int ff() const { return o->precision == PDESHEP_MIXED && o->rr_arith == PDESHEP_RR_FLOATFLOAT ? 1 : 0; }
+
+  // autotuned choices (see tune.cu)
+  int rhs_chunk = 32;
+  int gram_splits = 0;  // 0: heuristic
+  bool tune_solve = false, tune_gram = false;
+
+  void setup_tuning() {
+    rhs_chunk = o->rhs_chunk > 0 ? o->rhs_chunk : 32;
+    if (o->autotune <= 0) return;
+    int v = 0;
+    if (o->rhs_chunk <= 0) {
+      const std::string k = tune_key("solve", n, b, cplx, o->precision, K * ne, max_m0);
+      if (o->autotune == 1 && tune_lookup(o->tune_cache, k, &v))
+        rhs_chunk = v;
+      else
+        tune_solve = true;
+    }
+    const std::string kg = tune_key("gram", n, b, cplx, o->precision * 2 + ff(), K, max_m0);
+    if (o->autotune == 1 && tune_lookup(o->tune_cache, kg, &v))
+      gram_splits = v;
+    else
+      tune_gram = true;
+  }
 
   size_t per_system_bytes(int s) const {
     return fb + (((size_t)n * m0[s] * (cplx ? 2 : 1) * es + 255) & ~size_t(255));
@@ -631,6 +660,34 @@ struct FeastRun : Feast<S, C> {
       const int64_t tiles = (int64_t)na * t1 * (t1 + 1) / 2;
       int splits = (int)std::min<int64_t>(p.splits, std::max<int64_t>(1, ceil_div(8 * 152, tiles)));
       splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, n / 512));
+      if (this->tune_gram) {
+        cudaEvent_t e0, e1;
+        PD_CK(cudaEventCreate(&e0));
+        PD_CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int best_s = splits;
+        for (int sp : {2, 4, 8}) {
+          if (sp > p.splits || (int64_t)sp > std::max<int64_t>(1, n / 256)) continue;
+          PD_CK(cudaEventRecord(e0, st));
+          PD_TRY(launch_gemm<S>(true, na, d_it, mm, mm, (int)n, one, zero, sp, (S*)p.part, Msq, st, 1, 0, ff));
+          PD_CK(cudaEventRecord(e1, st));
+          PD_CK(cudaEventSynchronize(e1));
+          float ms = 0;
+          PD_CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            best_s = sp;
+          }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        this->gram_splits = best_s;
+        this->tune_gram = false;
+        stats.tuned += 1;
+        tune_store(o->tune_cache, tune_key("gram", n, b, cplx, o->precision * 2 + ff, K, max_m0), best_s);
+      }
+      if (this->gram_splits > 0) splits = std::min(this->gram_splits, p.splits);
+      stats.gram_splits_used = splits;
       PD_TRY(launch_gemm<S>(true, na, d_it, mm, mm, (int)n, one, zero, splits, (S*)p.part, Msq, st, 1, 0, ff));
     } else {
       PD_TRY(launch_gemm<S>(false, na, d_it, (int)n, mm, mm, one, zero, 1, (S*)p.part, Msq, st, 0, tri, ff));
@@ -813,9 +870,42 @@ struct FeastRun : Feast<S, C> {
     double cols = 0.0;
     for (auto& d : sd) cols += d.ncols;
     PD_TRY(this->kt.begin(PDESHEP_KG_SOLVE));
-    PD_TRY(launch_solve<C>(g, 0, ns, mcols, p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, 0, st));
+    if (this->tune_solve) {
+      // time the forward solves at each column block on these very systems
+      // (each run rewrites the same outputs) and keep the fastest
+      cudaEvent_t t0, t1;
+      PD_CK(cudaEventCreate(&t0));
+      PD_CK(cudaEventCreate(&t1));
+      float best = 1e30f;
+      int best_cw = 32;
+      for (int cw : {16, 32, 64}) {
+        if (solve_smem_bytes(g, cw, sizeof(C), 0) > 227 * 1024) continue;
+        PD_CK(cudaEventRecord(t0, st));
+        PD_TRY(launch_solve<C>(g, 0, ns, sd.data(), p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, cw,
+                               p.solve_queue, st));
+        PD_CK(cudaEventRecord(t1, st));
+        PD_CK(cudaEventSynchronize(t1));
+        float ms = 0;
+        PD_CK(cudaEventElapsedTime(&ms, t0, t1));
+        if (ms < best) {
+          best = ms;
+          best_cw = cw;
+        }
+      }
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      this->rhs_chunk = best_cw;
+      this->tune_solve = false;
+      stats.tuned += 1;
+      tune_store(o->tune_cache, tune_key("solve", n, b, cplx, o->precision, K * ne, max_m0), best_cw);
+    }
+    const int chunk = this->rhs_chunk;
+    stats.rhs_chunk_used = chunk;
+    PD_TRY(launch_solve<C>(g, 0, ns, sd.data(), p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, chunk,
+                           p.solve_queue, st));
     if (cplx)
-      PD_TRY(launch_solve<C>(g, 1, ns, mcols, p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, 0, st));
+      PD_TRY(launch_solve<C>(g, 1, ns, sd.data(), p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, chunk,
+                             p.solve_queue, st));
     PD_TRY(this->kt.end(24.0 * (double)n * b * cols * (cplx ? 2 : 1)));
     for (auto& d : sd) stats.rhs_sweeps += ceil_div(d.ncols, 32) * (cplx ? 2 : 1);
     stats.rhs_columns += (int64_t)cols * (cplx ? 2 : 1);
@@ -953,6 +1043,7 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   F.M = acc;
   F.Msq = accs;
   memset(&F.stats, 0, sizeof(F.stats));
+  F.setup_tuning();
   // workspace plan
   Arena a(d_work, work_bytes);
   F.fixed_bytes(a, true);
@@ -1169,7 +1260,10 @@ int check_slice_args(int64_t n, int32_t b, const void* d_band, int64_t ldab, int
   for (int s = 0; s < K; ++s)
     if (h_m0[s] < 1 || h_m0[s] > n || h_m0[s] > 4096) return -11;
   if (o && (!(o->tol > 0.0) || o->max_iter < 0 || (o->precision != PDESHEP_FP64 && o->precision != PDESHEP_MIXED) ||
-            !(o->ellipse_ratio > 0.0)))
+            !(o->ellipse_ratio > 0.0) ||
+            (o->rhs_chunk != 0 && o->rhs_chunk != 16 && o->rhs_chunk != 32 && o->rhs_chunk != 64) ||
+            (o->rr_arith != PDESHEP_RR_FLOATFLOAT && o->rr_arith != PDESHEP_RR_FP64) || o->autotune < 0 ||
+            o->autotune > 2))
     return -15;
   return 0;
 }

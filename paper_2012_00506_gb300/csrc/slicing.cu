@@ -195,6 +195,8 @@ extern "C" void pdeshep_opts_default(pdeshep_opts* o) {
   o->autotune = 0;
   o->verbose = 0;
   o->stream = nullptr;
+  o->rr_arith = PDESHEP_RR_FLOATFLOAT;
+  o->tune_cache = nullptr;
 }
 
 extern "C" int pdeshep_contour_rule(int32_t ne, double lo, double hi, double rho, pdeshep_c128* h_z,

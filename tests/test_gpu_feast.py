@@ -137,3 +137,87 @@ def test_mixed_eigensolver_needs_no_fallback(device, cplx):
     assert st["eig_refine_steps"] > 0
     assert st["eig_fallback_unconverged"] == 0 and st["eig_fallback_wide"] == 0, st
     assert st["jacobi_sweeps64"] == 0
+
+
+def _small_problem(device, cplx, seed=77, n=1200, b=16, ks=(40, 160, 200, 460)):
+    ab = synth.random_band(n, b, seed, cplx)
+    bounds = _bounds(ab, list(ks))
+    m0 = [oracle.m0_rule(ks[i + 1] - ks[i]) for i in range(len(ks) - 1)]   # uneven: 120+, 40+, 260+
+    X0 = synth.random_subspace(n, int(sum(m0)), 4, cplx)
+    return ab, bounds, m0, X0
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_rhs_block_width_does_not_change_results(device, cplx):
+    """The persistent solves give the same bits for work items of 16, 32 or 64
+    right-hand sides (each column's arithmetic is independent of the grouping)."""
+    import paper_2012_00506_gb300 as pk
+    ab, bounds, m0, X0 = _small_problem(device, cplx)
+    band = to_dev(ab, device)
+    outs = []
+    for cw in (16, 32, 64):
+        r = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), precision=pk.MIXED,
+                          bnorm=oracle.spectral_norm(ab), rhs_chunk=cw, max_iter=30)
+        assert r.status == 0 and r.stats["rhs_chunk_used"] == cw
+        outs.append((r.evals.cpu().numpy(), r.evecs.cpu().numpy(), list(r.nfound)))
+    for e, v, nf in outs[1:]:
+        assert nf == outs[0][2]
+        assert np.array_equal(e, outs[0][0]) and np.array_equal(v, outs[0][1])
+
+
+def test_uneven_slices_against_oracle(device):
+    """Slices of 120, 40 and 260 eigenvalues in one batch (the uneven-m0 case the
+    work queue balances) match the oracle slice by slice."""
+    _run_compare(device, synth.random_band(1200, 16, 78, True), [40, 160, 200, 460],
+                 [oracle.m0_rule(c) for c in (120, 40, 260)], 1, 21)
+
+
+def test_autotuner_measures_then_reuses(device, tmp_path):
+    import paper_2012_00506_gb300 as pk
+    ab, bounds, m0, X0 = _small_problem(device, True, seed=79)
+    band = to_dev(ab, device)
+    bn = oracle.spectral_norm(ab)
+    cache = str(tmp_path / "tune.txt")
+    pk.load().pdeshep_tune_reset()
+    r1 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, autotune=2, tune_cache=cache)
+    assert r1.status == 0 and r1.stats["tuned"] == 2
+    cw, sp = r1.stats["rhs_chunk_used"], r1.stats["gram_splits_used"]
+    assert cw in (16, 32, 64) and sp in (2, 4, 8)
+    r2 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, autotune=1, tune_cache=cache)
+    assert r2.stats["tuned"] == 0 and r2.stats["rhs_chunk_used"] == cw and r2.stats["gram_splits_used"] == sp
+    pk.load().pdeshep_tune_reset()          # in-process choices gone: the file still has them
+    r3 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, autotune=1, tune_cache=cache)
+    assert r3.stats["tuned"] == 0 and r3.stats["rhs_chunk_used"] == cw
+    lines = open(cache).read().split("\n")
+    assert any(l.startswith("solve/") for l in lines) and any(l.startswith("gram/") for l in lines)
+    for r in (r1, r2, r3):
+        assert list(r.nfound) == list(r.counts)
+    assert np.allclose(r1.evals.cpu().numpy(), r3.evals.cpu().numpy(), rtol=0, atol=1e-11 * bn)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_rr_fp64_and_floatfloat_agree(device, cplx):
+    """Mixed precision with the Rayleigh-Ritz products in FP64 or in float-float:
+    both give every in-slice eigenvalue within 1e-10 ||B|| of the dense spectrum
+    and agree with each other to 1e-11 ||B|| (each run stops at its own iterate
+    once the residuals pass 1e-10, so they are not expected to agree further)."""
+    import paper_2012_00506_gb300 as pk
+    ab, bounds, m0, X0 = _small_problem(device, cplx, seed=80)
+    band = to_dev(ab, device)
+    bn = oracle.spectral_norm(ab)
+    res = {}
+    for arith in (pk.RR_FLOATFLOAT, pk.RR_FP64):
+        r = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, rr_arith=arith, max_iter=30)
+        assert r.status == 0 and list(r.nfound) == list(r.counts)
+        res[arith] = r
+    ev = np.linalg.eigvalsh(synth.band_to_dense(ab))
+    off = 0
+    for i, m in enumerate(m0):
+        k = int(res[0].nfound[i])
+        a = res[0].evals.cpu().numpy()[off:off + k]
+        c = res[1].evals.cpu().numpy()[off:off + k]
+        truth = ev[(ev >= bounds[i]) & (ev < bounds[i + 1])]
+        assert np.max(np.abs(np.sort(a) - truth)) <= 1e-10 * bn
+        assert np.max(np.abs(np.sort(c) - truth)) <= 1e-10 * bn
+        assert np.max(np.abs(a - c)) <= 1e-11 * bn
+        off += m
