@@ -82,6 +82,11 @@ typedef struct {
   int32_t rr_arith;        /* PDESHEP_MIXED only: PDESHEP_RR_FLOATFLOAT (default) or PDESHEP_RR_FP64 */
   int32_t pad0;
   const char* tune_cache;  /* file that keeps tuned choices across processes; NULL = in-process */
+  int32_t graphs;          /* 1: with resident factors, each filter pass (right-hand sides,
+                              weights, both solves, accumulation) is captured once per set of
+                              active slices as a CUDA graph and replayed; needs a stream other
+                              than the legacy default stream.  0 (default): direct launches */
+  int32_t pad1;
 } pdeshep_opts;
 
 /* Arithmetic of the Rayleigh-Ritz products (Gram, projection, basis update,   */
@@ -136,6 +141,7 @@ typedef struct {
   int32_t rhs_chunk_used;  /* solve column block of the last filter pass */
   int32_t gram_splits_used;/* split count of the last tall Gram product */
   int32_t tuned;           /* number of choices measured by the autotuner in this call */
+  int32_t graph_launches;  /* filter passes replayed from CUDA graphs */
 } pdeshep_stats;
 
 /* Forget every tuned choice held in this process (cache files are kept). */

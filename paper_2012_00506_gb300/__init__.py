@@ -61,6 +61,7 @@ class Opts(C.Structure):
         ("bnorm", C.c_double), ("seed", C.c_uint64), ("hbm_cap_bytes", C.c_size_t),
         ("autotune", C.c_int32), ("verbose", C.c_int32), ("stream", C.c_void_p),
         ("rr_arith", C.c_int32), ("pad0", C.c_int32), ("tune_cache", C.c_char_p),
+        ("graphs", C.c_int32), ("pad1", C.c_int32),
     ]
 
 
@@ -79,6 +80,7 @@ class Stats(C.Structure):
         ("eig_refine_steps", C.c_int32), ("eig_clusters", C.c_int32), ("eig_max_cluster", C.c_int32),
         ("eig_fallback_unconverged", C.c_int32), ("eig_fallback_wide", C.c_int32),
         ("rhs_chunk_used", C.c_int32), ("gram_splits_used", C.c_int32), ("tuned", C.c_int32),
+        ("graph_launches", C.c_int32),
     ]
 
     def as_dict(self):

@@ -628,26 +628,33 @@ size_t solve_queue_bytes(int nsys, int max_cols) {
   return a.used();
 }
 
+// Work list of (system, first column) items of `chunk` right-hand sides into
+// the queue scratch (counter first, then the items).  Returns the item count.
+int upload_solve_items(int nsys, const SysDesc* h_sys, int chunk, void* queue, cudaStream_t st, int* nitems) {
+  std::vector<int2> it;
+  for (int s = 0; s < nsys; ++s)
+    for (int c = 0; c < h_sys[s].ncols; c += chunk) it.push_back(make_int2(s, c));
+  *nitems = (int)it.size();
+  if (it.empty()) return 0;
+  Arena qa(queue, ~size_t(0));
+  qa.take<int>(1);
+  int2* d_items = qa.take<int2>(it.size());
+  PD_CK(cudaMemcpyAsync(d_items, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice, st));
+  return 0;
+}
+
 template <typename C, int CW, int TRANS>
-static int launch_solve_cw(const FactorGeom& g, int nsys, const SysDesc* h_sys, const SysDesc* d_sys,
-                           const char* factor_arena, const C* rhs_arena, C* out_arena, void* queue,
-                           cudaStream_t st) {
+static int launch_solve_cw(const FactorGeom& g, int nitems, const SysDesc* d_sys, const char* factor_arena,
+                           const C* rhs_arena, C* out_arena, void* queue, cudaStream_t st) {
   const size_t smem = solve_smem_bytes(g, CW, sizeof(C), TRANS);
   if (smem > 227 * 1024) {
     set_last_error_msg("band too wide for the solve kernel's shared memory at this column block");
     return PDESHEP_CUDA_ERROR;
   }
-  // queue layout: the counter, then the (system, first column) items
-  std::vector<int2> it;
-  for (int s = 0; s < nsys; ++s)
-    for (int c = 0; c < h_sys[s].ncols; c += CW) it.push_back(make_int2(s, c));
-  const int nitems = (int)it.size();
   if (!nitems) return 0;
   Arena qa(queue, ~size_t(0));
   int* counter = qa.take<int>(1);
-  int2* d_items = qa.take<int2>((size_t)nitems);
-  PD_CK(cudaMemsetAsync(counter, 0, sizeof(int), st));
-  PD_CK(cudaMemcpyAsync(d_items, it.data(), sizeof(int2) * nitems, cudaMemcpyHostToDevice, st));
+  const int2* d_items = qa.take<int2>((size_t)nitems);
   auto kern = solve_kernel<C, CW, TRANS>;
   PD_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0, dev = 0, sms = 0;
@@ -655,9 +662,26 @@ static int launch_solve_cw(const FactorGeom& g, int nsys, const SysDesc* h_sys, 
   PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   PD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
   const int grid = std::max(1, std::min(nitems, sms * std::max(1, per_sm)));
+  PD_CK(cudaMemsetAsync(counter, 0, sizeof(int), st));
   kern<<<grid, kThreads, smem, st>>>(g, d_sys, factor_arena, rhs_arena, out_arena, d_items, nitems, counter);
   PD_CK_LAUNCH();
   return 0;
+}
+
+template <typename C>
+int launch_solve_queued(const FactorGeom& g, int trans, int nitems, const SysDesc* d_sys, const char* factor_arena,
+                        const C* rhs_arena, C* out_arena, int chunk, void* queue, cudaStream_t st) {
+  switch (chunk * 2 + (trans ? 1 : 0)) {
+    case 32: return launch_solve_cw<C, 16, 0>(g, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    case 33: return launch_solve_cw<C, 16, 1>(g, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    case 64: return launch_solve_cw<C, 32, 0>(g, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    case 65: return launch_solve_cw<C, 32, 1>(g, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    case 128: return launch_solve_cw<C, 64, 0>(g, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    case 129: return launch_solve_cw<C, 64, 1>(g, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    default:
+      set_last_error_msg("right-hand-side block width must be 16, 32 or 64");
+      return PDESHEP_CUDA_ERROR;
+  }
 }
 
 template <typename C>
@@ -666,23 +690,23 @@ int launch_solve(const FactorGeom& g, int trans, int nsys, const SysDesc* h_sys,
                  cudaStream_t st) {
   if (nsys <= 0) return 0;
   if (chunk <= 0) chunk = 32;
-  switch (chunk * 2 + (trans ? 1 : 0)) {
-    case 32: return launch_solve_cw<C, 16, 0>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
-    case 33: return launch_solve_cw<C, 16, 1>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
-    case 64: return launch_solve_cw<C, 32, 0>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
-    case 65: return launch_solve_cw<C, 32, 1>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
-    case 128: return launch_solve_cw<C, 64, 0>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
-    case 129: return launch_solve_cw<C, 64, 1>(g, nsys, h_sys, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
-    default:
-      set_last_error_msg("right-hand-side block width must be 16, 32 or 64");
-      return PDESHEP_CUDA_ERROR;
+  if (chunk != 16 && chunk != 32 && chunk != 64) {
+    set_last_error_msg("right-hand-side block width must be 16, 32 or 64");
+    return PDESHEP_CUDA_ERROR;
   }
+  int nitems = 0;
+  PD_TRY(upload_solve_items(nsys, h_sys, chunk, queue, st, &nitems));
+  return launch_solve_queued<C>(g, trans, nitems, d_sys, factor_arena, rhs_arena, out_arena, chunk, queue, st);
 }
 
 template int launch_factor<float2>(const FactorGeom&, int, const void*, int64_t, int, const SysDesc*,
                                    char*, int*, int32_t*, cudaStream_t);
 template int launch_factor<double2>(const FactorGeom&, int, const void*, int64_t, int, const SysDesc*,
                                     char*, int*, int32_t*, cudaStream_t);
+template int launch_solve_queued<float2>(const FactorGeom&, int, int, const SysDesc*, const char*, const float2*,
+                                         float2*, int, void*, cudaStream_t);
+template int launch_solve_queued<double2>(const FactorGeom&, int, int, const SysDesc*, const char*, const double2*,
+                                          double2*, int, void*, cudaStream_t);
 template int launch_solve<float2>(const FactorGeom&, int, int, const SysDesc*, const SysDesc*, const char*,
                                   const float2*, float2*, int, void*, cudaStream_t);
 template int launch_solve<double2>(const FactorGeom&, int, int, const SysDesc*, const SysDesc*, const char*,

@@ -94,6 +94,13 @@ int launch_solve(const FactorGeom& g, int trans, int nsys, const SysDesc* h_sys,
                  const char* factor_arena, const C* rhs_arena, C* out_arena, int chunk, void* queue,
                  cudaStream_t st);
 
+// The same in two steps: the work list is uploaded once (a host-to-device
+// copy, outside any stream capture), then launches replay it (capturable).
+int upload_solve_items(int nsys, const SysDesc* h_sys, int chunk, void* queue, cudaStream_t st, int* nitems);
+template <typename C>
+int launch_solve_queued(const FactorGeom& g, int trans, int nitems, const SysDesc* d_sys, const char* factor_arena,
+                        const C* rhs_arena, C* out_arena, int chunk, void* queue, cudaStream_t st);
+
 size_t solve_smem_bytes(const FactorGeom& g, int chunk, size_t es, int trans);
 size_t solve_queue_bytes(int nsys, int max_cols);
 

@@ -21,6 +21,7 @@ void set_last_error(const char* where, cudaError_t e);
 void set_last_error_msg(const char* msg);
 // process-wide count of kernels launched by this library
 void count_launch();
+void count_launches(long long k);  // k kernels run by a graph launch (or -k captured but not run)
 unsigned long long launches_so_far();
 
 #define PD_CK(...)                                    \

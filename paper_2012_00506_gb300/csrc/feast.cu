@@ -918,10 +918,115 @@ struct FeastRun : Feast<S, C> {
     return this->kt.end(8.0 * (double)n * cols * (cplx ? 2 : 1));
   }
 
+  // systems and accumulation descriptors of the active slices (resident factors)
+  void resident_descs(std::vector<SysDesc>& sd, std::vector<AccDesc>& acc) const {
+    sd.clear();
+    acc.clear();
+    for (int s : active) {
+      for (int j = 0; j < ne; ++j) sd.push_back(sys_desc(s, j, sys_off[(size_t)s * ne + j]));
+      AccDesc a;
+      a.col_off = col_off[s];
+      a.xoff0 = sd[sd.size() - ne].out_off;
+      a.xstride = (ne > 1) ? (sd[sd.size() - ne + 1].out_off - sd[sd.size() - ne].out_off) : 0;
+      a.coef_off = (int64_t)ne * col_off[s];
+      a.m0 = m0[s];
+      a.j0 = 0;
+      a.j1 = ne;
+      a.pad = 0;
+      acc.push_back(a);
+    }
+  }
+
+  // CUDA graphs of the filter pass, one per (active slices, mode)
+  struct FilterGraph {
+    std::vector<int> active;
+    int mode;
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::vector<FilterGraph> fgraphs;
+  ~FeastRun() {
+    for (auto& f : fgraphs) cudaGraphExecDestroy(f.exec);
+  }
+  bool graph_ready() const {
+    return o->graphs && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread && resident &&
+           factored && !this->tune_solve;
+  }
+
+  // the filter launches after the descriptors are on the device
+  int filter_launches(int na, int mm, int nitems) {
+    const S* src = mode ? (const S*)p.BQ : (const S*)p.Xt;
+    make_rhs_kernel<S, C><<<dim3(grid1(n * mm), na), 256, 0, st>>>(n, p.d_sd, src, mode ? p.colscale : nullptr,
+                                                                  (C*)p.Yc);
+    PD_CK_LAUNCH();
+    coef_kernel<<<dim3((unsigned)ceil_div(mm, 128), na), 128, 0, st>>>(p.d_sd, ne, p.zw, p.lam, p.colscale,
+                                                                       mode, p.coef, p.beta);
+    PD_CK_LAUNCH();
+    q_init_kernel<S><<<dim3(grid1(n * mm), na), 256, 0, st>>>(n, p.d_sd, p.beta, (const S*)p.Xt, (S*)p.Q, mode);
+    PD_CK_LAUNCH();
+    PD_TRY(launch_solve_queued<C>(g, 0, nitems, p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base,
+                                  this->rhs_chunk, p.solve_queue, st));
+    if (cplx)
+      PD_TRY(launch_solve_queued<C>(g, 1, nitems, p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base,
+                                    this->rhs_chunk, p.solve_queue, st));
+    accumulate_kernel<S, C><<<dim3(grid1(n * mm), na), 256, 0, st>>>(n, p.d_acc, p.coef, (const C*)p.wave_base,
+                                                                      (S*)p.Q, cplx);
+    PD_CK_LAUNCH();
+    return 0;
+  }
+
+  // the filter pass replayed from a CUDA graph (resident factors)
+  int filter_graph() {
+    const int na = (int)active.size();
+    PD_TRY(upload_active());
+    const int mm = act_max_m0();
+    std::vector<SysDesc> sd;
+    std::vector<AccDesc> acc;
+    resident_descs(sd, acc);
+    PD_CK(cudaMemcpyAsync(p.d_sys, sd.data(), sizeof(SysDesc) * sd.size(), cudaMemcpyHostToDevice, st));
+    PD_CK(cudaMemcpyAsync(p.d_acc, acc.data(), sizeof(AccDesc) * acc.size(), cudaMemcpyHostToDevice, st));
+    int nitems = 0;
+    PD_TRY(upload_solve_items((int)sd.size(), sd.data(), this->rhs_chunk, p.solve_queue, st, &nitems));
+    FilterGraph* fg = nullptr;
+    for (auto& f : fgraphs)
+      if (f.mode == mode && f.active == active) fg = &f;
+    if (!fg) {
+      const unsigned long long l0 = launches_so_far();
+      cudaGraph_t graph;
+      PD_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+      const int r = filter_launches(na, mm, nitems);
+      const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+      if (r) return r;
+      PD_CK(ec);
+      FilterGraph f;
+      f.active = active;
+      f.mode = mode;
+      f.kernels = (long long)(launches_so_far() - l0);
+      count_launches(-f.kernels);  // counted when they run
+      const cudaError_t ei = cudaGraphInstantiate(&f.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      PD_CK(ei);
+      fgraphs.push_back(f);
+      fg = &fgraphs.back();
+    }
+    double cols = 0.0;
+    for (auto& d : sd) cols += d.ncols;
+    PD_TRY(this->kt.begin(PDESHEP_KG_SOLVE));
+    PD_CK(cudaGraphLaunch(fg->exec, st));
+    count_launches(fg->kernels);
+    PD_TRY(this->kt.end(24.0 * (double)n * b * cols * (cplx ? 2 : 1)));
+    for (auto& d : sd) stats.rhs_sweeps += ceil_div(d.ncols, this->rhs_chunk) * (cplx ? 2 : 1);
+    stats.rhs_columns += (int64_t)cols * (cplx ? 2 : 1);
+    stats.rhs_chunk_used = this->rhs_chunk;
+    stats.graph_launches += 1;
+    return 0;
+  }
+
   // Q = filter(Xt or residuals) for the active slices
   int filter() {
     const int na = (int)active.size();
     if (!na) return 0;
+    if (graph_ready()) return filter_graph();
     PD_TRY(upload_active());
     const int mm = act_max_m0();
     const S* src = mode ? (const S*)p.BQ : (const S*)p.Xt;
@@ -946,19 +1051,7 @@ struct FeastRun : Feast<S, C> {
       }
       std::vector<SysDesc> sd;
       std::vector<AccDesc> acc;
-      for (int s : active) {
-        for (int j = 0; j < ne; ++j) sd.push_back(sys_desc(s, j, sys_off[(size_t)s * ne + j]));
-        AccDesc a;
-        a.col_off = col_off[s];
-        a.xoff0 = sd[sd.size() - ne].out_off;
-        a.xstride = (ne > 1) ? (sd[sd.size() - ne + 1].out_off - sd[sd.size() - ne].out_off) : 0;
-        a.coef_off = (int64_t)ne * col_off[s];
-        a.m0 = m0[s];
-        a.j0 = 0;
-        a.j1 = ne;
-        a.pad = 0;
-        acc.push_back(a);
-      }
+      resident_descs(sd, acc);
       return solve_and_accumulate(sd, acc);
     }
     // streaming waves: systems of the active slices packed while they fit

@@ -16,6 +16,7 @@ static thread_local char g_last_error[512] = "";
 static unsigned long long g_launches = 0;
 
 void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+void count_launches(long long k) { __atomic_add_fetch(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
 unsigned long long launches_so_far() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 void set_last_error(const char* where, cudaError_t e) {
@@ -197,6 +198,7 @@ extern "C" void pdeshep_opts_default(pdeshep_opts* o) {
   o->stream = nullptr;
   o->rr_arith = PDESHEP_RR_FLOATFLOAT;
   o->tune_cache = nullptr;
+  o->graphs = 0;
 }
 
 extern "C" int pdeshep_contour_rule(int32_t ne, double lo, double hi, double rho, pdeshep_c128* h_z,

@@ -221,3 +221,26 @@ def test_rr_fp64_and_floatfloat_agree(device, cplx):
         assert np.max(np.abs(np.sort(c) - truth)) <= 1e-10 * bn
         assert np.max(np.abs(a - c)) <= 1e-11 * bn
         off += m
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_graph_replay_matches_direct_launches(device, cplx):
+    """Filter passes replayed from CUDA graphs give the same bits as direct launches."""
+    import torch
+    import paper_2012_00506_gb300 as pk
+    ab, bounds, m0, X0 = _small_problem(device, cplx, seed=81)
+    band = to_dev(ab, device)
+    bn = oracle.spectral_norm(ab)
+    s = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(s):
+        for graphs in (0, 1):
+            r = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, graphs=graphs, stream=s,
+                              rhs_chunk=32, max_iter=30)
+            s.synchronize()
+            assert r.status == 0 and list(r.nfound) == list(r.counts)
+            outs.append(r)
+    assert outs[0].stats["graph_launches"] == 0 and outs[1].stats["graph_launches"] >= 1
+    assert outs[0].stats["iterations"] == outs[1].stats["iterations"]
+    assert np.array_equal(outs[0].evals.cpu().numpy(), outs[1].evals.cpu().numpy())
+    assert np.array_equal(outs[0].evecs.cpu().numpy(), outs[1].evecs.cpu().numpy())
