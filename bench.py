@@ -240,6 +240,7 @@ def run_gpu(args):
     kg_fl = {g: 0.0 for g in pk.KERNEL_GROUPS}
     kg_n = {g: 0 for g in pk.KERNEL_GROUPS}
     iters, statuses, sweeps, eig_rep = [], [], [], []
+    tuned_choice = {}
     for k in range(W, W + K):
         inputs.append((k, x0, bounds))
         r = seq.step(k, x0, bounds, pk.MIXED)
@@ -250,6 +251,7 @@ def run_gpu(args):
         sweeps.append((r.stats["rr_calls"], r.stats["jacobi_sweeps32"], r.stats["jacobi_sweeps64"]))
         eig_rep.append({key: r.stats[key] for key in ("eig_refine_steps", "eig_clusters", "eig_max_cluster",
                                                     "eig_fallback_unconverged", "eig_fallback_wide")})
+        tuned_choice = {"rhs_chunk": r.stats["rhs_chunk_used"], "gram_splits": r.stats["gram_splits_used"]}
         for g in pk.KERNEL_GROUPS:
             kg_ms[g] += r.stats["kg_ms"][g]
             kg_fl[g] += r.stats["kg_flops"][g]
@@ -296,7 +298,7 @@ def run_gpu(args):
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "iterations_per_step": iters, "status_per_step": statuses, "cluster_ctas": cluster_ctas,
            "rr_calls_sweeps32_sweeps64": sweeps,
-           "eigensolver": eig_rep,
+           "eigensolver": eig_rep, "autotuned": tuned_choice,
            "kernel_groups": groups, "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
 
     if rank == 0 and not args.no_plain and args.plain_steps > 0:
@@ -458,6 +460,39 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def profile_case(args):
+    """A reduced instance of the bench workload for ncu captures: the first matrix of the
+    sequence, the first `--profile-slices` slices of its partition (same n, b, m0, Ne),
+    random start vectors, two band_slice calls (the second with resident tuning choices)."""
+    import torch
+    import paper_2012_00506_gb300 as pk
+    from paper_2012_00506_gb300 import build as cb
+
+    cb.build()
+    dev = torch.device("cuda:0")
+    ab = make_sequence(1)[0]
+    band = torch.from_numpy(ab).to(dev)
+    ks = boundary_indices()[: args.profile_slices + 1]
+    idx = sorted(set([k for k in ks[1:]] + [k - 1 for k in ks[1:]] + [0]))
+    lo, hi = pk.bisect(band, idx, rtol=1e-12, fanout=8)
+    lam = {k: 0.5 * (lo[i] + hi[i]) for i, k in enumerate(idx)}
+    spacing = (lam[ks[1]] - lam[0]) / ks[1]
+    bounds = [lam[0] - 2 * spacing] + [0.5 * (lam[k - 1] + lam[k]) for k in ks[1:]]
+    m0 = [m0_rule(ks[i + 1] - ks[i]) for i in range(args.profile_slices)]
+    g = synth.rng(SEED + 999)
+    x0 = torch.from_numpy((g.normal(size=(sum(m0), N)) + 1j * g.normal(size=(sum(m0), N))) / np.sqrt(2.0)).to(dev)
+    lo2, hi2 = pk.bisect(band, [0, N - 1], rtol=1e-8, fanout=16)
+    bn = max(abs(lo2[0]), abs(hi2[0]), abs(lo2[1]), abs(hi2[1]))
+    for rep in range(2):
+        r = pk.band_slice(band, bounds, m0, x0, bnorm=bn, precision=pk.MIXED, ne=NE, tol=TOL, ellipse_ratio=RHO,
+                          max_iter=40, autotune=1, raise_on_error=False)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_case": WORKLOAD_KEY, "slices": args.profile_slices, "m0": m0, "status": r.status,
+                      "nfound": [int(v) for v in r.nfound], "counts": [int(v) for v in r.counts]}))
+    if r.status != 0 or list(r.nfound) != list(r.counts):
+        sys.exit(1)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -469,10 +504,15 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run a reduced instance of the workload (for ncu captures) instead of the bench")
+    ap.add_argument("--profile-slices", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 1:
         args.warmup = 1
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -372,6 +372,82 @@ __device__ __forceinline__ void zero_acc(C acc[NJ]) {
 }
 
 // ---------------------------------------------------------------------------
+// Factor tiles reach shared memory through a two-slot cp.async pipeline: the
+// tile of the next step is requested before the current one is used, so its
+// L2/HBM latency overlaps the current tile product.  Tiles keep their stored
+// layout (element (r, c) at r + c kLdt); conjugate-transposed use reads them
+// transposed (tile_mul_ct).
+// ---------------------------------------------------------------------------
+template <typename C>
+__device__ __forceinline__ void cp_async_tile(C* dst, const C* __restrict__ src) {
+  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+    const int r = e % kTile, c = e / kTile;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst + r + c * kLdt);
+    if constexpr (sizeof(C) == 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + e));
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + e));
+  }
+  asm volatile("cp.async.commit_group;\n" ::);
+}
+
+// acc[jj] += / -= Tc(:, lane)^H-row times Bm: a = conj(Traw(k, lane))
+template <typename C, int NJ, bool SUB>
+__device__ __forceinline__ void tile_mul_ct(C acc[NJ], const C* Traw, const C* Bm, int ldb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 8
+  for (int k = 0; k < kTile; ++k) {
+    const C a = cconj(Traw[k + lane * kLdt]);
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+      const C bv = Bm[k + (warp + 8 * jj) * ldb];
+      if (SUB)
+        cfms(acc[jj], a, bv);
+      else
+        cfma(acc[jj], a, bv);
+    }
+  }
+}
+
+// Ordered tile requests of one sweep.  next() returns the source of the
+// following request (nullptr after the last); acquire() starts the request
+// after the current one, waits for the current one and returns its slot.
+template <typename C>
+struct TilePipe {
+  C* slot[2];
+  int cur = 0;
+  const C* pending = nullptr;  // source of the request issued into slot[cur ^ 1]
+  __device__ void start(const C* first, const C* second) {
+    cur = 0;
+    cp_async_tile(slot[0], first);
+    pending = second;
+    if (second) cp_async_tile(slot[1], second);
+  }
+  // current tile is ready on return; `after_next` is the request after the pending one
+  __device__ C* acquire() {
+    if (pending)
+      asm volatile("cp.async.wait_group 1;\n" ::);
+    else
+      asm volatile("cp.async.wait_group 0;\n" ::);
+    __syncthreads();
+    return slot[cur];
+  }
+  // the current slot is free again (every thread is past its use): refill it
+  __device__ void release(const C* after_next) {
+    __syncthreads();
+    cur ^= 1;
+    const C* next = after_next;
+    if (pending && next) cp_async_tile(slot[cur ^ 1], next);
+    pending = pending ? next : nullptr;
+  }
+};
+
+// Iterators over the tile requests of each sweep (same order as the sweeps).
+struct SweepIt {
+  int K, q;
+};
+
+// ---------------------------------------------------------------------------
 // trans = 0: forward (P, L) then backward (U), for columns col0 .. col0+CW-1
 // ---------------------------------------------------------------------------
 template <typename C, int CW>
@@ -387,77 +463,110 @@ __device__ void solve_n_body(const FactorGeom& g, const SysDesc& d, int col0, co
   const int64_t n = g.n;
   const int ncols = d.ncols;
   const int tid = threadIdx.x;
+  const int Nb = g.Nb;
 
-  C* Tb = (C*)smem;                    // T x kLdt
-  C* tS = Tb + T * kLdt;               // T x CW
-  C* U0 = tS + T * CW;                 // union area
-  C* Wn = U0;                          // Pmax x CW
-  C* G = U0 + (size_t)Pmax * CW;       // Pmax x CW
-  C* xwin = U0;                        // 2bt slots of T x CW
+  TilePipe<C> pipe;
+  pipe.slot[0] = (C*)smem;                     // T x kLdt
+  pipe.slot[1] = pipe.slot[0] + T * kLdt;      // T x kLdt
+  C* tS = pipe.slot[1] + T * kLdt;             // T x CW
+  C* U0 = tS + T * CW;                         // union area
+  C* Wn = U0;                                  // Pmax x CW
+  C* G = U0 + (size_t)Pmax * CW;               // Pmax x CW
+  C* xwin = U0;                                // 2bt slots of T x CW
 
+  // forward requests: per K, Linv(K) then L(K+q, K), q = 1..min(bt, Nb-1-K)
+  auto fsrc = [&](SweepIt it) -> const C* {
+    if (it.K >= Nb) return nullptr;
+    return it.q == 0 ? f.inv + (int64_t)(2 * it.K) * g.tile_elems
+                     : f.tiles + g.tile_index(it.K + it.q, it.K) * g.tile_elems;
+  };
+  auto fnext = [&](SweepIt it) -> SweepIt {
+    if (it.q < min(bt, Nb - 1 - it.K)) return SweepIt{it.K, it.q + 1};
+    return SweepIt{it.K + 1, 0};
+  };
   // ---------------- forward ----------------
   {
-    const int nbb0 = min(bt, g.Nb - 1);
+    SweepIt it0{0, 0};
+    SweepIt it1 = fnext(it0);
+    SweepIt it2 = fnext(it1);
+    pipe.start(fsrc(it0), fsrc(it1));
+    const int nbb0 = min(bt, Nb - 1);
     for (int q = 0; q <= nbb0; ++q) load_rhs_block<C, NJ>(Wn + q * T, ldw, Y, n, (int64_t)q * T, col0, ncols);
     __syncthreads();
-    for (int K = 0; K < g.Nb; ++K) {
-      const int nbb = min(bt, g.Nb - 1 - K);
+    for (int K = 0; K < Nb; ++K) {
+      const int nbb = min(bt, Nb - 1 - K);
       const int P = (nbb + 1) * T;
       const int16_t* pm = f.perm + (int64_t)K * Pmax;
       for (int e = tid; e < P * CW; e += blockDim.x) {
         const int r = e % P, c = e / P;
         G[r + c * ldw] = Wn[pm[r] + c * ldw];
       }
-      load_tile<C, false>(Tb, f.inv + (int64_t)(2 * K) * g.tile_elems);
-      __syncthreads();
+      C* Tb = pipe.acquire();
       C acc[NJ];
       zero_acc<C, NJ>(acc);
       tile_mul<C, NJ, false>(acc, Tb, G, ldw);
-      __syncthreads();
+      pipe.release(fsrc(it2));
+      it2 = fnext(it2);
       put_acc<C, NJ>(G, ldw, acc);
       store_rows<C, NJ>(X, n, (int64_t)K * T, col0, ncols, acc);
       __syncthreads();
       for (int q = 1; q <= nbb; ++q) {
-        load_tile<C, false>(Tb, f.tiles + g.tile_index(K + q, K) * g.tile_elems);
-        __syncthreads();
+        Tb = pipe.acquire();
         get_acc<C, NJ>(acc, G + q * T, ldw);
         tile_mul<C, NJ, true>(acc, Tb, G, ldw);
         put_acc<C, NJ>(G + q * T, ldw, acc);
-        __syncthreads();
+        pipe.release(fsrc(it2));
+        it2 = fnext(it2);
       }
-      if (K + 1 < g.Nb) {
+      if (K + 1 < Nb) {
         for (int e = tid; e < nbb * T * CW; e += blockDim.x) {
           const int r = e % (nbb * T), c = e / (nbb * T);
           Wn[r + c * ldw] = G[T + r + c * ldw];
         }
-        const int nbn = min(bt, g.Nb - 2 - K);
+        const int nbn = min(bt, Nb - 2 - K);
         if (nbn == nbb)
           load_rhs_block<C, NJ>(Wn + nbb * T, ldw, Y, n, (int64_t)(K + bt + 1) * T, col0, ncols);
         __syncthreads();
       }
     }
   }
+  // backward requests: per K (descending), U(K, K+q), q = 1..min(2bt, Nb-1-K), then Uinv(K)
+  auto bsrc = [&](SweepIt it) -> const C* {
+    if (it.K < 0) return nullptr;
+    return it.q > 0 ? f.tiles + g.tile_index(it.K, it.K + it.q) * g.tile_elems
+                    : f.inv + (int64_t)(2 * it.K + 1) * g.tile_elems;
+  };
+  auto bfirst = [&](int K) -> SweepIt { return SweepIt{K, min(2 * bt, Nb - 1 - K) > 0 ? 1 : 0}; };
+  auto bnext = [&](SweepIt it) -> SweepIt {
+    if (it.q > 0 && it.q < min(2 * bt, Nb - 1 - it.K)) return SweepIt{it.K, it.q + 1};
+    if (it.q > 0) return SweepIt{it.K, 0};
+    return it.K - 1 >= 0 ? bfirst(it.K - 1) : SweepIt{-1, 0};
+  };
   // ---------------- backward ----------------
   {
     const int ns = 2 * bt;
-    for (int K = g.Nb - 1; K >= 0; --K) {
-      const int nbr = min(2 * bt, g.Nb - 1 - K);
+    SweepIt it0 = bfirst(Nb - 1);
+    SweepIt it1 = bnext(it0);
+    SweepIt it2 = bnext(it1);
+    pipe.start(bsrc(it0), bsrc(it1));
+    for (int K = Nb - 1; K >= 0; --K) {
+      const int nbr = min(2 * bt, Nb - 1 - K);
       C acc[NJ];
       load_acc<C, NJ>(acc, X, n, (int64_t)K * T, col0, ncols);
       for (int q = 1; q <= nbr; ++q) {
-        load_tile<C, false>(Tb, f.tiles + g.tile_index(K, K + q) * g.tile_elems);
-        __syncthreads();
+        C* Tb = pipe.acquire();
         tile_mul<C, NJ, true>(acc, Tb, xwin + ((K + q) % ns) * T * CW, T);
-        __syncthreads();
+        pipe.release(bsrc(it2));
+        it2 = bnext(it2);
       }
       put_acc<C, NJ>(tS, T, acc);
-      load_tile<C, false>(Tb, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
-      __syncthreads();
+      C* Tb = pipe.acquire();
       zero_acc<C, NJ>(acc);
       tile_mul<C, NJ, false>(acc, Tb, tS, T);
       put_acc<C, NJ>(xwin + (K % ns) * T * CW, T, acc);
       store_rows<C, NJ>(X, n, (int64_t)K * T, col0, ncols, acc);
-      __syncthreads();
+      pipe.release(bsrc(it2));
+      it2 = bnext(it2);
     }
   }
 }
@@ -478,55 +587,91 @@ __device__ void solve_c_body(const FactorGeom& g, const SysDesc& d, int col0, co
   const int64_t n = g.n;
   const int ncols = d.ncols;
   const int tid = threadIdx.x;
+  const int Nb = g.Nb;
 
-  C* Tb = (C*)smem;
-  C* tS = Tb + T * kLdt;
+  TilePipe<C> pipe;
+  pipe.slot[0] = (C*)smem;
+  pipe.slot[1] = pipe.slot[0] + T * kLdt;
+  C* tS = pipe.slot[1] + T * kLdt;
   C* U0 = tS + T * CW;
   C* wwin = U0;                        // 2bt slots of T x CW
   C* V = U0;                           // Pmax x CW
   C* Vn = U0 + (size_t)Pmax * CW;      // Pmax x CW
 
+  // forward requests: per K, U(K-q, K), q = 1..min(2bt, K), then Uinv(K)
+  auto fsrc = [&](SweepIt it) -> const C* {
+    if (it.K >= Nb) return nullptr;
+    return it.q > 0 ? f.tiles + g.tile_index(it.K - it.q, it.K) * g.tile_elems
+                    : f.inv + (int64_t)(2 * it.K + 1) * g.tile_elems;
+  };
+  auto ffirst = [&](int K) -> SweepIt { return SweepIt{K, min(2 * bt, K) > 0 ? 1 : 0}; };
+  auto fnext = [&](SweepIt it) -> SweepIt {
+    if (it.q > 0 && it.q < min(2 * bt, it.K)) return SweepIt{it.K, it.q + 1};
+    if (it.q > 0) return SweepIt{it.K, 0};
+    return ffirst(it.K + 1);
+  };
   // ---------------- forward: U^H w = y ----------------
   {
     const int ns = 2 * bt;
-    for (int K = 0; K < g.Nb; ++K) {
+    SweepIt it0 = ffirst(0);
+    SweepIt it1 = fnext(it0);
+    SweepIt it2 = fnext(it1);
+    pipe.start(fsrc(it0), fsrc(it1));
+    for (int K = 0; K < Nb; ++K) {
       C acc[NJ];
       load_acc<C, NJ>(acc, Y, n, (int64_t)K * T, col0, ncols);
       const int nq = min(2 * bt, K);
       for (int q = 1; q <= nq; ++q) {
-        load_tile<C, true>(Tb, f.tiles + g.tile_index(K - q, K) * g.tile_elems);
-        __syncthreads();
-        tile_mul<C, NJ, true>(acc, Tb, wwin + ((K - q) % ns) * T * CW, T);
-        __syncthreads();
+        C* Tb = pipe.acquire();
+        tile_mul_ct<C, NJ, true>(acc, Tb, wwin + ((K - q) % ns) * T * CW, T);
+        pipe.release(fsrc(it2));
+        it2 = fnext(it2);
       }
       put_acc<C, NJ>(tS, T, acc);
-      load_tile<C, true>(Tb, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
-      __syncthreads();
+      C* Tb = pipe.acquire();
       zero_acc<C, NJ>(acc);
-      tile_mul<C, NJ, false>(acc, Tb, tS, T);
+      tile_mul_ct<C, NJ, false>(acc, Tb, tS, T);
       put_acc<C, NJ>(wwin + (K % ns) * T * CW, T, acc);
       store_rows<C, NJ>(X, n, (int64_t)K * T, col0, ncols, acc);
-      __syncthreads();
+      pipe.release(fsrc(it2));
+      it2 = fnext(it2);
     }
   }
+  // backward requests: per K (descending), L(K+q, K), q = 1..min(bt, Nb-1-K), then Linv(K)
+  auto bsrc = [&](SweepIt it) -> const C* {
+    if (it.K < 0) return nullptr;
+    return it.q > 0 ? f.tiles + g.tile_index(it.K + it.q, it.K) * g.tile_elems
+                    : f.inv + (int64_t)(2 * it.K) * g.tile_elems;
+  };
+  auto bfirst = [&](int K) -> SweepIt { return SweepIt{K, min(bt, Nb - 1 - K) > 0 ? 1 : 0}; };
+  auto bnext = [&](SweepIt it) -> SweepIt {
+    if (it.q > 0 && it.q < min(bt, Nb - 1 - it.K)) return SweepIt{it.K, it.q + 1};
+    if (it.q > 0) return SweepIt{it.K, 0};
+    return it.K - 1 >= 0 ? bfirst(it.K - 1) : SweepIt{-1, 0};
+  };
   // ---------------- backward: x = P_0^T E_0^H ... P_{Nb-1}^T E_{Nb-1}^H w ----------------
   {
-    for (int K = g.Nb - 1; K >= 0; --K) {
-      const int nbb = min(bt, g.Nb - 1 - K);
+    SweepIt it0 = bfirst(Nb - 1);
+    SweepIt it1 = bnext(it0);
+    SweepIt it2 = bnext(it1);
+    pipe.start(bsrc(it0), bsrc(it1));
+    for (int K = Nb - 1; K >= 0; --K) {
+      const int nbb = min(bt, Nb - 1 - K);
       const int P = (nbb + 1) * T;
       C acc[NJ];
       load_acc<C, NJ>(acc, X, n, (int64_t)K * T, col0, ncols);
       for (int q = 1; q <= nbb; ++q) {
-        load_tile<C, true>(Tb, f.tiles + g.tile_index(K + q, K) * g.tile_elems);
-        __syncthreads();
-        tile_mul<C, NJ, true>(acc, Tb, V + q * T, ldw);
-        __syncthreads();
+        C* Tb = pipe.acquire();
+        tile_mul_ct<C, NJ, true>(acc, Tb, V + q * T, ldw);
+        pipe.release(bsrc(it2));
+        it2 = bnext(it2);
       }
       put_acc<C, NJ>(tS, T, acc);
-      load_tile<C, true>(Tb, f.inv + (int64_t)(2 * K) * g.tile_elems);
-      __syncthreads();
+      C* Tb = pipe.acquire();
       zero_acc<C, NJ>(acc);
-      tile_mul<C, NJ, false>(acc, Tb, tS, T);
+      tile_mul_ct<C, NJ, false>(acc, Tb, tS, T);
+      pipe.release(bsrc(it2));
+      it2 = bnext(it2);
       put_acc<C, NJ>(V, ldw, acc);
       __syncthreads();
       const int16_t* pm = f.perm + (int64_t)K * Pmax;
@@ -541,7 +686,7 @@ __device__ void solve_c_body(const FactorGeom& g, const SysDesc& d, int col0, co
         for (int jj = 0; jj < NJ; ++jj) acc[jj] = Vn[bt * T + (tid & 31) + ((tid >> 5) + 8 * jj) * ldw];
         store_rows<C, NJ>(X, n, (int64_t)(K + bt) * T, col0, ncols, acc);
       }
-      const int nbn = min(bt, g.Nb - K);  // window blocks kept for step K-1 (beyond its top block)
+      const int nbn = min(bt, Nb - K);  // window blocks kept for step K-1 (beyond its top block)
       for (int e = tid; e < nbn * T * CW; e += blockDim.x) {
         const int r = e % (nbn * T), c = e / (nbn * T);
         V[T + r + c * ldw] = Vn[r + c * ldw];
@@ -549,7 +694,7 @@ __device__ void solve_c_body(const FactorGeom& g, const SysDesc& d, int col0, co
       __syncthreads();
     }
     // remaining window blocks 0 .. min(bt, Nb)-1 sit in V[T : ...]
-    const int nrem = min(bt, g.Nb);
+    const int nrem = min(bt, Nb);
     for (int q = 0; q < nrem; ++q) {
       C acc[NJ];
 #pragma unroll
@@ -591,7 +736,7 @@ size_t solve_smem_bytes(const FactorGeom& g, int chunk, size_t es, int trans) {
   size_t uni = 2 * Pmax * (size_t)chunk;
   size_t win = (size_t)2 * g.bt * T * chunk;
   if (win > uni) uni = win;
-  return es * ((size_t)T * kLdt + (size_t)T * chunk + uni);
+  return es * ((size_t)2 * T * kLdt + (size_t)T * chunk + uni);  // two tile slots
 }
 
 static size_t factor_smem_bytes(const FactorGeom& g, size_t es) {
