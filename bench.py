@@ -60,7 +60,7 @@ PEAK_FF_TFLOPS = 152 * 128 * 2.07e9 * 8 / 52 / 1e12
 GROUP_BOUND = {"factor": ("alu", PEAK_FP32_TFLOPS, "fp32"), "solve": ("alu", PEAK_FP32_TFLOPS, "fp32"),
                "accum": ("hbm", None, None), "gemm": ("alu", PEAK_FF_TFLOPS, "float-float (FP32 pipe)"),
                "small": ("alu", PEAK_FP64_TFLOPS, "fp64"), "bandmm": ("alu", PEAK_FF_TFLOPS, "float-float (FP32 pipe)"),
-               "inertia": ("alu", PEAK_FP64_TFLOPS, "fp64")}
+               "inertia": ("alu", PEAK_FP64_TFLOPS, "fp64"), "eig": ("alu", PEAK_FP32_TFLOPS, "fp32")}
 
 
 def boundary_indices():
@@ -385,7 +385,7 @@ def traffic_for(group):
 
 WORKLOAD_KEY = "c2"
 GROUP_SOURCES = {"solve": "band_lu.cu", "factor": "band_lu.cu", "gemm": "dense.cu", "small": "dense.cu",
-                 "bandmm": "dense.cu", "accum": "feast.cu", "inertia": "inertia.cu"}
+                 "bandmm": "dense.cu", "accum": "feast.cu", "inertia": "inertia.cu", "eig": "dense.cu"}
 
 
 def source_hash(group):

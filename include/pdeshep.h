@@ -102,10 +102,11 @@ typedef struct {
 #define PDESHEP_KG_FACTOR 1      /* shifted band LU (tile init + factorization) */
 #define PDESHEP_KG_SOLVE 2       /* multi-RHS band solves (forward + backward sweeps) */
 #define PDESHEP_KG_ACCUM 3       /* right-hand-side preparation and weighted accumulation of Q */
-#define PDESHEP_KG_GEMM 4        /* FP64 tall products (Gram, projection, basis updates) */
-#define PDESHEP_KG_SMALL 5       /* FP64 Cholesky, triangular inverse, Jacobi */
-#define PDESHEP_KG_BANDMM 6      /* FP64 band times block (B Q, B X) and residual norms */
-#define PDESHEP_KG_COUNT 7
+#define PDESHEP_KG_GEMM 4        /* tall products (Gram, projection, basis update): FP64 or float-float */
+#define PDESHEP_KG_SMALL 5       /* FP64 Cholesky and triangular inverse, small m0 x m0 products */
+#define PDESHEP_KG_BANDMM 6      /* band times block (B Q, B X; FP64 or float-float) and residual norms */
+#define PDESHEP_KG_EIG 7         /* small eigensolver: FP32 Jacobi, FP64-class refinement, clusters */
+#define PDESHEP_KG_COUNT 8
 
 typedef struct {
   int32_t iterations;      /* FEAST iterations of the slowest slice */

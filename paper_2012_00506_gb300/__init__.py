@@ -65,7 +65,7 @@ class Opts(C.Structure):
     ]
 
 
-KERNEL_GROUPS = ["inertia", "factor", "solve", "accum", "gemm", "small", "bandmm"]
+KERNEL_GROUPS = ["inertia", "factor", "solve", "accum", "gemm", "small", "bandmm", "eig"]
 
 
 class Stats(C.Structure):
@@ -74,7 +74,7 @@ class Stats(C.Structure):
         ("rhs_sweeps", C.c_int64), ("ms_inertia", C.c_double), ("ms_factor", C.c_double),
         ("ms_solve", C.c_double), ("ms_rr", C.c_double), ("ms_total", C.c_double),
         ("max_residual", C.c_double), ("min_rel_error_est", C.c_double),
-        ("kg_ms", C.c_double * 7), ("kg_launches", C.c_int64 * 7), ("kg_flops", C.c_double * 7),
+        ("kg_ms", C.c_double * 8), ("kg_launches", C.c_int64 * 8), ("kg_flops", C.c_double * 8),
         ("rhs_columns", C.c_int64), ("cluster_ctas", C.c_int32), ("jacobi_sweeps64", C.c_int32),
         ("jacobi_sweeps32", C.c_int32), ("rr_calls", C.c_int32),
         ("eig_refine_steps", C.c_int32), ("eig_clusters", C.c_int32), ("eig_max_cluster", C.c_int32),

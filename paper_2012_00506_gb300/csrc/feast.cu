@@ -785,7 +785,7 @@ struct FeastRun : Feast<S, C> {
     PD_TRY(gemm(0, (S*)p.Q, (S*)p.BQ, Aq));         // Q^H B Q
     PD_TRY(small_mm(false, Aq, I, T, 0, 1));         // (Q^H B Q) R^{-1}
     PD_TRY(small_mm(true, I, T, G, 1, 0));           // A~ = R^{-H} (Q^H B Q) R^{-1}
-    PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
+    PD_TRY(this->kt.begin(PDESHEP_KG_EIG));
     symmetrize_kernel<S><<<dim3(grid1((int64_t)mm * mm), na), 256, 0, st>>>(p.d_small, G);
     PD_CK_LAUNCH();
     offratio_kernel<S><<<na, 256, 0, st>>>(p.d_small, G, p.offratio);
