@@ -556,27 +556,23 @@ struct Rot {
   int p, q;
 };
 
+// Rotation of the pair (p, q) of one round.  Indices >= m (the dummy player of
+// an odd m) are stored as -1; a pair without rotation keeps c = 1, s = 0, u = 1.
 template <typename S>
 __device__ __forceinline__ void make_rot(const S* A, int m, int p, int q, Rot<S>& r) {
   using R = typename real_t<S>::type;
-  r.p = p;
-  r.q = q;
+  r.p = p < m ? p : -1;
+  r.q = q < m ? q : -1;
   r.c = R(1);
   r.s = R(0);
   r.u = sc<S>::from_re(R(1));
-  if (p >= m || q >= m) {
-    r.p = -1;
-    return;
-  }
+  if (p >= m || q >= m) return;
   const S apq = A[p + (int64_t)q * m];
   // |A(p,q)| without squaring: in FP32 the square of an element below ~1e-19
   // is subnormal, and a modulus taken from it makes the rotation non-unitary
   const R g = sc<S>::absv(apq);
   const R tiny = sizeof(R) == 8 ? R(1e-290) : R(1e-30);
-  if (!(g > tiny)) {
-    r.p = -1;
-    return;
-  }
+  if (!(g > tiny)) return;
   r.u = sc<S>::scale(apq, R(1) / g);
   const R app = sc<S>::re(A[p + (int64_t)p * m]), aqq = sc<S>::re(A[q + (int64_t)q * m]);
   const R th = (aqq - app) / (R(2) * g);
@@ -586,8 +582,9 @@ __device__ __forceinline__ void make_rot(const S* A, int m, int p, int q, Rot<S>
 }
 
 template <typename S>
-__global__ void __launch_bounds__(512) jacobi_kernel(const SmallDesc* desc, S* Aall, S* Vall, S* Vout, double* lamall,
-                              double tol, int max_sweeps, int* sweeps_out, double* scratch) {
+__global__ void __launch_bounds__(512) jacobi_kernel(const SmallDesc* desc, S* Aall, S* Aalt, S* Vall, S* Vout,
+                                                     double* lamall, double tol, int max_sweeps, int* sweeps_out,
+                                                     double* scratch) {
   using R = typename real_t<S>::type;
   extern __shared__ __align__(16) char smem[];
   Rot<S>* rot = (Rot<S>*)smem;
@@ -595,7 +592,11 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const SmallDesc* desc, S* A
   const int t = cl_slice();
   const SmallDesc d = desc[t];
   const int m = d.m;
+  // A is updated out of place, alternating between the two buffers: a round
+  // reads its pivots and blocks from one and writes the other, so no CTA can see
+  // a half-updated round and one cluster barrier per round suffices
   S* A = Aall + d.off;
+  S* Anext = Aalt + d.off;
   S* V = Vall + d.off;
   const int cr = cl_rank(), G = cl_size();
   const int gid = cr * blockDim.x + threadIdx.x, gsz = G * blockDim.x;
@@ -649,6 +650,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const SmallDesc* desc, S* A
     }
     if (sweeps >= max_sweeps) break;
     for (int r = 0; r < M - 1; ++r) {
+      // every CTA derives the round's rotations from the same A
       for (int i = threadIdx.x; i < np; i += blockDim.x) {
         int p, q;
         if (i == 0) {
@@ -660,81 +662,65 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const SmallDesc* desc, S* A
         }
         make_rot<S>(A, m, p, q, rot[i]);
       }
-      // every CTA must have read the pivots of this round before any column changes
-      cl_sync();
-      // columns of A and V: A <- A J, V <- V J (four independent updates in flight per thread)
-      constexpr int U = 4;
-      const int64_t tc = (int64_t)np * m;
-      for (int64_t e0 = gid; e0 < tc; e0 += (int64_t)gsz * U) {
-        S akp[U], akq[U], vkp[U], vkq[U];
-        int ip[U], iq[U], kk[U], ri[U];
+      __syncthreads();
+      // A <- J^H A J in one pass: the 2 x 2 block of A in rows (p_i, q_i) and columns
+      // (p_k, q_k) needs only the rotations of pairs i and k, so the blocks are
+      // independent; V <- V J likewise per (row, pair).  One cluster barrier per round.
+      const int64_t nb = (int64_t)np * np;
+      for (int64_t e = gid; e < nb; e += gsz) {
+        const int i = (int)(e % np), k = (int)(e / np);
+        const Rot<S> ri = rot[i], rk = rot[k];
+        const int ra[2] = {ri.p, ri.q}, cb[2] = {rk.p, rk.q};
+        S x[2][2];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int64_t e = e0 + (int64_t)u * gsz;
-          ri[u] = -1;
-          if (e < tc) {
-            const int i = (int)(e / m);
-            if (rot[i].p >= 0) {
-              ri[u] = i;
-              ip[u] = rot[i].p;
-              iq[u] = rot[i].q;
-              kk[u] = (int)(e % m);
-              akp[u] = A[kk[u] + (int64_t)ip[u] * m];
-              akq[u] = A[kk[u] + (int64_t)iq[u] * m];
-              vkp[u] = V[kk[u] + (int64_t)ip[u] * m];
-              vkq[u] = V[kk[u] + (int64_t)iq[u] * m];
-            }
-          }
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 2; ++b2)
+            x[a][b2] = (ra[a] >= 0 && cb[b2] >= 0) ? A[ra[a] + (int64_t)cb[b2] * m] : sc<S>::zero();
+        // columns: [x_p, x_q] <- [x_p u c - x_q s, x_p u s + x_q c] (pair k)
+        const S uck = sc<S>::scale(rk.u, rk.c), usk = sc<S>::scale(rk.u, rk.s);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const S xp = x[a][0], xq = x[a][1];
+          x[a][0] = sc<S>::sub(sc<S>::mul(xp, uck), sc<S>::scale(xq, rk.s));
+          x[a][1] = sc<S>::add(sc<S>::mul(xp, usk), sc<S>::scale(xq, rk.c));
+        }
+        // rows: [x_p; x_q] <- [conj(u c) x_p - s x_q; conj(u s) x_p + c x_q] (pair i)
+        const S ucc = sc<S>::conj(sc<S>::scale(ri.u, ri.c)), usc = sc<S>::conj(sc<S>::scale(ri.u, ri.s));
+#pragma unroll
+        for (int b2 = 0; b2 < 2; ++b2) {
+          const S xp = x[0][b2], xq = x[1][b2];
+          x[0][b2] = sc<S>::sub(sc<S>::mul(ucc, xp), sc<S>::scale(xq, ri.s));
+          x[1][b2] = sc<S>::add(sc<S>::mul(usc, xp), sc<S>::scale(xq, ri.c));
+        }
+        if (i == k && ri.p >= 0 && ri.q >= 0) {  // the rotated pivot block: exact zeros, real diagonal
+          x[0][1] = sc<S>::zero();
+          x[1][0] = sc<S>::zero();
+          x[0][0] = sc<S>::from_re(sc<S>::re(x[0][0]));
+          x[1][1] = sc<S>::from_re(sc<S>::re(x[1][1]));
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (ri[u] < 0) continue;
-          const Rot<S> ro = rot[ri[u]];
-          const S uc = sc<S>::scale(ro.u, ro.c), us = sc<S>::scale(ro.u, ro.s);
-          A[kk[u] + (int64_t)ip[u] * m] = sc<S>::sub(sc<S>::mul(akp[u], uc), sc<S>::scale(akq[u], ro.s));
-          A[kk[u] + (int64_t)iq[u] * m] = sc<S>::add(sc<S>::mul(akp[u], us), sc<S>::scale(akq[u], ro.c));
-          V[kk[u] + (int64_t)ip[u] * m] = sc<S>::sub(sc<S>::mul(vkp[u], uc), sc<S>::scale(vkq[u], ro.s));
-          V[kk[u] + (int64_t)iq[u] * m] = sc<S>::add(sc<S>::mul(vkp[u], us), sc<S>::scale(vkq[u], ro.c));
-        }
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 2; ++b2)
+            if (ra[a] >= 0 && cb[b2] >= 0) Anext[ra[a] + (int64_t)cb[b2] * m] = x[a][b2];
       }
-      cl_sync();
-      // rows of A: A <- J^H A
-      for (int64_t e0 = gid; e0 < tc; e0 += (int64_t)gsz * U) {
-        S apk[U], aqk[U];
-        int ri[U], kk[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int64_t e = e0 + (int64_t)u * gsz;
-          ri[u] = -1;
-          if (e < tc) {
-            const int i = (int)(e % np);
-            if (rot[i].p >= 0) {
-              ri[u] = i;
-              kk[u] = (int)(e / np);
-              apk[u] = A[rot[i].p + (int64_t)kk[u] * m];
-              aqk[u] = A[rot[i].q + (int64_t)kk[u] * m];
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (ri[u] < 0) continue;
-          const Rot<S> ro = rot[ri[u]];
-          const int k = kk[u];
-          const S ucc = sc<S>::conj(sc<S>::scale(ro.u, ro.c)), usc = sc<S>::conj(sc<S>::scale(ro.u, ro.s));
-          S np_ = sc<S>::sub(sc<S>::mul(ucc, apk[u]), sc<S>::scale(aqk[u], ro.s));
-          S nq_ = sc<S>::add(sc<S>::mul(usc, apk[u]), sc<S>::scale(aqk[u], ro.c));
-          if (k == ro.q) np_ = sc<S>::zero();
-          if (k == ro.p) {
-            nq_ = sc<S>::zero();
-            np_ = sc<S>::from_re(sc<S>::re(np_));
-          }
-          if (k == ro.q) nq_ = sc<S>::from_re(sc<S>::re(nq_));
-          A[ro.p + (int64_t)k * m] = np_;
-          A[ro.q + (int64_t)k * m] = nq_;
-        }
+      const int64_t nv = (int64_t)np * m;
+      for (int64_t e = gid; e < nv; e += gsz) {
+        const int k = (int)(e / m), row = (int)(e % m);
+        const Rot<S> rk = rot[k];
+        if (rk.p < 0 || rk.q < 0) continue;
+        const S vp = V[row + (int64_t)rk.p * m], vq = V[row + (int64_t)rk.q * m];
+        const S uc = sc<S>::scale(rk.u, rk.c), us = sc<S>::scale(rk.u, rk.s);
+        V[row + (int64_t)rk.p * m] = sc<S>::sub(sc<S>::mul(vp, uc), sc<S>::scale(vq, rk.s));
+        V[row + (int64_t)rk.q * m] = sc<S>::add(sc<S>::mul(vp, us), sc<S>::scale(vq, rk.c));
       }
+      // (every row and column index is in exactly one pair, so the blocks cover all of A;
+      // the partner of the dummy player of an odd m is rotated by the identity)
       cl_sync();
+      S* tmp = A;
+      A = Anext;
+      Anext = tmp;
     }
   }
   // sort ascending by eigenvalue (rank sort, ties by index), phase-normalise
@@ -769,12 +755,12 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const SmallDesc* desc, S* A
 }
 
 template <typename S>
-int launch_jacobi(int nblk, const SmallDesc* d_desc, int max_m, S* A, S* Vwork, S* Vout, double* lam,
+int launch_jacobi(int nblk, const SmallDesc* d_desc, int max_m, S* A, S* Aalt, S* Vwork, S* Vout, double* lam,
                   double tol, int max_sweeps, int* sweeps_out, double* scratch, cudaStream_t st) {
   if (nblk <= 0) return 0;
   const size_t smem = sizeof(Rot<S>) * (size_t)((max_m + 2) / 2);
   if (smem > 48 * 1024) PD_CK(cudaFuncSetAttribute(jacobi_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  return launch_cluster_t(jacobi_kernel<S>, nblk, smem, 512, st, d_desc, A, Vwork, Vout, lam, tol, max_sweeps,
+  return launch_cluster_t(jacobi_kernel<S>, nblk, smem, 512, st, d_desc, A, Aalt, Vwork, Vout, lam, tol, max_sweeps,
                           sweeps_out, scratch);
 }
 
@@ -1010,6 +996,7 @@ EighScratch<S> plan_eigh_scratch(Arena& a, int64_t msq, int64_t mtot, int nblk) 
   using L = typename lowp<S>::type;
   EighScratch<S> w;
   w.A32 = a.take<L>(msq);
+  w.A32b = a.take<L>(msq);
   w.V32w = a.take<L>(msq);
   w.V32 = a.take<L>(msq);
   w.Vd = a.take<S>(msq);
@@ -1248,7 +1235,8 @@ static int resolve_clusters(const std::vector<ClusterRef>& cl, const S* A, doubl
   std::vector<SmallDesc> cd(nq);
   for (int q = 0; q < nq; ++q) cd[q] = SmallDesc{col(cl[q]), cl[q].voff + cl[q].i0, cl[q].c, 0};
   PD_CK(cudaMemcpyAsync(w.cdesc, cd.data(), sizeof(SmallDesc) * nq, cudaMemcpyHostToDevice, st));
-  PD_TRY(launch_jacobi<S>(nq, w.cdesc, mx_c, w.A64, w.Vw, w.W64, w.lam32, 1e-14, 60, w.csweeps, w.cjscratch, st));
+  PD_TRY(launch_jacobi<S>(nq, w.cdesc, mx_c, w.A64, w.T, w.Vw, w.W64, w.lam32, 1e-14, 60, w.csweeps, w.cjscratch,
+                          st));
   // Vc Wc -> Vd, then back into W; eigenvalues back into lam
   for (int q = 0; q < nq; ++q) {
     const ClusterRef& c = cl[q];
@@ -1299,7 +1287,8 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
     const dim3 g((unsigned)gcast.x, (unsigned)ns);
     small_cast_kernel<S, L><<<g, 256, 0, st>>>(w.dsub, A, w.A32);
     PD_CK_LAUNCH();
-    PD_TRY(launch_jacobi<L>(ns, w.dsub, max_m, w.A32, w.V32w, w.V32, w.lam32, 1e-6, 30, w.sweeps, w.jscratch, st));
+    PD_TRY(launch_jacobi<L>(ns, w.dsub, max_m, w.A32, w.A32b, w.V32w, w.V32, w.lam32, 1e-6, 30, w.sweeps,
+                            w.jscratch, st));
     if (fp32_sweeps_out)
       PD_CK(cudaMemcpyAsync(fp32_sweeps_out, w.sweeps, sizeof(int) * ns, cudaMemcpyDeviceToDevice, st));
     small_cast_kernel<L, S><<<g, 256, 0, st>>>(w.dsub, w.V32, w.Vd);
@@ -1471,7 +1460,7 @@ int eigh_mixed(int nblk, const SmallDesc* d_desc, const SmallDesc* h_desc, int m
       S* abc[3] = {w.Vd, w.T, w.A64};  // H = V^H A V
       PD_TRY(small_gemm<S>(true, fb, max_m, abc, 1, 0, w.items, st));
     }
-    PD_TRY(launch_jacobi<S>(nfb, w.dsub, max_m, w.A64, w.Vw, w.W64, lam, 1e-13, 60, w.sweeps, w.jscratch, st));
+    PD_TRY(launch_jacobi<S>(nfb, w.dsub, max_m, w.A64, w.T, w.Vw, w.W64, lam, 1e-13, 60, w.sweeps, w.jscratch, st));
     {
       S* abc[3] = {w.Vd, w.W64, W};
       PD_TRY(small_gemm<S>(false, fb, max_m, abc, 0, 0, w.items, st));
@@ -1516,13 +1505,13 @@ template int launch_cholesky<double>(int, const SmallDesc*, double*, int*, cudaS
 template int launch_cholesky<double2>(int, const SmallDesc*, double2*, int*, cudaStream_t, double*, double*);
 template int launch_triinv<double>(int, const SmallDesc*, const double*, double*, cudaStream_t);
 template int launch_triinv<double2>(int, const SmallDesc*, const double2*, double2*, cudaStream_t);
-template int launch_jacobi<double>(int, const SmallDesc*, int, double*, double*, double*, double*, double,
-                                   int, int*, double*, cudaStream_t);
-template int launch_jacobi<double2>(int, const SmallDesc*, int, double2*, double2*, double2*, double*,
+template int launch_jacobi<double>(int, const SmallDesc*, int, double*, double*, double*, double*, double*,
+                                   double, int, int*, double*, cudaStream_t);
+template int launch_jacobi<double2>(int, const SmallDesc*, int, double2*, double2*, double2*, double2*, double*,
                                     double, int, int*, double*, cudaStream_t);
-template int launch_jacobi<float>(int, const SmallDesc*, int, float*, float*, float*, double*, double, int,
+template int launch_jacobi<float>(int, const SmallDesc*, int, float*, float*, float*, float*, double*, double, int,
                                   int*, double*, cudaStream_t);
-template int launch_jacobi<float2>(int, const SmallDesc*, int, float2*, float2*, float2*, double*, double,
+template int launch_jacobi<float2>(int, const SmallDesc*, int, float2*, float2*, float2*, float2*, double*, double,
                                    int, int*, double*, cudaStream_t);
 template int launch_band_split<double>(int64_t, int, const void*, int64_t, void*, cudaStream_t);
 template int launch_band_split<double2>(int64_t, int, const void*, int64_t, void*, cudaStream_t);

@@ -55,11 +55,11 @@ int cluster_ctas_used();
 template <typename S>
 int launch_triinv(int nblk, const SmallDesc* d_desc, const S* R, S* Rinv, cudaStream_t st);
 
-// Hermitian Jacobi: A (overwritten), eigenvalues ascending into lam (offset
-// voff), eigenvectors into Vout (same layout as A).  Vwork: scratch like A.
-// sweeps_out[t]: sweeps used or -1 if max_sweeps hit.
+// Hermitian Jacobi: A and Aalt (scratch like A) are overwritten, eigenvalues
+// ascending into lam (offset voff), eigenvectors into Vout (same layout as A).
+// Vwork: scratch like A.  sweeps_out[t]: sweeps used or -1 if max_sweeps hit.
 template <typename S>
-int launch_jacobi(int nblk, const SmallDesc* d_desc, int max_m, S* A, S* Vwork, S* Vout, double* lam,
+int launch_jacobi(int nblk, const SmallDesc* d_desc, int max_m, S* A, S* Aalt, S* Vwork, S* Vout, double* lam,
                   double tol, int max_sweeps, int* sweeps_out, double* scratch, cudaStream_t st);
 
 // Mixed-precision small Hermitian eigensolver: FP32 Jacobi gives V32 (blocks
@@ -70,6 +70,7 @@ int launch_jacobi(int nblk, const SmallDesc* d_desc, int max_m, S* A, S* Vwork, 
 template <typename S>
 struct EighScratch {
   typename lowp<S>::type* A32;
+  typename lowp<S>::type* A32b;
   typename lowp<S>::type* V32w;
   typename lowp<S>::type* V32;
   S* Vd;
