@@ -11,6 +11,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "dense.cuh"
@@ -348,20 +349,70 @@ struct ClusterShape {
 };
 static const ClusterShape kShapes[] = {{16, 120 * 1024}, {8, 120 * 1024}, {8, 0}};
 static int g_shape = 0;
+static int g_last_ctas = 0;  // cluster size of the last cluster launch
 
-int cluster_ctas_used() { return kShapes[g_shape].ctas; }
+int cluster_ctas_used() { return g_last_ctas ? g_last_ctas : kShapes[g_shape].ctas; }
 
 __device__ __forceinline__ int cl_rank() { return (int)cg::this_cluster().block_rank(); }
 __device__ __forceinline__ int cl_size() { return (int)cg::this_cluster().num_blocks(); }
 __device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
 __device__ __forceinline__ int cl_slice() { return blockIdx.x / cl_size(); }
 
+// Per launch, with `resident`, the widest shape whose nblk clusters are all
+// resident at once (a 16-CTA cluster needs 16 SMs of one GPC, so only a few
+// fit); otherwise, or if none fits, the widest usable shape.  Occupancy answers
+// are cached per kernel and shape.
+static std::map<std::pair<const void*, int>, int> g_cluster_fit;
+
 template <typename K, typename... Args>
-static int launch_cluster_t(K kernel, int nblk, size_t smem, int threads, cudaStream_t st, Args... args) {
+static int launch_cluster_t(bool resident, K kernel, int nblk, size_t smem, int threads, cudaStream_t st,
+                            Args... args) {
+  const int nshapes = (int)(sizeof(kShapes) / sizeof(kShapes[0]));
   for (;;) {
-    const ClusterShape sh = kShapes[g_shape];
+    int pick = -1;
+    for (int sidx = g_shape; sidx < nshapes; ++sidx) {
+      const ClusterShape sh = kShapes[sidx];
+      const size_t dyn = std::max(smem, sh.spread_smem);
+      const auto key = std::make_pair((const void*)kernel, sidx * 4096 + (int)(dyn >> 10));
+      auto it = g_cluster_fit.find(key);
+      int nc = 0;
+      if (it != g_cluster_fit.end()) {
+        nc = it->second;
+      } else {
+        cudaError_t e = cudaSuccess;
+        if (sh.ctas > 8) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess && dyn > 48 * 1024)
+          e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nblk * sh.ctas));
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = dyn;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = sh.ctas;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&nc, kernel, &cfg);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          nc = 0;
+        }
+        g_cluster_fit[key] = nc;
+      }
+      if (nc < 1) continue;
+      if (pick < 0) pick = sidx;          // widest usable
+      if (!resident) break;
+      if (nc >= nblk) {                   // widest with every cluster resident
+        pick = sidx;
+        break;
+      }
+    }
+    if (pick < 0) pick = nshapes - 1;
+    const ClusterShape sh = kShapes[pick];
     const size_t dyn = std::max(smem, sh.spread_smem);
-    const bool last = g_shape == (int)(sizeof(kShapes) / sizeof(kShapes[0])) - 1;
     cudaError_t e = cudaSuccess;
     if (sh.ctas > 8) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess && dyn > 48 * 1024)
@@ -378,31 +429,32 @@ static int launch_cluster_t(K kernel, int nblk, size_t smem, int threads, cudaSt
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (e == cudaSuccess && !last) {
-      int nclusters = 0;
-      e = cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg);
-      if (e == cudaSuccess && nclusters < 1) e = cudaErrorInvalidConfiguration;
-    }
     if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, kernel, args...);
-    if (e != cudaSuccess && !last) {
+    if (e != cudaSuccess && pick < nshapes - 1) {
       cudaGetLastError();
-      ++g_shape;
+      g_shape = pick + 1;  // this shape is not usable here
       continue;
     }
     PD_CK(e);
     count_launch();
+    g_last_ctas = sh.ctas;
     return 0;
   }
 }
 
 template <typename K, typename... Args>
 static int launch_cluster(K kernel, int nblk, size_t smem, cudaStream_t st, Args... args) {
-  return launch_cluster_t(kernel, nblk, smem, kSmallThreads, st, args...);
+  return launch_cluster_t(false, kernel, nblk, smem, kSmallThreads, st, args...);
 }
 
 // ---------------------------------------------------------------------------
 // Cholesky G = R^H R, upper, in place; one cluster per block
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double shfl_s(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double2 shfl_s(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
 template <typename S>
 __global__ void __launch_bounds__(1024) cholesky_kernel(const SmallDesc* desc, S* Gall, int* info, double* diag0,
                                                         double* minratio) {
@@ -415,29 +467,94 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const SmallDesc* desc, S
     for (int i = gid; i < m; i += gsz) diag0[d.voff + i] = sc<S>::re(G[i + (int64_t)i * m]);
     cl_sync();
   }
+  // Blocked right-looking factorization in panels of CB columns, three cluster
+  // barriers per panel: (1) CTA 0 factors the diagonal block in shared memory,
+  // (2) every CTA solves R_JJ^H R_JK = G_JK for its columns right of the panel,
+  // (3) the trailing upper triangle gets G_KK -= R_JK^H R_JK.
+  constexpr int CB = 32;
+  __shared__ S Rjj[CB][CB + 1];  // R_JJ (row, col)
+  __shared__ int sh_bad;
   int bad = 0;
-  for (int j = 0; j < m; ++j) {
-    const double dj = sc<S>::re(G[j + (int64_t)j * m]);
-    if (!(dj > 0.0) || !isfinite(dj)) {
-      bad = j + 1;
-      break;
+  for (int j0 = 0; j0 < m && !bad; j0 += CB) {
+    const int nb = min(CB, m - j0);
+    if (cl_rank() == 0) {
+      for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int r = e % nb, c = e / nb;
+        Rjj[r][c] = G[(j0 + r) + (int64_t)(j0 + c) * m];
+      }
+      if (threadIdx.x == 0) sh_bad = 0;
+      __syncthreads();
+      if (threadIdx.x < 32) {  // one warp factors the diagonal block; lane c owns column c
+        const int lane = threadIdx.x;
+        for (int j = 0; j < nb; ++j) {
+          const double dj = sc<S>::re(Rjj[j][j]);
+          if (!((dj > 0.0) && isfinite(dj))) {
+            if (lane == 0) sh_bad = j0 + j + 1;
+            break;
+          }
+          const double r = sqrt(dj);
+          __syncwarp();
+          if (lane > j && lane < nb) Rjj[j][lane] = sc<S>::scale(Rjj[j][lane], 1.0 / r);
+          __syncwarp();
+          if (lane > j && lane < nb)
+            for (int i = j + 1; i <= lane; ++i)
+              Rjj[i][lane] = sc<S>::sub(Rjj[i][lane], sc<S>::mul(sc<S>::conj(Rjj[j][i]), Rjj[j][lane]));
+          __syncwarp();
+          if (lane == j) Rjj[j][j] = sc<S>::from_re(r);
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        const int r = e % nb, c = e / nb;
+        if (r <= c) G[(j0 + r) + (int64_t)(j0 + c) * m] = Rjj[r][c];
+      }
+      if (threadIdx.x == 0) info[t] = sh_bad;  // provisional; rewritten below
     }
-    const double r = sqrt(dj);
-    const double ri = 1.0 / r;
-    for (int i = j + 1 + gid; i < m; i += gsz) G[j + (int64_t)i * m] = sc<S>::scale(G[j + (int64_t)i * m], ri);
     cl_sync();
-    const int tt = m - j - 1;
+    bad = info[t];
+    if (bad) break;
+    // every CTA: R_JJ into shared memory, then one warp per column k of the row panel
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+      const int r = e % nb, c = e / nb;
+      Rjj[r][c] = r <= c ? G[(j0 + r) + (int64_t)(j0 + c) * m] : sc<S>::zero();
+    }
+    __syncthreads();
+    const int k0 = j0 + nb;
+    {
+      const int lane = threadIdx.x & 31;
+      const int gw = gid >> 5, nw = gsz >> 5;
+      for (int k = k0 + gw; k < m; k += nw) {
+        // forward substitution R_JJ^H x = g, column-oriented: once x_i is final
+        // (lane i), the rows below subtract conj(R(i, row)) x_i
+        S g = lane < nb ? G[(j0 + lane) + (int64_t)k * m] : sc<S>::zero();
+        for (int i = 0; i < nb; ++i) {
+          S xi = shfl_s(g, i);
+          xi = sc<S>::scale(xi, 1.0 / sc<S>::re(Rjj[i][i]));
+          if (lane == i) g = xi;
+          if (lane > i && lane < nb) g = sc<S>::sub(g, sc<S>::mul(sc<S>::conj(Rjj[i][lane]), xi));
+        }
+        if (lane < nb) {
+          G[(j0 + lane) + (int64_t)k * m] = g;
+          // transposed copy into the (unused) strict lower triangle of the panel
+          // columns: R(j0+l, k) at G(k, j0+l), read with unit stride below
+          G[k + (int64_t)(j0 + lane) * m] = g;
+        }
+      }
+    }
+    cl_sync();
+    // trailing update of the upper triangle: G(i,k) -= sum_l conj(R(l,i)) R(l,k), k0 <= i <= k
+    const int tt = m - k0;
     for (int64_t e = gid; e < (int64_t)tt * tt; e += gsz) {
-      const int i = j + 1 + (int)(e % tt), k = j + 1 + (int)(e / tt);
+      const int i = k0 + (int)(e % tt), k = k0 + (int)(e / tt);
       if (i > k) continue;
-      // G(i,k) -= conj(R(j,i)) R(j,k)
       S v = G[i + (int64_t)k * m];
-      const S a = sc<S>::conj(G[j + (int64_t)i * m]);
-      const S b = G[j + (int64_t)k * m];
-      v = sc<S>::sub(v, sc<S>::mul(a, b));
+      for (int l = 0; l < nb; ++l) {
+        const S* pl = G + (int64_t)(j0 + l) * m;
+        v = sc<S>::sub(v, sc<S>::mul(sc<S>::conj(pl[i]), pl[k]));
+      }
       G[i + (int64_t)k * m] = v;
     }
-    if (gid == 0) G[j + (int64_t)j * m] = sc<S>::from_re(r);
     cl_sync();
   }
   // clear the strict lower triangle
@@ -471,7 +588,7 @@ template <typename S>
 int launch_cholesky(int nblk, const SmallDesc* d_desc, S* G, int* info, cudaStream_t st, double* diag0,
                     double* minratio) {
   if (nblk <= 0) return 0;
-  return launch_cluster_t(cholesky_kernel<S>, nblk, 0, 1024, st, d_desc, G, info, diag0, minratio);
+  return launch_cluster_t(true, cholesky_kernel<S>, nblk, 0, 1024, st, d_desc, G, info, diag0, minratio);
 }
 
 // ---------------------------------------------------------------------------
@@ -540,7 +657,7 @@ __global__ void __launch_bounds__(1024) triinv_kernel(const SmallDesc* desc, con
 template <typename S>
 int launch_triinv(int nblk, const SmallDesc* d_desc, const S* R, S* Rinv, cudaStream_t st) {
   if (nblk <= 0) return 0;
-  return launch_cluster_t(triinv_kernel<S>, nblk, 0, 1024, st, d_desc, R, Rinv);
+  return launch_cluster_t(true, triinv_kernel<S>, nblk, 0, 1024, st, d_desc, R, Rinv);
 }
 
 // ---------------------------------------------------------------------------
@@ -760,7 +877,7 @@ int launch_jacobi(int nblk, const SmallDesc* d_desc, int max_m, S* A, S* Aalt, S
   if (nblk <= 0) return 0;
   const size_t smem = sizeof(Rot<S>) * (size_t)((max_m + 2) / 2);
   if (smem > 48 * 1024) PD_CK(cudaFuncSetAttribute(jacobi_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  return launch_cluster_t(jacobi_kernel<S>, nblk, smem, 512, st, d_desc, A, Aalt, Vwork, Vout, lam, tol, max_sweeps,
+  return launch_cluster_t(false, jacobi_kernel<S>, nblk, smem, 512, st, d_desc, A, Aalt, Vwork, Vout, lam, tol, max_sweeps,
                           sweeps_out, scratch);
 }
 
