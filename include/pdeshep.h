@@ -79,7 +79,8 @@ typedef struct {
                               tall Gram products (2/4/8) */
   int32_t verbose;         /* 0 quiet */
   void* stream;            /* cudaStream_t */
-  int32_t rr_arith;        /* PDESHEP_MIXED only: PDESHEP_RR_FLOATFLOAT (default) or PDESHEP_RR_FP64 */
+  int32_t rr_arith;        /* PDESHEP_MIXED only: PDESHEP_RR_FLOATFLOAT (default; iterations after the
+                              third run FP64 products) or PDESHEP_RR_FP64 */
   int32_t pad0;
   const char* tune_cache;  /* file that keeps tuned choices across processes; NULL = in-process */
   int32_t graphs;          /* 1: with resident factors, each filter pass (right-hand sides,
@@ -143,6 +144,10 @@ typedef struct {
   int32_t gram_splits_used;/* split count of the last tall Gram product */
   int32_t tuned;           /* number of choices measured by the autotuner in this call */
   int32_t graph_launches;  /* filter passes replayed from CUDA graphs */
+  int32_t cholqr_shifted;  /* slices whose Gram matrix needed a shifted Cholesky */
+  int32_t gram_fp64;       /* float-float mode: slices whose Gram matrices were redone in FP64 */
+  int32_t rr_fp64_from;    /* float-float mode: iteration from which the Rayleigh-Ritz products ran in
+                              FP64 because slices were still unconverged after 3 iterations (0: never) */
 } pdeshep_stats;
 
 /* Forget every tuned choice held in this process (cache files are kept). */

@@ -162,6 +162,25 @@ __global__ void accumulate_kernel(int64_t n, const AccDesc* ad, const double2* _
   }
 }
 
+// G <- G + rel * max_i G_ii * I for each small block (shifted Cholesky)
+template <typename S>
+__global__ void shift_diag_kernel(const SmallDesc* desc, S* Gall, double rel) {
+  const SmallDesc d = desc[blockIdx.x];
+  S* G = Gall + d.off;
+  __shared__ double red[32];
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < d.m; i += blockDim.x) mx = fmax(mx, sc<S>::re(G[i + (int64_t)i * d.m]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+  for (int i = threadIdx.x; i < d.m; i += blockDim.x) {
+    S* g = G + i + (int64_t)i * d.m;
+    *g = sc<S>::from_re(sc<S>::re(*g) + rel * t);
+  }
+}
+
 // A <- (A + A^H)/2 for each small block
 template <typename S>
 __global__ void symmetrize_kernel(const SmallDesc* desc, S* Aall) {
@@ -546,7 +565,14 @@ struct Feast {
 
   // Mixed precision runs the FP64-class products of the Rayleigh-Ritz step in
   // float-float arithmetic on the FP32 pipes; plain FEAST keeps them in FP64.
-  int ff() const { return o->precision == PDESHEP_MIXED && o->rr_arith == PDESHEP_RR_FLOATFLOAT ? 1 : 0; }
+  int ff() const {
+    return o->precision == PDESHEP_MIXED && o->rr_arith == PDESHEP_RR_FLOATFLOAT && !rr_fp64_now ? 1 : 0;
+  }
+  // Float-float products resolve eigenvector components down to ~1e-13 ||B|| / gap;
+  // slices whose spectrum is dense enough that this stalls their residuals above the
+  // tolerance are finished with FP64 products (set after kFFIterations iterations).
+  bool rr_fp64_now = false;
+  static constexpr int kFFIterations = 3;
 
   // autotuned choices (see tune.cu)
   int rhs_chunk = 32;
@@ -616,7 +642,7 @@ struct FeastRun : Feast<S, C> {
 
   // C = op(A) B over the active slices; kind 0: C(m0 x m0) = A^H B with A,B n x m0 blocks;
   // kind 1: C(n x m0) = A(n x m0) * B(m0 x m0 small block).
-  int gemm(int kind, const S* A, const S* Bm, S* Cm, int tri = 0) {
+  int gemm(int kind, const S* A, const S* Bm, S* Cm, int tri = 0, int force_fp64 = 0) {
     const int na = (int)active.size();
     std::vector<GemmItem<S>> it(na);
     for (int a = 0; a < na; ++a) {
@@ -654,7 +680,7 @@ struct FeastRun : Feast<S, C> {
     double fl = 0.0;  // algorithmic: Hermitian or triangular products count half
     for (int s : active) fl += this->cw() * (double)n * m0[s] * m0[s] * ((kind == 0 || tri) ? 0.5 : 1.0);
     PD_TRY(this->kt.begin(PDESHEP_KG_GEMM));
-    const int ff = this->ff();
+    const int ff = this->ff() && !force_fp64;
     if (kind == 0) {
       const int64_t t1 = ceil_div(mm, ff ? 64 : 32);
       const int64_t tiles = (int64_t)na * t1 * (t1 + 1) / 2;
@@ -716,14 +742,20 @@ struct FeastRun : Feast<S, C> {
   }
 
   // Gram matrix, Cholesky and R^{-1} of the active slices' blocks of p.Q (Q itself unchanged).
-  int chol_factor() {
+  // shift_rel > 0: factor G + shift_rel max_i G_ii I instead (shifted CholQR)
+  // fp64_gram: the Gram matrix in FP64 arithmetic even in float-float mode
+  int chol_factor(double shift_rel = 0.0, int fp64_gram = 0) {
     const int na = (int)active.size();
     S* G = (S*)p.small_G;
     S* I = (S*)p.small_I;
     double flsmall = 0.0;
     for (int s : active) flsmall += this->cw() * (double)m0[s] * m0[s] * m0[s] / 3.0;
-    PD_TRY(gemm(0, (S*)p.Q, (S*)p.Q, G));
+    PD_TRY(gemm(0, (S*)p.Q, (S*)p.Q, G, 0, fp64_gram));
     PD_TRY(this->kt.begin(PDESHEP_KG_SMALL));
+    if (shift_rel > 0.0) {
+      shift_diag_kernel<S><<<na, 256, 0, st>>>(p.d_small, G, shift_rel);
+      PD_CK_LAUNCH();
+    }
     PD_TRY(launch_cholesky<S>(na, p.d_small, G, p.info, st, p.diag0, p.minratio));
     PD_TRY(launch_triinv<S>(na, p.d_small, G, I, st));
     return this->kt.end(flsmall);
@@ -753,34 +785,90 @@ struct FeastRun : Feast<S, C> {
     S* W = (S*)p.small_W;
     S* Aq = (S*)p.small_A;
     S* T = (S*)p.small_T;
+    // Orthonormalisation.  Every active slice gets Q^H Q = R^H R.  A slice whose
+    // Cholesky breaks down is refactored with a small diagonal shift (shifted
+    // CholQR); slices with a shifted factor or nearly dependent columns
+    // (min_c R_cc^2 / G_cc < 1/4) get explicit passes Q <- Q R^{-1} (at most 3)
+    // before the final factor, which the Rayleigh-Ritz step applies implicitly.
+    const std::vector<int> keep = active;
+    std::vector<int> info_s(K, 0), shifted(K, 0);
+    std::vector<double> mr_s(K, 1.0);
+    auto read_status = [&](const std::vector<int>& set) -> int {
+      std::vector<int> info(K, 0);
+      std::vector<double> mr(K, 1.0);
+      PD_CK(cudaMemcpyAsync(info.data(), p.info, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
+      PD_CK(cudaMemcpyAsync(mr.data(), p.minratio, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
+      PD_CK(cudaStreamSynchronize(st));
+      // per-slice kernel outputs are indexed by position in the batch
+      for (size_t a = 0; a < set.size(); ++a) {
+        info_s[set[a]] = info[a];
+        mr_s[set[a]] = mr[a];
+      }
+      return 0;
+    };
     PD_TRY(chol_factor());
-    std::vector<int> info(K, 0);
-    std::vector<double> mr(K, 1.0);
-    PD_CK(cudaMemcpyAsync(info.data(), p.info, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
-    PD_CK(cudaMemcpyAsync(mr.data(), p.minratio, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
-    PD_CK(cudaStreamSynchronize(st));
-    // per-slice kernel outputs (info, minratio, sweeps, offratio) are indexed by position in the active batch
-    for (int a = 0; a < na; ++a)
-      if (info[a]) return PDESHEP_CHOLQR_BREAKDOWN;
-    std::vector<int> again;
-    for (int a = 0; a < na; ++a)
-      if (mr[a] < 0.25) again.push_back(active[a]);
-    if (!again.empty()) {
-      std::vector<int> keep = active;
+    PD_TRY(read_status(active));
+    // Float-float Gram entries carry ~1e-13 relative error, too coarse for a basis
+    // whose condition number passes ~1e3 (the error enters R through cond^2): such
+    // slices get their Gram matrices in FP64 for the rest of this orthonormalisation.
+    std::vector<int> gram64(K, 0);
+    if (this->ff()) {
+      std::vector<int> ill;
+      for (int s : keep)
+        if (info_s[s] || mr_s[s] < 1e-6) {
+          ill.push_back(s);
+          gram64[s] = 1;
+        }
+      if (!ill.empty()) {
+        active = ill;
+        PD_TRY(upload_active());
+        PD_TRY(chol_factor(0.0, 1));
+        PD_TRY(read_status(active));
+        stats.gram_fp64 += (int)ill.size();
+      }
+    }
+    auto any64 = [&](const std::vector<int>& set) {
+      for (int s : set)
+        if (gram64[s]) return 1;
+      return 0;
+    };
+    const double shift_rel = 1e-14;
+    for (int pass = 0;; ++pass) {
+      std::vector<int> bad, again;
+      for (int s : keep) {
+        if (info_s[s])
+          bad.push_back(s);
+        else if (mr_s[s] < 0.25 || shifted[s] == 1)
+          again.push_back(s);
+      }
+      if (!bad.empty()) {
+        for (int s : bad) {
+          if (shifted[s] || pass >= 3) return PDESHEP_CHOLQR_BREAKDOWN;
+          shifted[s] = 1;
+        }
+        active = bad;
+        PD_TRY(upload_active());
+        PD_TRY(chol_factor(shift_rel, any64(bad)));
+        PD_TRY(read_status(active));
+        for (int s : bad) {
+          if (info_s[s]) return PDESHEP_CHOLQR_BREAKDOWN;
+          again.push_back(s);
+        }
+        stats.cholqr_shifted += (int)bad.size();
+      }
+      if (again.empty() || pass >= 3) break;
       active = again;
       PD_TRY(upload_active());
-      PD_TRY(gemm(1, (S*)p.Q, I, (S*)p.Q2, 1));
+      PD_TRY(gemm(1, (S*)p.Q, I, (S*)p.Q2, 1));   // Q R^{-1}
       for (int s : active)
         PD_CK(cudaMemcpyAsync((S*)p.Q + col_off[s] * n, (S*)p.Q2 + col_off[s] * n, sizeof(S) * n * m0[s],
                               cudaMemcpyDeviceToDevice, st));
-      PD_TRY(chol_factor());
-      active = keep;
-      PD_TRY(upload_active());
-      PD_CK(cudaMemcpyAsync(info.data(), p.info, sizeof(int) * K, cudaMemcpyDeviceToHost, st));
-      PD_CK(cudaStreamSynchronize(st));
-      for (int a = 0; a < (int)again.size(); ++a)
-        if (info[a]) return PDESHEP_CHOLQR_BREAKDOWN;
+      PD_TRY(chol_factor(0.0, any64(again)));
+      PD_TRY(read_status(active));
+      for (int s : again) shifted[s] = shifted[s] ? 2 : 0;  // a shifted slice had its explicit pass
     }
+    active = keep;
+    PD_TRY(upload_active());
     PD_TRY(band_mm((S*)p.Q, (S*)p.BQ));
     PD_TRY(gemm(0, (S*)p.Q, (S*)p.BQ, Aq));         // Q^H B Q
     PD_TRY(small_mm(false, Aq, I, T, 0, 1));         // (Q^H B Q) R^{-1}
@@ -1276,6 +1364,11 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   int it = 1;
   for (; it <= o->max_iter && !F.active.empty(); ++it) {
     F.mode = (refine && it > 1) ? 1 : 0;
+    if (it > F.kFFIterations && F.ff()) {
+      F.rr_fp64_now = true;
+      F.eig.ff = 0;
+      F.stats.rr_fp64_from = it;
+    }
     // a failure of the counts (non-finite band, subspace too small) takes precedence
     auto first_error = [&](int r) -> int {
       if (!r) return 0;
