@@ -308,6 +308,8 @@ def run_gpu(args):
                                          dtype="c64+f64", rr_arith=pk.RR_FP64)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_leg(pk, torch, seq, inputs[: max(1, min(K, args.e2e_steps))], stream)
+    if rank == 0 and not args.no_proposal:
+        out["slice_proposal"] = proposal_leg(pk, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(seq.host, seq.bounds0, seq.m0, seq.bnorm[0])
     if dist:
@@ -337,6 +339,48 @@ def plain_leg(pk, torch, seq, inputs, stream, precision=None, dtype="c128+f64", 
     return {"value": round(pairs / t, 2), "unit": "eigenpairs/s", "steps": len(inputs),
             "ms_per_step": round(t * 1e3 / len(inputs), 3), "iterations_per_step": iters,
             "dtype": dtype}
+
+
+def proposal_leg(pk, torch, dev):
+    """Learned slice proposal at the proposer's configuration (complex mixture bands, n = 16384,
+    b = 64, 64 equal-count slices), reported beside the FEAST metric.  The network is trained here
+    on 256 smaller spectra of the same generator (n = 1024, b = 8; the features are scale-free),
+    labels by inertia bisection, 800 Adam steps; then held-out bands are sliced with the network
+    and with equal widths (the no-network baseline); counts are exact in both."""
+    from paper_2012_00506_gb300 import slicer
+
+    def family(seed, n, b):
+        g = np.random.default_rng(seed)
+        k = int(g.integers(1, 7))
+        return synth.mixture_band(n, b, seed, is_complex=True, ncomp=k, comp_sigma=float(g.uniform(0.01, 0.2)),
+                                  off_sigma=float(g.uniform(0.005, 0.03)), means=g.uniform(-1.0, 1.0, size=k),
+                                  weights=g.dirichlet(np.ones(k)))
+
+    t0 = time.perf_counter()
+    train = [torch.from_numpy(family(synth.config_seed(4) + s, 1024, 8)).to(dev) for s in range(256)]
+    params, losses, _ = slicer.train(train, steps=800, batch=64, lr=1e-3, seed=0, log_every=799)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    res = {"mlp": [], "none": []}
+    n, nsl = 16384, 64
+    tgt = np.floor(n * np.arange(nsl + 1) / nsl + 0.5).astype(int)
+    for s in range(3):
+        band = torch.from_numpy(family(synth.config_seed(4) + 10000 + s, n, 64)).to(dev)
+        for name, p in (("mlp", params), ("none", None)):
+            slicer.propose_slices(band, p, nslices=nsl, count_tol=16)          # warm
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            pr = slicer.propose_slices(band, p, nslices=nsl, count_tol=16)
+            t = time.perf_counter() - t1
+            res[name].append((t, pr.inertia_evals, pr.used_fallback,
+                              float(np.mean(np.abs(pr.proposed_counts - tgt)[1:-1])), int(pr.counts.sum())))
+    out = {"config": "complex mixture bands n=16384 b=64, 64 slices, count tolerance 16", "train_seconds":
+           round(t_train, 2), "train_loss": [round(l, 6) for _, l in losses]}
+    for name in ("mlp", "none"):
+        r = np.array([x[:4] for x in res[name]])
+        out[name] = {"ms": round(1e3 * float(np.mean(r[:, 0])), 2), "inertia_evals": float(np.mean(r[:, 1])),
+                     "boundaries_fixed": float(np.mean(r[:, 2])), "proposal_count_error": round(float(np.mean(r[:, 3])), 1)}
+    return out
 
 
 def e2e_leg(pk, torch, seq, inputs, stream):
@@ -504,6 +548,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-proposal", action="store_true", help="skip the slice-proposal report")
     ap.add_argument("--profile-case", action="store_true",
                     help="run a reduced instance of the workload (for ncu captures) instead of the bench")
     ap.add_argument("--profile-slices", type=int, default=2)

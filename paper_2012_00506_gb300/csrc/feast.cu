@@ -808,14 +808,16 @@ struct FeastRun : Feast<S, C> {
     };
     PD_TRY(chol_factor());
     PD_TRY(read_status(active));
-    // Float-float Gram entries carry ~1e-13 relative error, too coarse for a basis
-    // whose condition number passes ~1e3 (the error enters R through cond^2): such
-    // slices get their Gram matrices in FP64 for the rest of this orthonormalisation.
+    // Float-float Gram entries carry ~1e-13 relative error, which enters R through
+    // cond(Q)^2: an explicit pass still repairs a basis of condition up to ~1e6, but
+    // beyond that the Cholesky factor breaks down.  Slices whose float-float Gram
+    // breaks down get their Gram matrices in FP64 for the rest of this
+    // orthonormalisation (a shift below 1e-13 would not help there).
     std::vector<int> gram64(K, 0);
     if (this->ff()) {
       std::vector<int> ill;
       for (int s : keep)
-        if (info_s[s] || mr_s[s] < 1e-6) {
+        if (info_s[s]) {
           ill.push_back(s);
           gram64[s] = 1;
         }
