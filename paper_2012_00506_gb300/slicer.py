@@ -153,12 +153,14 @@ def equal_count_targets(band, nslices: int = N_OUT, rtol: float = 1e-7, b=None, 
 
 
 def train(bands, steps: int = 2000, batch: int = 64, lr: float = 1e-3, seed: int = 0, params=None,
-          feature_seed: int = 0, log_every: int = 0):
-    """Train on a list of bands (CUDA tensors).  Returns (params, losses, (X, T))."""
+          feature_seed: int = 0, log_every: int = 0, label_rtol: float = 1e-7):
+    """Train on a list of bands (CUDA tensors).  Returns (params, losses, (X, T)).
+    ``label_rtol``: relative accuracy of the eigenvalue enclosures behind the labels
+    (regression targets only: 1e-4 of the spectrum is far below the network's error)."""
     torch = _torch()
     device = bands[0].device
     X = torch.stack([features(bd, seed=feature_seed) for bd in bands])
-    T = torch.from_numpy(np.stack([equal_count_targets(bd) for bd in bands])).to(device)
+    T = torch.from_numpy(np.stack([equal_count_targets(bd, rtol=label_rtol) for bd in bands])).to(device)
     if params is None:
         params = init_params(seed, device)
     tr = Trainer(params, lr=lr, max_batch=batch)
