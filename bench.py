@@ -46,8 +46,9 @@ SEED = synth.config_seed(2)
 WORKLOAD = ("SCF sequence of complex Hermitian bands n=8192 b=64 (B_k+1 = B_k + 1e-3 E_k), 8 slices "
             "over the lowest 20% (1638 eigenpairs), Ne=8, m0=max(1.3m, m+10), warm start")
 METRIC = ("eigenpairs/s at residual <= 1e-10 (mixed path: complex64 band LU/solves with FP64 residual refinement, "
-          "float-float Rayleigh-Ritz products, FP64 inertia and small eigensolve; plain FP64 and mixed with FP64 "
-          "Rayleigh-Ritz products reported alongside)")
+          "tall Rayleigh-Ritz products as bf16 digit products on the tensor cores (FP64-class), float-float band "
+          "and small products, FP64 inertia and eigensolver refinement; plain FP64 and mixed with float-float or "
+          "FP64 Rayleigh-Ritz products reported alongside)")
 
 # FP64 / FP32 ALU peaks from unit counts and clocks (152 SMs at 2070 MHz): FP32 = 152 x 128
 # lanes x 2 flops x 2.07 GHz; FP64 = the part's 1.25 TFLOP/s figure.
@@ -57,10 +58,31 @@ PEAK_FP64_TFLOPS = 1.25
 # instructions (4 real products x (2 for the exact product, 2 for the cross terms, 6 for the
 # two-sum, 3 for the low word)); the FP32 pipes issue 152 x 128 x 2.07e9 instructions/s.
 PEAK_FF_TFLOPS = 152 * 128 * 2.07e9 * 8 / 52 / 1e12
-GROUP_BOUND = {"factor": ("alu", PEAK_FP32_TFLOPS, "fp32"), "solve": ("alu", PEAK_FP32_TFLOPS, "fp32"),
-               "accum": ("hbm", None, None), "gemm": ("alu", PEAK_FF_TFLOPS, "float-float (FP32 pipe)"),
-               "small": ("alu", PEAK_FP64_TFLOPS, "fp64"), "bandmm": ("alu", PEAK_FF_TFLOPS, "float-float (FP32 pipe)"),
-               "inertia": ("alu", PEAK_FP64_TFLOPS, "fp64"), "eig": ("alu", PEAK_FP32_TFLOPS, "fp32")}
+# Tensor-core tall products: 26 bf16 digit products per FP64-class product, so the usable peak is
+# the measured sustained bf16 tensor rate (the GEMM runs inside a long step) divided by 26.
+TC_DIGIT_PAIRS = 26
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "of fallback"
+
+
+BF16_SUSTAINED_TFLOPS, BF16_PEAK_SOURCE = _measured_peaks()
+PEAK_TC_TFLOPS = BF16_SUSTAINED_TFLOPS / TC_DIGIT_PAIRS
+GROUP_BOUND = {"factor": ("alu", PEAK_FP32_TFLOPS, "fp32 from unit counts and clocks"),
+               "solve": ("alu", PEAK_FP32_TFLOPS, "fp32 from unit counts and clocks"),
+               "accum": ("hbm", None, None),
+               "gemm": ("tensor", PEAK_TC_TFLOPS, "bf16 tensor cores (sustained, %s) / %d digit products per "
+                        "FP64-class product" % (BF16_PEAK_SOURCE, TC_DIGIT_PAIRS)),
+               "small": ("alu", PEAK_FP64_TFLOPS, "fp64 (part's figure)"),
+               "bandmm": ("alu", PEAK_FF_TFLOPS, "float-float (FP32 pipe) from unit counts and clocks"),
+               "inertia": ("alu", PEAK_FP64_TFLOPS, "fp64 (part's figure)"),
+               "eig": ("alu", PEAK_FP32_TFLOPS, "fp32 from unit counts and clocks")}
 
 
 def boundary_indices():
@@ -156,7 +178,7 @@ class Sequence:
         g = synth.rng(SEED + 999)
         x0 = (g.normal(size=(self.M, N)) + 1j * g.normal(size=(self.M, N))) / np.sqrt(2.0)
         self.x0 = torch.from_numpy(x0).to(dev)
-        self.opts = dict(ne=NE, tol=TOL, ellipse_ratio=RHO, max_iter=40, autotune=1)
+        self.opts = dict(ne=NE, tol=TOL, ellipse_ratio=RHO, max_iter=40, autotune=1, rr_arith=pk.RR_TENSOR)
         self.ws = {}
 
     def next_bounds(self, res, bounds):
@@ -181,17 +203,22 @@ class Sequence:
         nb.append(0.5 * (lam[-1] + nxt) if lam.size == NEV else bounds[-1])
         return nb
 
-    def workspace(self, precision):
-        if precision not in self.ws:
-            nbytes = self.pk.workspace_size(N, BW, True, self.m0, NE, self.pk.default_opts(precision=precision))
-            self.ws[precision] = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.dev)
-        return self.ws[precision]
+    def workspace(self, precision, rr_arith=None):
+        """Workspace for the given arithmetic (its size depends on both choices)."""
+        rr = self.opts["rr_arith"] if rr_arith is None else rr_arith
+        key = (precision, rr)
+        if key not in self.ws:
+            o = self.pk.default_opts(precision=precision, rr_arith=rr)
+            nbytes = self.pk.workspace_size(N, BW, True, self.m0, NE, o)
+            self.ws[key] = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.dev)
+        return self.ws[key]
 
     def step(self, k, x0, bounds, precision, **extra):
         kw = dict(self.opts)
         kw.update(extra)
-        return self.pk.band_slice(self.bands[k], bounds, self.m0, x0, workspace=self.workspace(precision),
-                                  bnorm=self.bnorm[k], precision=precision, raise_on_error=False, **kw)
+        return self.pk.band_slice(self.bands[k], bounds, self.m0, x0,
+                                  workspace=self.workspace(precision, kw["rr_arith"]), bnorm=self.bnorm[k],
+                                  precision=precision, raise_on_error=False, **kw)
 
 
 def good_pairs(res, m0):
@@ -282,7 +309,7 @@ def run_gpu(args):
         achieved = kg_fl[dom] / (kg_ms[dom] / 1e3) / 1e12
         roof = {"kernel_group": dom, "bound": bound, "achieved": round(achieved, 4), "peak": peak,
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None,
-                "peak_kind": f"{kind} from unit counts and clocks", "traffic": traffic_for(dom),
+                "peak_kind": kind, "traffic": traffic_for(dom),
                 "launches": kg_n[dom], "share_of_step": round(kg_ms[dom] / 1e3 / t_s, 4)}
     groups = {g: {"ms": round(kg_ms[g], 3), "launches": kg_n[g],
                   "tflops": round(kg_fl[g] / (kg_ms[g] / 1e3) / 1e12, 4) if kg_ms[g] > 0 else None}
@@ -291,7 +318,7 @@ def run_gpu(args):
     out = {"metric": METRIC,
            "value": round(value, 2), "unit": "eigenpairs/s", "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": round(t_s * 1e3 / K, 3), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "c64+ff32x2+f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "c64+bf16x6+ff32x2+f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": N, "b": BW, "slices": NSLICE, "ne": NE, "nev": NEV,
                       "m0": seq.m0.tolist(), "tol": TOL, "ellipse_ratio": RHO,
                       "l2": "inputs larger than L2 (factor set ~1.2 GB per step)",
@@ -304,6 +331,9 @@ def run_gpu(args):
     if rank == 0 and not args.no_plain and args.plain_steps > 0:
         out["plain_fp64"] = plain_leg(pk, torch, seq, inputs[: args.plain_steps], stream)
         # mixed precision with the Rayleigh-Ritz products kept in FP64 arithmetic
+        out["mixed_rr_floatfloat"] = plain_leg(pk, torch, seq, inputs[: args.plain_steps], stream,
+                                               precision=pk.MIXED, dtype="c64+ff32x2+f64",
+                                               rr_arith=pk.RR_FLOATFLOAT)
         out["mixed_rr_fp64"] = plain_leg(pk, torch, seq, inputs[: args.plain_steps], stream, precision=pk.MIXED,
                                          dtype="c64+f64", rr_arith=pk.RR_FP64)
     if rank == 0 and not args.no_e2e:
@@ -324,7 +354,7 @@ def plain_leg(pk, torch, seq, inputs, stream, precision=None, dtype="c128+f64", 
     precision = pk.FP64 if precision is None else precision
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    seq.workspace(precision)
+    seq.workspace(precision, extra.get("rr_arith"))
     seq.step(*inputs[0], precision, **extra)     # untimed: tunes this arithmetic's choices
     torch.cuda.synchronize()
     e0.record(stream)
@@ -429,7 +459,7 @@ def traffic_for(group):
 
 
 WORKLOAD_KEY = "c2"
-GROUP_SOURCES = {"solve": "band_lu.cu", "factor": "band_lu.cu", "gemm": "dense.cu", "small": "dense.cu",
+GROUP_SOURCES = {"solve": "band_lu.cu", "factor": "band_lu.cu", "gemm": "tcgemm.cu", "small": "dense.cu",
                  "bandmm": "dense.cu", "accum": "feast.cu", "inertia": "inertia.cu", "eig": "dense.cu"}
 
 

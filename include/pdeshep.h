@@ -79,8 +79,12 @@ typedef struct {
                               tall Gram products (2/4/8) */
   int32_t verbose;         /* 0 quiet */
   void* stream;            /* cudaStream_t */
-  int32_t rr_arith;        /* PDESHEP_MIXED only: PDESHEP_RR_FLOATFLOAT (default; iterations after the
-                              third run FP64 products) or PDESHEP_RR_FP64 */
+  int32_t rr_arith;        /* PDESHEP_MIXED only: arithmetic of the Rayleigh-Ritz products.
+                              PDESHEP_RR_TENSOR: tall products (Gram, projection, basis update) as
+                              bf16 digit products on the tensor cores, FP64-class; band and small
+                              products float-float.  PDESHEP_RR_FLOATFLOAT (default): all products
+                              float-float.  In both, iterations after the third run the
+                              float-float products in FP64.  PDESHEP_RR_FP64: all products FP64 */
   int32_t pad0;
   const char* tune_cache;  /* file that keeps tuned choices across processes; NULL = in-process */
   int32_t graphs;          /* 1: with resident factors, each filter pass (right-hand sides,
@@ -97,6 +101,7 @@ typedef struct {
 /* FP64 arithmetic.  Counts and residual tests are the same either way.       */
 #define PDESHEP_RR_FLOATFLOAT 0
 #define PDESHEP_RR_FP64 1
+#define PDESHEP_RR_TENSOR 2   /* bf16 digit products on the tensor cores (FP64-class) */
 
 /* Kernel groups timed separately (CUDA events around each launch). */
 #define PDESHEP_KG_INERTIA 0     /* LDL^T inertia (and the band amax reduction) */
@@ -280,6 +285,30 @@ int pdeshep_band_matmul(int64_t n, int32_t b, int32_t is_complex, const void* d_
 size_t pdeshep_cholqr_workspace_size(int64_t n, int32_t nblk, const int32_t* h_m, int32_t is_complex);
 int pdeshep_cholqr(int64_t n, int32_t is_complex, int32_t nblk, const int32_t* h_m, void* d_q,
                    int32_t passes, void* d_r, void* d_work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Tall block products of the Rayleigh-Ritz step (Section 2.2: the Gram      */
+/* matrix Q^H Q of the orthonormalisation, the projection Q^H (B Q) and the  */
+/* basis update Q W) on a batch of column blocks of n rows.  Block t of d_a   */
+/* (and d_b for kind 0) is n x m_t, column-major (ld n), at column           */
+/* sum_{u<t} m_u; the m_t x m_t blocks (output of kinds 0 and 1, second      */
+/* operand of kind 2) sit at element offset sum_{u<t} m_u^2, column-major.   */
+/*   kind PDESHEP_GEMM_AHB    C_t = A_t^H B_t                                 */
+/*   kind PDESHEP_GEMM_GRAM   C_t = A_t^H A_t (Hermitian; d_b unused)         */
+/*   kind PDESHEP_GEMM_UPDATE C_t = A_t B_t, n x m_t in the layout of d_a     */
+/* arith: PDESHEP_RR_FP64 (FP64 pipes), PDESHEP_RR_FLOATFLOAT (float-float   */
+/* on the FP32 pipes) or PDESHEP_RR_TENSOR (bf16 digit products on the       */
+/* tcgen05 tensor cores, FP64-class accuracy: a few units of 2^-48 |a| |b|  */
+/* per entry).  Returns PDESHEP_DEVICE_TIMEOUT (after synchronising) if a    */
+/* tensor-core kernel's bounded wait gave up.                                */
+/* ------------------------------------------------------------------------ */
+#define PDESHEP_GEMM_AHB 0
+#define PDESHEP_GEMM_GRAM 1
+#define PDESHEP_GEMM_UPDATE 2
+size_t pdeshep_block_gemm_workspace_size(int64_t n, int32_t is_complex, int32_t nblk, const int32_t* h_m);
+int pdeshep_block_gemm(int32_t kind, int32_t arith, int64_t n, int32_t is_complex, int32_t nblk,
+                       const int32_t* h_m, const void* d_a, const void* d_b, void* d_c, void* d_work,
+                       size_t work_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched small dense Hermitian eigensolver for A_q W_q = W_q Lambda_q       */

@@ -26,6 +26,10 @@ FP64 = 0
 MIXED = 1
 RR_FLOATFLOAT = 0
 RR_FP64 = 1
+RR_TENSOR = 2
+GEMM_AHB = 0
+GEMM_GRAM = 1
+GEMM_UPDATE = 2
 REFINE_NONE = 0
 REFINE_RESIDUAL = 1
 
@@ -47,6 +51,7 @@ EXPORTED = [
     "pdeshep_mlp_param_count", "pdeshep_slice_features_workspace_size", "pdeshep_slice_features",
     "pdeshep_mlp_workspace_size", "pdeshep_mlp_forward", "pdeshep_mlp_grad", "pdeshep_mlp_train_step",
     "pdeshep_propose_workspace_size", "pdeshep_propose_slices", "pdeshep_tune_reset",
+    "pdeshep_block_gemm_workspace_size", "pdeshep_block_gemm",
 ]
 
 
@@ -132,6 +137,8 @@ def load(path: str = LIB_PATH):
         "pdeshep_cholqr_workspace_size": (sz, [i64, i32, P, i32]),
         "pdeshep_cholqr": (C.c_int, [i64, i32, i32, P, P, i32, P, P, sz, P]),
         "pdeshep_eigh_workspace_size": (sz, [i32, P, i32]),
+        "pdeshep_block_gemm_workspace_size": (sz, [i64, i32, i32, P]),
+        "pdeshep_block_gemm": (C.c_int, [i32, i32, i64, i32, i32, P, P, P, P, P, sz, P]),
         "pdeshep_eigh": (C.c_int, [i32, i32, P, P, P, P, P, sz, P]),
         "pdeshep_workspace_size": (sz, [i64, i32, i32, i32, P, i32, C.POINTER(Opts)]),
         "pdeshep_band_slice": (C.c_int, [i64, i32, i32, P, i64, i32, P, i32, P, P, P, P, P, sz,
@@ -324,6 +331,40 @@ def cholqr(Q, sizes, passes=2, stream=None):
         out.append(R[off: off + mt * mt].reshape(mt, mt).T)  # column-major -> (row, col)
         off += mt * mt
     return Q, out
+
+
+def block_gemm(kind, A, sizes, B=None, arith=RR_TENSOR, stream=None):
+    """Batched tall products of the Rayleigh-Ritz step on column blocks.
+
+    ``A`` (and ``B`` for GEMM_AHB): tensors of shape (sum(sizes), n), i.e. column-major
+    n x sum(sizes), block t holding sizes[t] columns.  GEMM_AHB / GEMM_GRAM return the list
+    [A_t^H B_t] (B_t = A_t for the Gram matrix) of (m_t, m_t) tensors; GEMM_UPDATE takes
+    ``B`` as a list of (m_t, m_t) tensors and returns the blocks A_t B_t in the layout of A.
+    ``arith``: RR_TENSOR (tensor-core digit products), RR_FLOATFLOAT or RR_FP64."""
+    torch = _torch()
+    lib = load()
+    A = A.contiguous()
+    n = A.shape[1]
+    cplx = 1 if A.is_complex() else 0
+    m = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32))
+    msq = int(np.sum(m.astype(np.int64) ** 2))
+    if kind == GEMM_UPDATE:
+        Bd = torch.cat([b_.to(A.dtype).T.contiguous().reshape(-1) for b_ in B])
+        Cm = torch.empty_like(A)
+    else:
+        Bd = A if kind == GEMM_GRAM else B.to(A.dtype).contiguous()
+        Cm = torch.empty(msq, dtype=A.dtype, device=A.device)
+    ws = _workspace(lib.pdeshep_block_gemm_workspace_size(n, cplx, m.size, _np_ptr(m)), A.device)
+    st = lib.pdeshep_block_gemm(int(kind), int(arith), n, cplx, m.size, _np_ptr(m), _ptr(A), _ptr(Bd), _ptr(Cm),
+                                _ptr(ws), ws.numel(), _stream(stream))
+    _check("pdeshep_block_gemm", st)
+    if kind == GEMM_UPDATE:
+        return Cm
+    out, off = [], 0
+    for mt in m:
+        out.append(Cm[off: off + mt * mt].reshape(mt, mt).T)
+        off += mt * mt
+    return out
 
 
 def eigh(blocks, stream=None):

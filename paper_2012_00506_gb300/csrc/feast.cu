@@ -28,6 +28,7 @@
 
 #include "band_lu.cuh"
 #include "dense.cuh"
+#include "tcgemm.cuh"
 
 namespace pdeshep {
 
@@ -392,6 +393,7 @@ struct Plan {
   char* inertia_ws;
   size_t inertia_bytes;
   void* band_ff;   // float-float copy of the band (mixed precision only)
+  TcScratch tc;    // digit planes of the tensor-core products (PDESHEP_RR_TENSOR only)
   void* solve_queue; // work list of the persistent solves
   // wave area
   char* wave_base;
@@ -555,6 +557,7 @@ struct Feast {
     q.inertia_bytes = std::max(inertia_ws_bytes(b, cplx, K + 1), bisect_ws_bytes(b, cplx, 2, 16));
     q.inertia_ws = a.take<char>(q.inertia_bytes);
     q.band_ff = ff() ? (void*)a.take<char>(band_split_bytes(n, b, cplx)) : nullptr;
+    if (tc()) q.tc = plan_tc_scratch(a, TcShape{n, cplx, m0});
     q.solve_queue = a.take<char>(solve_queue_bytes(K * ne, max_m0));
     if (carve) {
       p = q;
@@ -564,13 +567,18 @@ struct Feast {
   }
 
   // Mixed precision runs the FP64-class products of the Rayleigh-Ritz step in
-  // float-float arithmetic on the FP32 pipes; plain FEAST keeps them in FP64.
+  // float-float arithmetic on the FP32 pipes (band products, small m0 x m0
+  // products, eigensolver refinement) and, with PDESHEP_RR_TENSOR, the tall
+  // products (Gram matrix, projection, basis update) as bf16 digit products on
+  // the tensor cores; plain FEAST keeps everything in FP64.
   int ff() const {
-    return o->precision == PDESHEP_MIXED && o->rr_arith == PDESHEP_RR_FLOATFLOAT && !rr_fp64_now ? 1 : 0;
+    return o->precision == PDESHEP_MIXED && o->rr_arith != PDESHEP_RR_FP64 && !rr_fp64_now ? 1 : 0;
   }
+  int tc() const { return o->precision == PDESHEP_MIXED && o->rr_arith == PDESHEP_RR_TENSOR ? 1 : 0; }
   // Float-float products resolve eigenvector components down to ~1e-13 ||B|| / gap;
   // slices whose spectrum is dense enough that this stalls their residuals above the
-  // tolerance are finished with FP64 products (set after kFFIterations iterations).
+  // tolerance are finished with FP64 products (set after kFFIterations iterations;
+  // the tensor-core tall products are FP64-class already and stay).
   bool rr_fp64_now = false;
   static constexpr int kFFIterations = 3;
 
@@ -642,8 +650,22 @@ struct FeastRun : Feast<S, C> {
 
   // C = op(A) B over the active slices; kind 0: C(m0 x m0) = A^H B with A,B n x m0 blocks;
   // kind 1: C(n x m0) = A(n x m0) * B(m0 x m0 small block).
-  int gemm(int kind, const S* A, const S* Bm, S* Cm, int tri = 0, int force_fp64 = 0) {
+  int gemm(int kind, const S* A, const S* Bm, S* Cm, int tri = 0, int force_fp64 = 0, int reuse_a = 0) {
     const int na = (int)active.size();
+    if (this->tc()) {
+      // tensor-core digit products (FP64-class: no escalation needed)
+      double fl = 0.0;
+      for (int s : active) fl += this->cw() * (double)n * m0[s] * m0[s] * ((kind == 0 && A == Bm) ? 0.5 : 1.0);
+      PD_TRY(this->kt.begin(PDESHEP_KG_GEMM));
+      const TcShape sh{n, cplx, m0};
+      std::vector<int64_t> xo(K);
+      for (int t = 0; t < K; ++t) xo[t] = col_off[t] * n;
+      if (kind == 0)
+        PD_TRY(tc_gemm_herm<S>(p.tc, sh, active, xo, small_off, A, Bm, Cm, A == Bm, reuse_a && A != Bm, A == Bm, st));
+      else
+        PD_TRY(tc_gemm_update<S>(p.tc, sh, active, xo, small_off, A, Bm, Cm, st));
+      return this->kt.end(fl);
+    }
     std::vector<GemmItem<S>> it(na);
     for (int a = 0; a < na; ++a) {
       const int s = active[a];
@@ -814,7 +836,7 @@ struct FeastRun : Feast<S, C> {
     // breaks down get their Gram matrices in FP64 for the rest of this
     // orthonormalisation (a shift below 1e-13 would not help there).
     std::vector<int> gram64(K, 0);
-    if (this->ff()) {
+    if (this->ff() && !this->tc()) {
       std::vector<int> ill;
       for (int s : keep)
         if (info_s[s]) {
@@ -872,7 +894,7 @@ struct FeastRun : Feast<S, C> {
     active = keep;
     PD_TRY(upload_active());
     PD_TRY(band_mm((S*)p.Q, (S*)p.BQ));
-    PD_TRY(gemm(0, (S*)p.Q, (S*)p.BQ, Aq));         // Q^H B Q
+    PD_TRY(gemm(0, (S*)p.Q, (S*)p.BQ, Aq, 0, 0, 1));  // Q^H B Q (Q's digits from its last Gram matrix)
     PD_TRY(small_mm(false, Aq, I, T, 0, 1));         // (Q^H B Q) R^{-1}
     PD_TRY(small_mm(true, I, T, G, 1, 0));           // A~ = R^{-H} (Q^H B Q) R^{-1}
     PD_TRY(this->kt.begin(PDESHEP_KG_EIG));
@@ -1253,6 +1275,7 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   F.resident = all_sys <= F.p.wave_bytes;
   F.factored = false;
   cudaStream_t st = F.st;
+  if (F.tc()) PD_TRY(tc_clear_error(F.p.tc, st));
 
   cudaEvent_t e0, e1;
   PD_CK(cudaEventCreate(&e0));
@@ -1383,6 +1406,7 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
     update_active(it);
   }
   PD_TRY(read_counts());
+  if (F.tc()) PD_TRY(tc_read_error(F.p.tc, st));  // a tensor-core product whose bounded wait gave up
   if (!F.active.empty()) status = PDESHEP_NOT_CONVERGED;
   // outputs for every slice
   F.active.clear();
@@ -1450,7 +1474,8 @@ int check_slice_args(int64_t n, int32_t b, const void* d_band, int64_t ldab, int
   if (o && (!(o->tol > 0.0) || o->max_iter < 0 || (o->precision != PDESHEP_FP64 && o->precision != PDESHEP_MIXED) ||
             !(o->ellipse_ratio > 0.0) ||
             (o->rhs_chunk != 0 && o->rhs_chunk != 16 && o->rhs_chunk != 32 && o->rhs_chunk != 64) ||
-            (o->rr_arith != PDESHEP_RR_FLOATFLOAT && o->rr_arith != PDESHEP_RR_FP64) || o->autotune < 0 ||
+            (o->rr_arith != PDESHEP_RR_FLOATFLOAT && o->rr_arith != PDESHEP_RR_FP64 &&
+             o->rr_arith != PDESHEP_RR_TENSOR) || o->autotune < 0 ||
             o->autotune > 2))
     return -15;
   return 0;

@@ -1,7 +1,9 @@
 """The benchmark configurations at full size, in the launch configuration the bench uses.
 
 * Config 1 (plain FP64 FEAST, real n = 2000, b = 32, one slice of eigenvalues 500-599, Ne = 8,
-  m0 = 150, random start, tol 1e-10): element by element against the oracle's own FEAST run.
+  m0 = 150, random start, tol 1e-10): element by element against the oracle's own FEAST run, also
+  in mixed precision with float-float (arith 0) and tensor-core (arith 2) Rayleigh-Ritz products.
+  Configs 2 and 3 run with both Rayleigh-Ritz arithmetics.
 * Config 2 (complex n = 8192, b = 64, 8 slices over the lowest 20 %, m0 = 267, mixed
   precision): what the oracle can compute one by one -- the exact counts at every boundary, the
   residual of every converged pair, orthogonality, and sampled eigenvalues by bisection.
@@ -23,8 +25,8 @@ def device():
     return dev()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_config1_full_size_against_oracle(device, precision):
+@pytest.mark.parametrize("precision,arith", [(0, 0), (1, 0), (1, 2)])
+def test_config1_full_size_against_oracle(device, precision, arith):
     import paper_2012_00506_gb300 as pk
     n, b = 2000, 32
     ab = synth.random_band(n, b, synth.config_seed(1), False, off_sigma=0.1)
@@ -32,7 +34,7 @@ def test_config1_full_size_against_oracle(device, precision):
     bnorm = oracle.spectral_norm(ab)
     X0 = synth.random_subspace(n, 150, synth.config_seed(1) + 1, False)
     r = pk.band_slice(to_dev(ab, device), bounds, [150], block_to_dev(X0, device), ne=8, precision=precision,
-                      bnorm=bnorm, tol=1e-10, max_iter=40)
+                      bnorm=bnorm, tol=1e-10, max_iter=40, rr_arith=arith)
     assert r.status == 0
     assert r.counts[0] == 100 == oracle.inertia(ab, bounds[1]) - oracle.inertia(ab, bounds[0])
     assert r.nfound[0] == 100
@@ -47,7 +49,8 @@ def test_config1_full_size_against_oracle(device, precision):
     assert oracle.orth(Xg) < 1e-13
 
 
-def test_config2_full_size_properties(device):
+@pytest.mark.parametrize("arith", [0, 2])
+def test_config2_full_size_properties(device, arith):
     import paper_2012_00506_gb300 as pk
     n, b, nslice = 8192, 64, 8
     ab = synth.random_band(n, b, synth.config_seed(2), True, off_sigma=0.1)
@@ -63,7 +66,7 @@ def test_config2_full_size_properties(device):
     bnorm = oracle.spectral_norm(ab, tol=1e-10)
     X0 = synth.random_subspace(n, int(sum(m0)), synth.config_seed(2) + 999, True)
     r = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), ne=8, precision=pk.MIXED, bnorm=bnorm,
-                      tol=1e-10, max_iter=40, autotune=1)
+                      tol=1e-10, max_iter=40, autotune=1, rr_arith=arith)
     assert r.status == 0
     neg = [oracle.inertia(ab, s) for s in bounds]
     assert list(r.counts) == list(np.diff(neg))          # bit-exact counts at every boundary
@@ -87,7 +90,8 @@ def test_config2_full_size_properties(device):
         assert abs(allev[k] - 0.5 * (elo + ehi)) <= 1e-10 * bnorm
 
 
-def test_config3_uneven_slices_in_waves(device):
+@pytest.mark.parametrize("arith", [0, 2])
+def test_config3_uneven_slices_in_waves(device, arith):
     import paper_2012_00506_gb300 as pk
     n, b, nslice, ne = 32768, 128, 64, 16
     ab = synth.mixture_band(n, b, synth.config_seed(3), off_sigma=0.02)
@@ -105,7 +109,7 @@ def test_config3_uneven_slices_in_waves(device):
     bnorm = max(abs(lo2[0]), abs(hi2[0]), abs(lo2[1]), abs(hi2[1]))
     X0 = synth.random_subspace(n, int(sum(m0)), synth.config_seed(3) + 2, False)
     r = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), ne=ne, precision=pk.MIXED, bnorm=bnorm,
-                      tol=1e-10, max_iter=40, hbm_cap_bytes=100 << 30, autotune=1)
+                      tol=1e-10, max_iter=40, hbm_cap_bytes=100 << 30, autotune=1, rr_arith=arith)
     assert r.status == 0
     assert r.stats["waves"] >= 2                      # the 1024 factorizations did not fit one wave
     assert list(r.counts) == [int(c) for c in sizes]

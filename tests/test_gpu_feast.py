@@ -196,30 +196,34 @@ def test_autotuner_measures_then_reuses(device, tmp_path):
 
 
 @pytest.mark.parametrize("cplx", [False, True])
-def test_rr_fp64_and_floatfloat_agree(device, cplx):
-    """Mixed precision with the Rayleigh-Ritz products in FP64 or in float-float:
-    both give every in-slice eigenvalue within 1e-10 ||B|| of the dense spectrum
-    and agree with each other to 1e-11 ||B|| (each run stops at its own iterate
-    once the residuals pass 1e-10, so they are not expected to agree further)."""
+def test_rr_arithmetics_agree(device, cplx):
+    """Mixed precision with the Rayleigh-Ritz products in FP64, in float-float or as
+    tensor-core digit products: each gives every in-slice eigenvalue within 1e-10 ||B||
+    of the dense spectrum, residuals <= 1e-10 and orthonormal vectors, and they agree
+    with each other to 1e-11 ||B|| (each run stops at its own iterate once the
+    residuals pass 1e-10, so they are not expected to agree further)."""
     import paper_2012_00506_gb300 as pk
     ab, bounds, m0, X0 = _small_problem(device, cplx, seed=80)
     band = to_dev(ab, device)
     bn = oracle.spectral_norm(ab)
     res = {}
-    for arith in (pk.RR_FLOATFLOAT, pk.RR_FP64):
+    ariths = (pk.RR_FLOATFLOAT, pk.RR_FP64, pk.RR_TENSOR)
+    for arith in ariths:
         r = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, rr_arith=arith, max_iter=30)
         assert r.status == 0 and list(r.nfound) == list(r.counts)
         res[arith] = r
     ev = np.linalg.eigvalsh(synth.band_to_dense(ab))
     off = 0
     for i, m in enumerate(m0):
-        k = int(res[0].nfound[i])
-        a = res[0].evals.cpu().numpy()[off:off + k]
-        c = res[1].evals.cpu().numpy()[off:off + k]
+        k = int(res[pk.RR_FP64].nfound[i])
         truth = ev[(ev >= bounds[i]) & (ev < bounds[i + 1])]
-        assert np.max(np.abs(np.sort(a) - truth)) <= 1e-10 * bn
-        assert np.max(np.abs(np.sort(c) - truth)) <= 1e-10 * bn
-        assert np.max(np.abs(a - c)) <= 1e-11 * bn
+        vals = {a: res[a].evals.cpu().numpy()[off:off + k] for a in ariths}
+        for a in ariths:
+            assert np.max(np.abs(np.sort(vals[a]) - truth)) <= 1e-10 * bn
+            assert np.max(np.abs(vals[a] - vals[pk.RR_FP64])) <= 1e-11 * bn
+        X = block_from_dev(res[pk.RR_TENSOR].evecs)[:, off:off + k]
+        assert np.max(oracle.residuals(ab, vals[pk.RR_TENSOR], X, bn)) <= 1e-10
+        assert oracle.orth(X) < 1e-13
         off += m
 
 
