@@ -80,9 +80,9 @@ typedef struct {
   int32_t verbose;         /* 0 quiet */
   void* stream;            /* cudaStream_t */
   int32_t rr_arith;        /* PDESHEP_MIXED only: arithmetic of the Rayleigh-Ritz products.
-                              PDESHEP_RR_TENSOR: tall products (Gram, projection, basis update) as
-                              bf16 digit products on the tensor cores, FP64-class; band and small
-                              products float-float.  PDESHEP_RR_FLOATFLOAT (default): all products
+                              PDESHEP_RR_TENSOR (default): tall products (Gram, projection, basis
+                              update) as bf16 digit products on the tensor cores, FP64-class; band
+                              and small products float-float.  PDESHEP_RR_FLOATFLOAT: all products
                               float-float.  In both, iterations after the third run the
                               float-float products in FP64.  PDESHEP_RR_FP64: all products FP64 */
   int32_t pad0;

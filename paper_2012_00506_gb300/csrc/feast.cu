@@ -598,6 +598,7 @@ struct Feast {
       else
         tune_solve = true;
     }
+    if (tc()) return;  // the tensor-core products choose their own split
     const std::string kg = tune_key("gram", n, b, cplx, o->precision * 2 + ff(), K, max_m0);
     if (o->autotune == 1 && tune_lookup(o->tune_cache, kg, &v))
       gram_splits = v;

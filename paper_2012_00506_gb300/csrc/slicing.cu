@@ -196,7 +196,7 @@ extern "C" void pdeshep_opts_default(pdeshep_opts* o) {
   o->autotune = 0;
   o->verbose = 0;
   o->stream = nullptr;
-  o->rr_arith = PDESHEP_RR_FLOATFLOAT;
+  o->rr_arith = PDESHEP_RR_TENSOR;
   o->tune_cache = nullptr;
   o->graphs = 0;
 }

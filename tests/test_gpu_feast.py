@@ -173,20 +173,23 @@ def test_uneven_slices_against_oracle(device):
 
 
 def test_autotuner_measures_then_reuses(device, tmp_path):
+    """Float-float Rayleigh-Ritz products: the solve width and the Gram split are tuned once,
+    stored, and reused from the file by a later process."""
     import paper_2012_00506_gb300 as pk
     ab, bounds, m0, X0 = _small_problem(device, True, seed=79)
     band = to_dev(ab, device)
     bn = oracle.spectral_norm(ab)
     cache = str(tmp_path / "tune.txt")
     pk.load().pdeshep_tune_reset()
-    r1 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, autotune=2, tune_cache=cache)
+    ff = dict(rr_arith=pk.RR_FLOATFLOAT)
+    r1 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, autotune=2, tune_cache=cache, **ff)
     assert r1.status == 0 and r1.stats["tuned"] == 2
     cw, sp = r1.stats["rhs_chunk_used"], r1.stats["gram_splits_used"]
     assert cw in (16, 32, 64) and sp in (2, 4, 8)
-    r2 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, autotune=1, tune_cache=cache)
+    r2 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, autotune=1, tune_cache=cache, **ff)
     assert r2.stats["tuned"] == 0 and r2.stats["rhs_chunk_used"] == cw and r2.stats["gram_splits_used"] == sp
     pk.load().pdeshep_tune_reset()          # in-process choices gone: the file still has them
-    r3 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, autotune=1, tune_cache=cache)
+    r3 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, autotune=1, tune_cache=cache, **ff)
     assert r3.stats["tuned"] == 0 and r3.stats["rhs_chunk_used"] == cw
     lines = open(cache).read().split("\n")
     assert any(l.startswith("solve/") for l in lines) and any(l.startswith("gram/") for l in lines)
