@@ -302,6 +302,14 @@ int pdeshep_cholqr(int64_t n, int32_t is_complex, int32_t nblk, const int32_t* h
 /* per entry).  Returns PDESHEP_DEVICE_TIMEOUT (after synchronising) if a    */
 /* tensor-core kernel's bounded wait gave up.                                */
 /* ------------------------------------------------------------------------ */
+/* Y = B X for the Hermitian band (lower storage, as pdeshep_band_matmul) and X, Y n x ncols     */
+/* column-major (ld n), on the tensor cores with the same bf16 digit products: each 128-row tile */
+/* of B over its (128 + 2 b)-column window times the digit rows of X.  FP64-class accuracy (a   */
+/* few units of 2^-48 |B(i,:)| max|X(:,j)| per entry).                                          */
+size_t pdeshep_band_matmul_tc_workspace_size(int64_t n, int32_t b, int32_t is_complex, int32_t ncols);
+int pdeshep_band_matmul_tc(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                           int32_t ncols, const void* d_x, void* d_y, void* d_work, size_t work_bytes,
+                           void* stream);
 #define PDESHEP_GEMM_AHB 0
 #define PDESHEP_GEMM_GRAM 1
 #define PDESHEP_GEMM_UPDATE 2

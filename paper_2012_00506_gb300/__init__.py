@@ -52,6 +52,7 @@ EXPORTED = [
     "pdeshep_mlp_workspace_size", "pdeshep_mlp_forward", "pdeshep_mlp_grad", "pdeshep_mlp_train_step",
     "pdeshep_propose_workspace_size", "pdeshep_propose_slices", "pdeshep_tune_reset",
     "pdeshep_block_gemm_workspace_size", "pdeshep_block_gemm",
+    "pdeshep_band_matmul_tc_workspace_size", "pdeshep_band_matmul_tc",
 ]
 
 
@@ -139,6 +140,8 @@ def load(path: str = LIB_PATH):
         "pdeshep_eigh_workspace_size": (sz, [i32, P, i32]),
         "pdeshep_block_gemm_workspace_size": (sz, [i64, i32, i32, P]),
         "pdeshep_block_gemm": (C.c_int, [i32, i32, i64, i32, i32, P, P, P, P, P, sz, P]),
+        "pdeshep_band_matmul_tc_workspace_size": (sz, [i64, i32, i32, i32]),
+        "pdeshep_band_matmul_tc": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P, sz, P]),
         "pdeshep_eigh": (C.c_int, [i32, i32, P, P, P, P, P, sz, P]),
         "pdeshep_workspace_size": (sz, [i64, i32, i32, i32, P, i32, C.POINTER(Opts)]),
         "pdeshep_band_slice": (C.c_int, [i64, i32, i32, P, i64, i32, P, i32, P, P, P, P, P, sz,
@@ -331,6 +334,20 @@ def cholqr(Q, sizes, passes=2, stream=None):
         out.append(R[off: off + mt * mt].reshape(mt, mt).T)  # column-major -> (row, col)
         off += mt * mt
     return Q, out
+
+
+def band_matmul_tc(band, X, b=None, stream=None):
+    """Y = B X (X of shape (ncols, n), i.e. column-major n x ncols) on the tensor cores."""
+    torch = _torch()
+    lib = load()
+    n, b, cplx, ldab = _band_args(band, b)
+    X = X.to(band.dtype).contiguous()
+    Y = torch.empty_like(X)
+    ws = _workspace(lib.pdeshep_band_matmul_tc_workspace_size(n, b, cplx, X.shape[0]), band.device)
+    st = lib.pdeshep_band_matmul_tc(n, b, cplx, _ptr(band), ldab, X.shape[0], _ptr(X), _ptr(Y), _ptr(ws),
+                                    ws.numel(), _stream(stream))
+    _check("pdeshep_band_matmul_tc", st)
+    return Y
 
 
 def block_gemm(kind, A, sizes, B=None, arith=RR_TENSOR, stream=None):

@@ -556,8 +556,8 @@ struct Feast {
     }
     q.inertia_bytes = std::max(inertia_ws_bytes(b, cplx, K + 1), bisect_ws_bytes(b, cplx, 2, 16));
     q.inertia_ws = a.take<char>(q.inertia_bytes);
-    q.band_ff = ff() ? (void*)a.take<char>(band_split_bytes(n, b, cplx)) : nullptr;
-    if (tc()) q.tc = plan_tc_scratch(a, TcShape{n, cplx, m0});
+    q.band_ff = ff() && !tc() ? (void*)a.take<char>(band_split_bytes(n, b, cplx)) : nullptr;
+    if (tc()) q.tc = plan_tc_scratch(a, TcShape{n, cplx, m0}, b);
     q.solve_queue = a.take<char>(solve_queue_bytes(K * ne, max_m0));
     if (carve) {
       p = q;
@@ -755,6 +755,12 @@ struct FeastRun : Feast<S, C> {
     double fl = 0.0;
     for (int s : active) fl += this->cw() * (2.0 * b + 1.0) * (double)n * m0[s];
     PD_TRY(this->kt.begin(PDESHEP_KG_BANDMM));
+    if (this->tc() && this->ff()) {  // tensor-core digit products (until the FP64 switch)
+      std::vector<int64_t> xo(K);
+      for (int t = 0; t < K; ++t) xo[t] = col_off[t] * n;
+      PD_TRY(tc_band_matmul<S>(p.tc, TcShape{n, cplx, m0}, active, xo, X, Y, st));
+      return this->kt.end(fl);
+    }
     for (int s : active) {
       if (this->ff())
         PD_TRY(launch_band_matmul_ff<S>(n, b, p.band_ff, m0[s], X + col_off[s] * n, Y + col_off[s] * n, st));
@@ -1303,7 +1309,10 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   const long long inertia_launches = 2;
   if (F.ff()) {
     PD_TRY(F.kt.begin(PDESHEP_KG_BANDMM));
-    PD_TRY(launch_band_split<S>(n, b, band, ldab, F.p.band_ff, st));
+    if (F.tc())
+      PD_TRY(tc_band_split<S>(F.p.tc, n, b, band, ldab, st));
+    else
+      PD_TRY(launch_band_split<S>(n, b, band, ldab, F.p.band_ff, st));
     PD_TRY(F.kt.end(0.0));
   }
   F.counts.assign(K, 0);

@@ -304,6 +304,74 @@ __global__ void tc_split_small_kernel(const SplitInfo* info, const S* T, const i
   }
 }
 
+// Band digits.  Row i of the Hermitian band (lower storage, B(i, k) = conj(B(k, i)) above the
+// diagonal) over the window k = 128 (i / 128) - lo + w, w < W, of its 128-row tile: exponent
+// over the row's band, then the digits ([Re | Im] windows for complex, zeros off the band).
+template <typename S>
+__device__ inline S band_at(const S* ab, int64_t ldab, int b, int64_t n, int64_t i, int64_t k) {
+  if (k < 0 || k >= n || i - k > b || k - i > b) return S{};
+  return k <= i ? ab[(i - k) + k * ldab] : sc<S>::conj(ab[(k - i) + i * ldab]);
+}
+template <typename S>
+__global__ void tc_band_rowexp_kernel(int64_t n, int b, const S* ab, int64_t ldab, int* eband) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double mx = 0.0;
+  for (int64_t k = max((int64_t)0, i - b); k <= min(n - 1, i + (int64_t)b); ++k) {
+    const S v = band_at<S>(ab, ldab, b, n, i, k);
+    mx = fmax(mx, fmax(fabs(tcs<S>::re(v)), fabs(tcs<S>::im(v))));
+  }
+  eband[i] = row_exponent(mx);
+}
+template <typename S>
+__global__ void tc_band_digits_kernel(int64_t n, int b, const S* ab, int64_t ldab, const int* eband, int lo, int W,
+                                      unsigned short* dband, int64_t plane, int64_t pitch) {
+  constexpr int C = tcs<S>::C;
+  const int64_t i = blockIdx.x;
+  const int e = i < n ? eband[i] : 0;
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    S v{};
+    if (i < n) v = band_at<S>(ab, ldab, b, n, i, (i / BM) * BM - lo + w);
+    unsigned short dr[kTcDigits], di[kTcDigits];
+    digits6(tcs<S>::re(v), e, dr);
+    if (C) digits6(tcs<S>::im(v), e, di);
+    unsigned short* p = dband + i * pitch + w;
+#pragma unroll
+    for (int d = 0; d < kTcDigits; ++d) {
+      p[d * plane] = dr[d];
+      if (C) p[d * plane + W] = di[d];
+    }
+  }
+}
+// B rows of the band products: column j of X gives [Re x_j | -Im x_j] and [Im x_j | Re x_j]
+// (halves of `half` elements, zero past n), so that a.b gives Re and Im of (B X)(i, j)
+template <typename S>
+__global__ void tc_split_xcols_kernel(int64_t n, int64_t half, const SplitInfo* info, const S* X, const int* eb,
+                                      unsigned short* db, int64_t plane_b, int64_t pitch_b) {
+  constexpr int C = tcs<S>::C;
+  const SplitInfo f = info[blockIdx.z];
+  const int j = blockIdx.y;
+  if (j >= f.m) return;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= half) return;
+  S v{};
+  if (k < n) v = X[f.x_off + (int64_t)j * n + k];
+  const int e = eb[brow<C>(f.b_row0, j)];
+  unsigned short dr[kTcDigits], di[kTcDigits];
+  digits6(tcs<S>::re(v), e, dr);
+  if (C) digits6(tcs<S>::im(v), e, di);
+  unsigned short* p = db + (int64_t)brow<C>(f.b_row0, j) * pitch_b + k;
+#pragma unroll
+  for (int d = 0; d < kTcDigits; ++d) {
+    p[d * plane_b] = dr[d];
+    if (C) {
+      p[d * plane_b + half] = di[d] ^ 0x8000;
+      p[d * plane_b + 32 * pitch_b] = di[d];
+      p[d * plane_b + 32 * pitch_b + half] = dr[d];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // PTX wrappers: mbarrier, TMA, tcgen05
 // ---------------------------------------------------------------------------
@@ -432,9 +500,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_expect_tx(full0 + 8 * slot, kStage);
         const uint32_t sa = smem_u32(sm + slot * kStage);
         const int x = k0 + s * BK;
+        // band products: the B coordinate follows the tile's window (it may start below 0 or end
+        // past the data: TMA fills zeros there, and the band digits are zero outside the band)
+        const int xb = d.band ? x + it.tm * BM - d.band_lo + (x >= d.band_w ? d.band_half - d.band_w : 0) : x;
         for (int g = 0; g < kTcDigits; ++g) {
           tma_load_2d(sa + g * kATile, &tmA, x, g * plane_a + ya, full0 + 8 * slot);
-          tma_load_2d(sa + kTcDigits * kATile + g * kBTile, &tmB, x, g * plane_b + yb, full0 + 8 * slot);
+          tma_load_2d(sa + kTcDigits * kATile + g * kBTile, &tmB, xb, g * plane_b + yb, full0 + 8 * slot);
         }
         issued = s + 1;
       }
@@ -682,7 +753,12 @@ int launch_products(const TcScratch& w, const CUtensorMap& ma, const CUtensorMap
 
 }  // namespace
 
-TcScratch plan_tc_scratch(Arena& a, const TcShape& sh) {
+size_t tc_band_bytes(int64_t n, int b, int cplx) {
+  const int64_t lo = rup(b, BK), W = BM + 2 * lo;
+  return (size_t)(kTcDigits * rup(n, BM) * (cplx ? 2 : 1) * W * 2 + rup(n, BM) * 4 + 1024);
+}
+
+TcScratch plan_tc_scratch(Arena& a, const TcShape& sh, int band_b) {
   TcScratch w;
   const int K = (int)sh.m.size();
   const int64_t n = sh.n;
@@ -702,6 +778,14 @@ TcScratch plan_tc_scratch(Arena& a, const TcShape& sh) {
   w.pitch_u = ku;
   w.rows_u = (int64_t)K * rup(n, BM);
   w.pitch_b = std::max<int64_t>(w.pitch_a, ku);
+  if (band_b >= 0) {
+    w.band_lo = rup(band_b, BK);
+    w.band_w = BM + 2 * w.band_lo;
+    w.band_half = rup(n, BK);
+    w.rows_band = rup(n, BM);
+    w.pitch_band = (sh.cplx ? 2 : 1) * w.band_w;
+    w.pitch_b = std::max<int64_t>(w.pitch_b, (sh.cplx ? 2 : 1) * w.band_half);
+  }
   w.max_split = (int)std::max<int64_t>(8, cdiv((sh.cplx ? 2 : 1) * n, kMaxKSplit));
   w.max_blocks = K;
   w.max_items = std::max<int64_t>(tiles_h * w.max_split, tiles_u);
@@ -721,6 +805,10 @@ TcScratch plan_tc_scratch(Arena& a, const TcShape& sh) {
   w.list = a.take<int>((size_t)K);
   w.err = a.take<int>(1);
   w.part = a.take<char>((size_t)w.part_elems * (sh.cplx ? 16 : 8));
+  if (band_b >= 0) {
+    w.dband = a.take<unsigned short>((size_t)(kTcDigits * w.rows_band * w.pitch_band));
+    w.eband = a.take<int>((size_t)w.rows_band);
+  }
   return w;
 }
 
@@ -901,6 +989,79 @@ int tc_gemm_update(const TcScratch& w, const TcShape& sh, const std::vector<int>
   return launch_products<S>(w, ma, mb, (int)w.rows_u, (int)w.rows_b, hd, hi, w.eu, c, st);
 }
 
+template <typename S>
+int tc_band_split(const TcScratch& w, int64_t n, int b, const void* band, int64_t ldab, cudaStream_t st) {
+  if (!w.dband) {
+    set_last_error_msg("tensor-core band product: scratch planned without the band");
+    return PDESHEP_WORKSPACE_TOO_SMALL;
+  }
+  tc_band_rowexp_kernel<S><<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, b, (const S*)band, ldab, w.eband);
+  PD_CK_LAUNCH();
+  tc_band_digits_kernel<S><<<(unsigned)w.rows_band, 128, 0, st>>>(
+      n, b, (const S*)band, ldab, w.eband, (int)w.band_lo, (int)w.band_w, w.dband, w.rows_band * w.pitch_band,
+      w.pitch_band);
+  PD_CK_LAUNCH();
+  return 0;
+}
+
+template <typename S>
+int tc_band_matmul(const TcScratch& w, const TcShape& sh, const std::vector<int>& blocks,
+                   const std::vector<int64_t>& x_off, const S* X, S* Y, cudaStream_t st) {
+  constexpr int C = tcs<S>::C;
+  const int K = (int)sh.m.size();
+  const int64_t n = sh.n;
+  const int nl = (int)blocks.size();
+  if (!nl) return 0;
+  std::vector<int> b0(K);
+  for (int t = 0, rb = 0; t < K; ++t) {
+    b0[t] = rb;
+    rb += rows_b_of(C, sh.m[t]);
+  }
+  int mmax = 0;
+  for (int t : blocks) mmax = std::max(mmax, sh.m[t]);
+  const int64_t pitch = (C ? 2 : 1) * w.band_half;
+  SplitInfo* dinfo = (SplitInfo*)w.info;
+  std::vector<SplitInfo> inf(nl);
+  for (int l = 0; l < nl; ++l) {
+    const int t = blocks[l];
+    inf[l] = SplitInfo{x_off[t], sh.m[t], -1, b0[t], 0, 0};
+  }
+  PD_CK(cudaMemcpyAsync(dinfo, inf.data(), sizeof(SplitInfo) * nl, cudaMemcpyHostToDevice, st));
+  tc_colexp_kernel<S><<<dim3(mmax, nl), 256, 0, st>>>(n, dinfo, X, w.ea, w.eb);
+  PD_CK_LAUNCH();
+  tc_split_xcols_kernel<S><<<dim3((unsigned)cdiv(w.band_half, 256), mmax, nl), 256, 0, st>>>(
+      n, w.band_half, dinfo, X, w.eb, w.db, w.rows_b * pitch, pitch);
+  PD_CK_LAUNCH();
+  std::vector<TcDesc> hd(nl);
+  std::vector<TcItem> hi;
+  const int k2 = (int)((C ? 2 : 1) * w.band_w);
+  for (int l = 0; l < nl; ++l) {
+    const int t = blocks[l], m = sh.m[t];
+    TcDesc& d = hd[l];
+    d = TcDesc{};
+    d.a_row0 = 0;
+    d.b_row0 = b0[t];
+    d.m = (int)n;
+    d.ncols = m;
+    d.k2 = k2;
+    d.ksplit = k2;
+    d.nsplit = 1;
+    d.ldc = (int)n;
+    d.out_off = x_off[t];
+    d.band = 1;
+    d.band_lo = (int)w.band_lo;
+    d.band_w = (int)w.band_w;
+    d.band_half = (int)w.band_half;
+    const int tn_n = (int)(C ? cdiv(m, 32) : cdiv(m, 64));
+    for (int tn = 0; tn < tn_n; ++tn)
+      for (int tmi = 0; tmi < cdiv(n, BM); ++tmi) hi.push_back(TcItem{l, tmi, tn, 0});
+  }
+  CUtensorMap ma, mb;
+  PD_TRY(make_map(&ma, w.dband, k2, w.pitch_band, kTcDigits * w.rows_band, BM));
+  PD_TRY(make_map(&mb, w.db, pitch, pitch, kTcDigits * w.rows_b, BN));
+  return launch_products<S>(w, ma, mb, (int)w.rows_band, (int)w.rows_b, hd, hi, w.eband, Y, st);
+}
+
 int tc_read_error(const TcScratch& w, cudaStream_t st) {
   int e = 0;
   PD_CK(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -919,6 +1080,12 @@ template int tc_gemm_herm<double>(const TcScratch&, const TcShape&, const std::v
 template int tc_gemm_herm<double2>(const TcScratch&, const TcShape&, const std::vector<int>&,
                                    const std::vector<int64_t>&, const std::vector<int64_t>&, const double2*,
                                    const double2*, double2*, bool, bool, bool, cudaStream_t);
+template int tc_band_split<double>(const TcScratch&, int64_t, int, const void*, int64_t, cudaStream_t);
+template int tc_band_split<double2>(const TcScratch&, int64_t, int, const void*, int64_t, cudaStream_t);
+template int tc_band_matmul<double>(const TcScratch&, const TcShape&, const std::vector<int>&,
+                                    const std::vector<int64_t>&, const double*, double*, cudaStream_t);
+template int tc_band_matmul<double2>(const TcScratch&, const TcShape&, const std::vector<int>&,
+                                     const std::vector<int64_t>&, const double2*, double2*, cudaStream_t);
 template int tc_gemm_update<double>(const TcScratch&, const TcShape&, const std::vector<int>&,
                                     const std::vector<int64_t>&, const std::vector<int64_t>&, const double*,
                                     const double*, double*, cudaStream_t);
@@ -1000,6 +1167,43 @@ int block_gemm(int kind, int arith, int64_t n, int nblk, const int32_t* hm, cons
   return 0;
 }
 }  // namespace
+
+extern "C" size_t pdeshep_band_matmul_tc_workspace_size(int64_t n, int32_t b, int32_t is_complex, int32_t ncols) {
+  if (n <= 0 || b < 0 || ncols <= 0) return 0;
+  Arena a;
+  int32_t m = ncols;
+  plan_tc_scratch(a, TcShape{n, is_complex ? 1 : 0, std::vector<int>(1, m)}, b);
+  return a.used();
+}
+
+extern "C" int pdeshep_band_matmul_tc(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                                      int32_t ncols, const void* d_x, void* d_y, void* d_work, size_t work_bytes,
+                                      void* stream) {
+  if (n <= 0 || n > (int64_t)1 << 30) return -1;
+  if (b < 0 || b >= n) return -2;
+  if (!d_band) return -4;
+  if (ldab < b + 1) return -5;
+  if (ncols < 1 || ncols > 4096 || ncols > n) return -6;
+  if (!d_x) return -7;
+  if (!d_y) return -8;
+  if (!d_work) return -9;
+  cudaStream_t st = (cudaStream_t)stream;
+  Arena a(d_work, work_bytes);
+  const TcShape sh{n, is_complex ? 1 : 0, std::vector<int>(1, (int)ncols)};
+  TcScratch w = plan_tc_scratch(a, sh, b);
+  if (!a.fits()) return PDESHEP_WORKSPACE_TOO_SMALL;
+  PD_TRY(tc_clear_error(w, st));
+  const std::vector<int> blocks(1, 0);
+  const std::vector<int64_t> xo(1, 0);
+  if (is_complex) {
+    PD_TRY(tc_band_split<double2>(w, n, b, d_band, ldab, st));
+    PD_TRY(tc_band_matmul<double2>(w, sh, blocks, xo, (const double2*)d_x, (double2*)d_y, st));
+  } else {
+    PD_TRY(tc_band_split<double>(w, n, b, d_band, ldab, st));
+    PD_TRY(tc_band_matmul<double>(w, sh, blocks, xo, (const double*)d_x, (double*)d_y, st));
+  }
+  return tc_read_error(w, st);
+}
 
 extern "C" size_t pdeshep_block_gemm_workspace_size(int64_t n, int32_t is_complex, int32_t nblk,
                                                     const int32_t* h_m) {

@@ -48,6 +48,10 @@ struct TcDesc {
   int ldc;
   int64_t out_off; // element offset of the output block
   int64_t part_off;// element offset of split 0 in the partial buffer (nsplit > 1), layout as the output with ld m
+  // band products: A rows hold the band of 128-row tile tm over the window of W columns starting
+  // at 128 tm - band_lo ([Re | Im] windows for complex), B rows hold whole columns of X
+  // ([Re | -Im] and [Im | Re] halves of band_half elements each); 0 for the other products
+  int band, band_lo, band_w, band_half;
 };
 struct TcItem {
   int desc, tm, tn, split;
@@ -59,6 +63,8 @@ struct TcScratch {
   unsigned short* da = nullptr;  // A^H B: A digit rows (kTcDigits planes of rows_a x pitch_a bf16)
   unsigned short* du = nullptr;  // A T: A digit rows (planes of rows_u x pitch_u)
   unsigned short* db = nullptr;  // B digit rows of either product (planes of rows_b x pitch)
+  unsigned short* dband = nullptr;  // band digit rows (planes of rows_band x pitch_band), see tc_band_split
+  int* eband = nullptr;
   int* ea = nullptr;
   int* eu = nullptr;
   int* eb = nullptr;
@@ -70,6 +76,7 @@ struct TcScratch {
   int* err = nullptr;            // set by a bounded wait that gave up
   void* part = nullptr;
   int64_t rows_a = 0, rows_b = 0, rows_u = 0, pitch_a = 0, pitch_b = 0, pitch_u = 0;
+  int64_t rows_band = 0, pitch_band = 0, band_lo = 0, band_w = 0, band_half = 0;
   int64_t max_items = 0, max_blocks = 0, part_elems = 0;
   int max_split = 1;
 };
@@ -80,7 +87,7 @@ struct TcShape {
   int cplx;
   std::vector<int> m;
 };
-TcScratch plan_tc_scratch(Arena& a, const TcShape& sh);
+TcScratch plan_tc_scratch(Arena& a, const TcShape& sh, int band_b = -1);  // band_b >= 0: band products too
 
 // C_t = A_t^H B_t (m_t x m_t, ld ldc[t], at c + c_off[t]) for the listed blocks; A_t, B_t are n x m_t
 // column-major at a + x_off[t], b + x_off[t].  same_ab: B is A (the Gram matrix; one split pass).
@@ -96,6 +103,16 @@ template <typename S>
 int tc_gemm_update(const TcScratch& w, const TcShape& sh, const std::vector<int>& blocks,
                    const std::vector<int64_t>& x_off, const std::vector<int64_t>& t_off, const S* a, const S* tm,
                    S* c, cudaStream_t st);
+
+// Band products Y_t = B X_t (B Hermitian band, lower storage; X_t, Y_t n x m_t at x_off[t]):
+// tc_band_split writes the digits of B once (rows of 128-row tiles over their band window),
+// tc_band_matmul splits the columns of X and runs one tile per (128 rows, 32 or 64 columns).
+template <typename S>
+int tc_band_split(const TcScratch& w, int64_t n, int b, const void* band, int64_t ldab, cudaStream_t st);
+template <typename S>
+int tc_band_matmul(const TcScratch& w, const TcShape& sh, const std::vector<int>& blocks,
+                   const std::vector<int64_t>& x_off, const S* X, S* Y, cudaStream_t st);
+size_t tc_band_bytes(int64_t n, int b, int cplx);
 
 // PDESHEP_DEVICE_TIMEOUT if a product kernel's bounded wait gave up since the last clear (synchronises)
 int tc_read_error(const TcScratch& w, cudaStream_t st);

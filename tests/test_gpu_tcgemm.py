@@ -150,3 +150,23 @@ def test_update_with_badly_scaled_columns(pk, cplx):
     err = np.max(np.abs(X - ref) / np.outer(np.linalg.norm(U, axis=1), np.linalg.norm(W, axis=0)))
     print("update scaled", cplx, err)
     assert err < 1e-14
+
+
+@pytest.mark.parametrize("cplx,n,b,m", [(True, 8192, 64, 267), (False, 1000, 7, 37), (True, 333, 40, 5),
+                                        (False, 2000, 32, 150)])
+def test_band_product_tensor_matches_fp64(pk, cplx, n, b, m):
+    """Y = B X on the tensor cores (128-row tiles of the band over their window) against the
+    FP64 band product: every entry within 1e-13 |B(i,:)| max|X(:,j)| (the digits of a row of B
+    and of a column of X carry 2^-47 of their maxima; 2b+1 such terms add up); ragged n, b not
+    a multiple of 32, windows that start before row 0 and end past row n."""
+    import synth
+    ab = synth.random_band(n, b, 61 + n, cplx)
+    g = np.random.default_rng(62)
+    X = g.normal(size=(m, n)) + (1j * g.normal(size=(m, n)) if cplx else 0)
+    Y = pk.band_matmul_tc(_t(pk, ab), _t(pk, X)).cpu().numpy()
+    Bd = synth.band_to_dense(ab)
+    ref = X @ Bd.T                      # rows of the (m, n) layout: (B x_j)^T
+    scale = np.outer(np.max(np.abs(X), axis=1), np.linalg.norm(Bd, axis=1))
+    err = np.max(np.abs(Y - ref) / scale)
+    print("band", cplx, n, b, m, err)
+    assert err < 1e-13
