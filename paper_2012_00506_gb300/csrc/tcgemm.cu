@@ -517,18 +517,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       // MMA issue: 26 digit pairs per 16-element step.  Levels 0..4 go to the exact
       // accumulators (cleared at the start of every 128-element chunk, after the
       // accumulator warps have taken the previous chunk), levels 5..6 to the tail
-      // accumulator; a chunk's first tail products run while the previous chunk is read out.
+      // accumulator.  The tail products of the chunk's first stages (as many as are
+      // buffered) are issued before the wait for the accumulator warps, so the tensor
+      // pipe works through the read-out of the previous chunk.
       bool ok = true;
-      for (int s = 0; s < nst && ok; ++s) {
-        const int slot = s % kStages;
-        const int ch = s / kChunk;
-        const bool first = (s % kChunk) == 0;
-        if (!mbar_wait(full0 + 8 * slot, (s / kStages) & 1, err)) { ok = false; break; }
-        tc_fence_after();
-        // descriptors are linear in the address (14-bit field, shared memory < 256 KB)
-        const uint64_t da0 = sw64_desc(smem_u32(sm + slot * kStage));
+      bool tail_started = false;
+      auto tail = [&](int s) {
+        const uint64_t da0 = sw64_desc(smem_u32(sm + (s % kStages) * kStage));
         const uint64_t db0 = da0 + ((kTcDigits * kATile) >> 4);
-        bool tail_started = s > 0;
 #pragma unroll 1
         for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
@@ -542,10 +538,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-        if (first && ch > 0) {
-          if (!mbar_wait(acce, (ch - 1) & 1, err)) { ok = false; break; }
-          tc_fence_after();
-        }
+      };
+      auto exact = [&](int s, bool first) {
+        // descriptors are linear in the address (14-bit field, shared memory < 256 KB)
+        const uint64_t da0 = sw64_desc(smem_u32(sm + (s % kStages) * kStage));
+        const uint64_t db0 = da0 + ((kTcDigits * kATile) >> 4);
         uint32_t started = first ? 0u : 31u;  // bit L: exact level L already written in this chunk
 #pragma unroll 1
         for (int kk = 0; kk < BK / 16; ++kk) {
@@ -560,8 +557,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-        tc_commit(empty0 + 8 * slot);
-        if ((s % kChunk) == kChunk - 1 || s == nst - 1) tc_commit(accf);
+      };
+      for (int ch = 0; ch < nchunk && ok; ++ch) {
+        const int s0 = ch * kChunk, s1 = min(nst, s0 + kChunk);
+        const int pre = min(s1 - s0, kStages);  // stages whose tails run ahead of the read-out wait
+        for (int s = s0; s < s0 + pre; ++s) {
+          if (!mbar_wait(full0 + 8 * (s % kStages), (s / kStages) & 1, err)) { ok = false; break; }
+          tc_fence_after();
+          tail(s);
+        }
+        if (!ok) break;
+        if (ch > 0) {
+          if (!mbar_wait(acce, (ch - 1) & 1, err)) { ok = false; break; }
+          tc_fence_after();
+        }
+        for (int s = s0; s < s1; ++s) {
+          if (s >= s0 + pre) {
+            if (!mbar_wait(full0 + 8 * (s % kStages), (s / kStages) & 1, err)) { ok = false; break; }
+            tc_fence_after();
+            tail(s);
+          }
+          exact(s, s == s0);
+          tc_commit(empty0 + 8 * (s % kStages));
+        }
+        if (!ok) break;
+        tc_commit(accf);
       }
       // all MMAs complete before teardown (also on the error path)
       tc_commit(done);
