@@ -11,9 +11,10 @@ step's eigenvectors and re-sliced at gap midpoints of the previous eigenvalues
 
 One timed step = one call of pdeshep_band_slice on the next matrix of the
 sequence (inertia counts of all slices, complex64 shifted band LU and solves
-with FP64 residual refinement, CholQR2 and Rayleigh-Ritz in FP64, until every
-slice has its exact count of eigenpairs at residual <= 1e-10).  Inputs are
-resident in HBM when timing starts; the factors (about 1.2 GB) exceed L2.
+with FP64 residual refinement, CholQR2 and Rayleigh-Ritz with FP64-class
+products (tensor-core digit products for the tall and band products), until
+every slice has its exact count of eigenpairs at residual <= 1e-10).  Inputs
+are resident in HBM when timing starts; the factors (about 1.2 GB) exceed L2.
 
 Also reported: the plain FP64 path on the same steps, an end-to-end variant
 through the C ABI with host buffers, the dominant kernel group's achieved
@@ -46,9 +47,9 @@ SEED = synth.config_seed(2)
 WORKLOAD = ("SCF sequence of complex Hermitian bands n=8192 b=64 (B_k+1 = B_k + 1e-3 E_k), 8 slices "
             "over the lowest 20% (1638 eigenpairs), Ne=8, m0=max(1.3m, m+10), warm start")
 METRIC = ("eigenpairs/s at residual <= 1e-10 (mixed path: complex64 band LU/solves with FP64 residual refinement, "
-          "tall Rayleigh-Ritz products as bf16 digit products on the tensor cores (FP64-class), float-float band "
-          "and small products, FP64 inertia and eigensolver refinement; plain FP64 and mixed with float-float or "
-          "FP64 Rayleigh-Ritz products reported alongside)")
+          "tall Rayleigh-Ritz and band products as bf16 digit products on the tensor cores (FP64-class), "
+          "float-float small products, FP64 inertia and eigensolver refinement; plain FP64 and mixed with "
+          "float-float or FP64 Rayleigh-Ritz products reported alongside)")
 
 # FP64 / FP32 ALU peaks from unit counts and clocks (152 SMs at 2070 MHz): FP32 = 152 x 128
 # lanes x 2 flops x 2.07 GHz; FP64 = the part's 1.25 TFLOP/s figure.
@@ -80,7 +81,8 @@ GROUP_BOUND = {"factor": ("alu", PEAK_FP32_TFLOPS, "fp32 from unit counts and cl
                "gemm": ("tensor", PEAK_TC_TFLOPS, "bf16 tensor cores (sustained, %s) / %d digit products per "
                         "FP64-class product" % (BF16_PEAK_SOURCE, TC_DIGIT_PAIRS)),
                "small": ("alu", PEAK_FP64_TFLOPS, "fp64 (part's figure)"),
-               "bandmm": ("alu", PEAK_FF_TFLOPS, "float-float (FP32 pipe) from unit counts and clocks"),
+               "bandmm": ("tensor", PEAK_TC_TFLOPS, "bf16 tensor cores (sustained, %s) / %d digit products per "
+                          "FP64-class product" % (BF16_PEAK_SOURCE, TC_DIGIT_PAIRS)),
                "inertia": ("alu", PEAK_FP64_TFLOPS, "fp64 (part's figure)"),
                "eig": ("alu", PEAK_FP32_TFLOPS, "fp32 from unit counts and clocks")}
 
@@ -463,7 +465,7 @@ def traffic_for(group):
 
 WORKLOAD_KEY = "c2"
 GROUP_SOURCES = {"solve": "band_lu.cu", "factor": "band_lu.cu", "gemm": "tcgemm.cu", "small": "dense.cu",
-                 "bandmm": "dense.cu", "accum": "feast.cu", "inertia": "inertia.cu", "eig": "dense.cu"}
+                 "bandmm": "tcgemm.cu", "accum": "feast.cu", "inertia": "inertia.cu", "eig": "dense.cu"}
 
 
 def source_hash(group):
