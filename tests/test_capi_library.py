@@ -67,3 +67,30 @@ def test_argument_errors_without_gpu(lib):
     neg = np.zeros(1, dtype=np.int64)
     assert lib.pdeshep_inertia(-1, 2, 0, None, 3, 1, sig.ctypes.data, neg.ctypes.data, None, None, 0, None) == -1
     assert lib.pdeshep_inertia(10, 2, 0, None, 3, 1, sig.ctypes.data, neg.ctypes.data, None, None, 0, None) == -4
+
+
+def test_tensor_products_arguments_and_workspace(lib):
+    """Host-side checks of the tensor-core entry points: the default Rayleigh-Ritz arithmetic,
+    workspace sizes that grow with the problem (the digit planes of the operands and of the
+    band), and argument errors returned before any CUDA call."""
+    import paper_2012_00506_gb300 as pk
+    assert pk.default_opts().rr_arith == pk.RR_TENSOR
+    m = np.array([267, 40], dtype=np.int32)
+    ws = lambda n, c: lib.pdeshep_block_gemm_workspace_size(n, c, m.size, m.ctypes.data)
+    assert 0 < ws(1000, 0) < ws(1000, 1) < ws(8192, 1)
+    # six bf16 digit planes of the A rows (2n elements each, rows padded per block to 128) at least
+    assert ws(8192, 1) >= 6 * (256 + 128) * 2 * 8192 * 2
+    wb = lambda b: lib.pdeshep_band_matmul_tc_workspace_size(8192, b, 1, 267)
+    assert wb(0) < wb(64) < wb(128)
+    assert wb(64) - wb(0) >= 6 * 8192 * 2 * 128 * 2   # band digits widen with the window 128 + 2b
+    z = np.zeros(4)
+    p = z.ctypes.data
+    assert lib.pdeshep_block_gemm(3, 2, 100, 1, 2, m.ctypes.data, p, p, p, p, 1, None) == -1     # kind
+    assert lib.pdeshep_block_gemm(0, 3, 100, 1, 2, m.ctypes.data, p, p, p, p, 1, None) == -2     # arith
+    assert lib.pdeshep_block_gemm(0, 2, 0, 1, 2, m.ctypes.data, p, p, p, p, 1, None) == -3       # n
+    assert lib.pdeshep_block_gemm(0, 2, 100, 1, 2, m.ctypes.data, p, p, p, p, 1, None) == -6     # m > n
+    assert lib.pdeshep_block_gemm(0, 2, 1000, 1, 2, m.ctypes.data, p, None, p, p, 1, None) == -8  # B missing
+    assert lib.pdeshep_block_gemm(1, 2, 1000, 1, 2, m.ctypes.data, p, None, None, p, 1, None) == -9
+    assert lib.pdeshep_band_matmul_tc(-1, 4, 1, p, 5, 3, p, p, p, 1, None) == -1
+    assert lib.pdeshep_band_matmul_tc(100, 4, 1, p, 4, 3, p, p, p, 1, None) == -5             # ldab < b + 1
+    assert lib.pdeshep_band_matmul_tc(100, 4, 1, p, 5, 0, p, p, p, 1, None) == -6
