@@ -444,28 +444,30 @@ __device__ inline void tmem_wait16(uint32_t (&r)[16]) {
 }
 
 // ---------------------------------------------------------------------------
-// the product kernel: one 128 x 64 tile of A-rows . B-rows over one k range
+// the product kernel: persistent, one CTA per SM; CTA b takes items b, b + grid, ...
+// (each item one 128 x 64 tile of A-rows . B-rows over one k range).  The stage ring,
+// the chunk read-outs and the tail hand-over count across items, so the accumulator
+// warps store one item's tile while the tensor core runs the next item.
 // ---------------------------------------------------------------------------
 template <typename S>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const TcDesc* descs, const TcItem* items, int plane_a, int plane_b, const int* ea,
+                   const TcDesc* descs, const TcItem* items, int nitems, int plane_a, int plane_b, const int* ea,
                    const int* eb, S* out, S* part, int* err) {
   constexpr int C = tcs<S>::C;
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(sm + kStages * kStage);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages), accf = smem_u32(bars + 2 * kStages),
-                 acce = smem_u32(bars + 2 * kStages + 1), done = smem_u32(bars + 2 * kStages + 2);
-  uint32_t* tslot = (uint32_t*)(bars + 2 * kStages + 3);
-
-  const TcItem it = items[blockIdx.x];
-  const TcDesc d = descs[it.desc];
-  const int k0 = it.split * d.ksplit;
-  const int k1 = min(d.k2, k0 + d.ksplit);
-  const int nst = (int)cdiv(k1 - k0, BK);
-  const int nchunk = (int)cdiv(nst, kChunk);
+                 acce = smem_u32(bars + 2 * kStages + 1), done = smem_u32(bars + 2 * kStages + 2),
+                 tfree = smem_u32(bars + 2 * kStages + 3);
+  uint32_t* tslot = (uint32_t*)(bars + 2 * kStages + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto stages_of = [&](const TcItem& it, const TcDesc& d, int& k0) {
+    k0 = it.split * d.ksplit;
+    const int k1 = min(d.k2, k0 + d.ksplit);
+    return (int)cdiv(k1 - k0, BK);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -475,6 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(accf, 1);
     mbar_init(acce, 8);
     mbar_init(done, 1);
+    mbar_init(tfree, 8);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -492,38 +495,46 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       // producer: all six digit tiles of A and of B for each stage of 32 reduction elements
-      const int ya = d.a_row0 + it.tm * BM, yb = d.b_row0 + it.tn * BN;
-      int issued = 0;
-      for (int s = 0; s < nst; ++s) {
-        const int slot = s % kStages;
-        if (!mbar_wait(empty0 + 8 * slot, ((s / kStages) & 1) ^ 1, err)) break;
-        mbar_expect_tx(full0 + 8 * slot, kStage);
-        const uint32_t sa = smem_u32(sm + slot * kStage);
-        const int x = k0 + s * BK;
-        // band products: the B coordinate follows the tile's window (it may start below 0 or end
-        // past the data: TMA fills zeros there, and the band digits are zero outside the band)
-        const int xb = d.band ? x + it.tm * BM - d.band_lo + (x >= d.band_w ? d.band_half - d.band_w : 0) : x;
-        for (int g = 0; g < kTcDigits; ++g) {
-          tma_load_2d(sa + g * kATile, &tmA, x, g * plane_a + ya, full0 + 8 * slot);
-          tma_load_2d(sa + kTcDigits * kATile + g * kBTile, &tmB, xb, g * plane_b + yb, full0 + 8 * slot);
+      int gs = 0;  // stages issued so far (all items)
+      bool ok = true;
+      for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        const TcItem it = items[item];
+        const TcDesc d = descs[it.desc];
+        int k0;
+        const int nst = stages_of(it, d, k0);
+        const int ya = d.a_row0 + it.tm * BM, yb = d.b_row0 + it.tn * BN;
+        for (int s = 0; s < nst; ++s) {
+          const int G = gs, slot = G % kStages;
+          if (!mbar_wait(empty0 + 8 * slot, ((G / kStages) & 1) ^ 1, err)) { ok = false; break; }
+          mbar_expect_tx(full0 + 8 * slot, kStage);
+          const uint32_t sa = smem_u32(sm + slot * kStage);
+          const int x = k0 + s * BK;
+          // band products: the B coordinate follows the tile's window (it may start below 0 or end
+          // past the data: TMA fills zeros there, and the band digits are zero outside the band)
+          const int xb = d.band ? x + it.tm * BM - d.band_lo + (x >= d.band_w ? d.band_half - d.band_w : 0) : x;
+          for (int g = 0; g < kTcDigits; ++g) {
+            tma_load_2d(sa + g * kATile, &tmA, x, g * plane_a + ya, full0 + 8 * slot);
+            tma_load_2d(sa + kTcDigits * kATile + g * kBTile, &tmB, xb, g * plane_b + yb, full0 + 8 * slot);
+          }
+          ++gs;
         }
-        issued = s + 1;
       }
       // every issued copy has landed before the CTA may exit
-      for (int s = max(0, issued - kStages); s < issued; ++s) mbar_wait(full0 + 8 * (s % kStages), (s / kStages) & 1, err);
+      for (int G = max(0, gs - kStages); G < gs; ++G) mbar_wait(full0 + 8 * (G % kStages), (G / kStages) & 1, err);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issue: 26 digit pairs per 16-element step.  Levels 0..4 go to the exact
       // accumulators (cleared at the start of every 128-element chunk, after the
       // accumulator warps have taken the previous chunk), levels 5..6 to the tail
-      // accumulator.  The tail products of the chunk's first stages (as many as are
-      // buffered) are issued before the wait for the accumulator warps, so the tensor
-      // pipe works through the read-out of the previous chunk.
+      // accumulator (cleared at the start of every item, after the accumulator warps
+      // have taken the previous item's tail).  The tail products of the chunk's first
+      // stages (as many as are buffered) are issued before the wait for the accumulator
+      // warps, so the tensor pipe works through the read-out of the previous chunk.
       bool ok = true;
       bool tail_started = false;
-      auto tail = [&](int s) {
-        const uint64_t da0 = sw64_desc(smem_u32(sm + (s % kStages) * kStage));
+      auto tail = [&](int G) {
+        const uint64_t da0 = sw64_desc(smem_u32(sm + (G % kStages) * kStage));
         const uint64_t db0 = da0 + ((kTcDigits * kATile) >> 4);
 #pragma unroll 1
         for (int kk = 0; kk < BK / 16; ++kk) {
@@ -539,9 +550,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       };
-      auto exact = [&](int s, bool first) {
+      auto exact = [&](int G, bool first) {
         // descriptors are linear in the address (14-bit field, shared memory < 256 KB)
-        const uint64_t da0 = sw64_desc(smem_u32(sm + (s % kStages) * kStage));
+        const uint64_t da0 = sw64_desc(smem_u32(sm + (G % kStages) * kStage));
         const uint64_t db0 = da0 + ((kTcDigits * kATile) >> 4);
         uint32_t started = first ? 0u : 31u;  // bit L: exact level L already written in this chunk
 #pragma unroll 1
@@ -558,30 +569,46 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       };
-      for (int ch = 0; ch < nchunk && ok; ++ch) {
-        const int s0 = ch * kChunk, s1 = min(nst, s0 + kChunk);
-        const int pre = min(s1 - s0, kStages);  // stages whose tails run ahead of the read-out wait
-        for (int s = s0; s < s0 + pre; ++s) {
-          if (!mbar_wait(full0 + 8 * (s % kStages), (s / kStages) & 1, err)) { ok = false; break; }
-          tc_fence_after();
-          tail(s);
-        }
-        if (!ok) break;
-        if (ch > 0) {
-          if (!mbar_wait(acce, (ch - 1) & 1, err)) { ok = false; break; }
+      int gs = 0, gc = 0, ni = 0;  // stages, chunks and items consumed so far
+      for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++ni) {
+        const TcItem it = items[item];
+        const TcDesc d = descs[it.desc];
+        int k0;
+        const int nst = stages_of(it, d, k0);
+        const int nchunk = (int)cdiv(nst, kChunk);
+        if (ni > 0) {
+          if (!mbar_wait(tfree, (ni - 1) & 1, err)) { ok = false; break; }
           tc_fence_after();
         }
-        for (int s = s0; s < s1; ++s) {
-          if (s >= s0 + pre) {
-            if (!mbar_wait(full0 + 8 * (s % kStages), (s / kStages) & 1, err)) { ok = false; break; }
+        tail_started = false;
+        for (int ch = 0; ch < nchunk && ok; ++ch, ++gc) {
+          const int s0 = ch * kChunk, s1 = min(nst, s0 + kChunk);
+          const int pre = min(s1 - s0, kStages);  // stages whose tails run ahead of the read-out wait
+          for (int s = s0; s < s0 + pre; ++s) {
+            const int G = gs + s;
+            if (!mbar_wait(full0 + 8 * (G % kStages), (G / kStages) & 1, err)) { ok = false; break; }
             tc_fence_after();
-            tail(s);
+            tail(G);
           }
-          exact(s, s == s0);
-          tc_commit(empty0 + 8 * (s % kStages));
+          if (!ok) break;
+          if (gc > 0) {
+            if (!mbar_wait(acce, (gc - 1) & 1, err)) { ok = false; break; }
+            tc_fence_after();
+          }
+          for (int s = s0; s < s1; ++s) {
+            const int G = gs + s;
+            if (s >= s0 + pre) {
+              if (!mbar_wait(full0 + 8 * (G % kStages), (G / kStages) & 1, err)) { ok = false; break; }
+              tc_fence_after();
+              tail(G);
+            }
+            exact(G, s == s0);
+            tc_commit(empty0 + 8 * (G % kStages));
+          }
+          if (!ok) break;
+          tc_commit(accf);
         }
-        if (!ok) break;
-        tc_commit(accf);
+        gs += nst;
       }
       // all MMAs complete before teardown (also on the error path)
       tc_commit(done);
@@ -592,58 +619,70 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int p = warp & 3, h = (warp - 2) >> 2;
     const uint32_t lanebase = tbase + ((uint32_t)(32 * p) << 16);
     const int cA = C ? 16 * h : 32 * h, cB = C ? 32 + 16 * h : 32 * h + 16;
-    // exact levels 0..4 of each entry as one integer in units of 2^-32 (|T| < 2^60 for 16384 elements)
-    long long T[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) T[q] = 0;
     bool ok = true;
-    for (int ch = 0; ch < nchunk; ++ch) {
-      if (!mbar_wait(accf, ch & 1, err)) { ok = false; break; }
-      tc_fence_after();
-      // level L holds integer multiples of 2^(-8L), below 2^24 of them: exact in FP32 and in int32
+    int gc = 0;  // chunks read so far (all items)
+    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+      const TcItem it = items[item];
+      const TcDesc d = descs[it.desc];
+      int k0;
+      const int nst = stages_of(it, d, k0);
+      const int nchunk = (int)cdiv(nst, kChunk);
+      // exact levels 0..4 of each entry as one integer in units of 2^-32 (|T| < 2^60 for 16384 elements)
+      long long T[32];
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const uint32_t cc = half ? cB : cA;
-        {
-          uint32_t r0[16], r1[16], r2[16];
-          tmem_ld16(lanebase + 0 * BN + cc, r0);
-          tmem_ld16(lanebase + 1 * BN + cc, r1);
-          tmem_ld16(lanebase + 2 * BN + cc, r2);
-          tmem_wait16(r0);
-          tmem_wait16(r1);
-          tmem_wait16(r2);
+      for (int q = 0; q < 32; ++q) T[q] = 0;
+      for (int ch = 0; ch < nchunk; ++ch, ++gc) {
+        if (!mbar_wait(accf, gc & 1, err)) { ok = false; break; }
+        tc_fence_after();
+        // level L holds integer multiples of 2^(-8L), below 2^24 of them: exact in FP32 and in int32
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const long long i0 = __float2int_rn(__uint_as_float(r0[q]));
-            const long long i1 = __float2int_rn(__uint_as_float(r1[q]) * 256.0f);
-            const long long i2 = __float2int_rn(__uint_as_float(r2[q]) * 65536.0f);
-            T[16 * half + q] += (i0 << 32) + (i1 << 24) + (i2 << 16);
+        for (int half = 0; half < 2; ++half) {
+          const uint32_t cc = half ? cB : cA;
+          {
+            uint32_t r0[16], r1[16], r2[16];
+            tmem_ld16(lanebase + 0 * BN + cc, r0);
+            tmem_ld16(lanebase + 1 * BN + cc, r1);
+            tmem_ld16(lanebase + 2 * BN + cc, r2);
+            tmem_wait16(r0);
+            tmem_wait16(r1);
+            tmem_wait16(r2);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const long long i0 = __float2int_rn(__uint_as_float(r0[q]));
+              const long long i1 = __float2int_rn(__uint_as_float(r1[q]) * 256.0f);
+              const long long i2 = __float2int_rn(__uint_as_float(r2[q]) * 65536.0f);
+              T[16 * half + q] += (i0 << 32) + (i1 << 24) + (i2 << 16);
+            }
+          }
+          {
+            uint32_t r3[16], r4[16];
+            tmem_ld16(lanebase + 3 * BN + cc, r3);
+            tmem_ld16(lanebase + 4 * BN + cc, r4);
+            tmem_wait16(r3);
+            tmem_wait16(r4);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const long long i3 = __float2int_rn(__uint_as_float(r3[q]) * 16777216.0f);
+              const long long i4 = __float2int_rn(__uint_as_float(r4[q]) * 4294967296.0f);
+              T[16 * half + q] += (i3 << 8) + i4;
+            }
           }
         }
-        {
-          uint32_t r3[16], r4[16];
-          tmem_ld16(lanebase + 3 * BN + cc, r3);
-          tmem_ld16(lanebase + 4 * BN + cc, r4);
-          tmem_wait16(r3);
-          tmem_wait16(r4);
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const long long i3 = __float2int_rn(__uint_as_float(r3[q]) * 16777216.0f);
-            const long long i4 = __float2int_rn(__uint_as_float(r4[q]) * 4294967296.0f);
-            T[16 * half + q] += (i3 << 8) + i4;
-          }
-        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acce);
-    }
-    if (ok) {
+      if (!ok) break;
+      // the tail of this item (complete: the last read-out waited for all of its MMAs), then
+      // hand the tail accumulator back before the epilogue
       uint32_t ta[16], tb[16];
       tmem_ld16(lanebase + kExact * BN + cA, ta);
       tmem_ld16(lanebase + kExact * BN + cB, tb);
       tmem_wait16(ta);
       tmem_wait16(tb);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tfree);
       const int i = it.tm * BM + 32 * p + lane;
       if (i < d.m) {
         const int er = ea[d.a_row0 + i] - 14;
@@ -765,8 +804,16 @@ int launch_products(const TcScratch& w, const CUtensorMap& ma, const CUtensorMap
   PD_CK(cudaMemcpyAsync(w.desc, hd.data(), sizeof(TcDesc) * hd.size(), cudaMemcpyHostToDevice, st));
   PD_CK(cudaMemcpyAsync(w.items, hi.data(), sizeof(TcItem) * hi.size(), cudaMemcpyHostToDevice, st));
   PD_CK(cudaFuncSetAttribute(tc_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
-  tc_gemm_kernel<S><<<(unsigned)hi.size(), kThreads, kSmem, st>>>(ma, mb, w.desc, w.items, plane_a, plane_b, ea,
-                                                                   w.eb, out, (S*)w.part, w.err);
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    PD_CK(cudaGetDevice(&dev));
+    PD_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int nitems = (int)hi.size();
+  const int grid = std::min(nitems, std::max(1, nsm));  // one CTA per SM (222 KB shared memory each)
+  tc_gemm_kernel<S><<<(unsigned)grid, kThreads, kSmem, st>>>(ma, mb, w.desc, w.items, nitems, plane_a, plane_b, ea,
+                                                            w.eb, out, (S*)w.part, w.err);
   PD_CK_LAUNCH();
   return 0;
 }
