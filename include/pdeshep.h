@@ -287,6 +287,47 @@ int pdeshep_cholqr(int64_t n, int32_t is_complex, int32_t nblk, const int32_t* h
                    int32_t passes, void* d_r, void* d_work, size_t work_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Re-slicing from the previous step's eigenvalues (Section 3.1).  Host only  */
+/* (no GPU work): h_d[n] ascending (the previous eigenvalues), b0 <= h_d[0],  */
+/* h_d[n-1] < bK.  Groups are taken by value, G_i = [b_{i-1}, b_i).           */
+/*   PDESHEP_PART_KMEANS       the simplified 1-D k-means of Algorithm 3:     */
+/*                             from equal counts, each inner boundary moves   */
+/*                             to the gap after the midpoint of its groups'   */
+/*                             centroids (mean of a group's extreme points)   */
+/*                             until none moves (at most max_sweeps sweeps);  */
+/*                             empty groups are merged away (K may shrink)    */
+/*   PDESHEP_PART_EQUAL_COUNT  "Approach-1": equal counts (the first n mod K  */
+/*                             groups one more), boundaries at gap midpoints  */
+/*   PDESHEP_PART_EQUAL_WIDTH  "Approach-2": K equal pieces of [b0, bK]       */
+/* Out: h_bounds[K_out + 1], h_counts[K_out] (capacities K + 1 and K),        */
+/* *h_k_out = K_out <= K, *h_sweeps (optional) = k-means sweeps.              */
+/* ------------------------------------------------------------------------ */
+#define PDESHEP_PART_KMEANS 0
+#define PDESHEP_PART_EQUAL_COUNT 1
+#define PDESHEP_PART_EQUAL_WIDTH 2
+int pdeshep_partition(int32_t method, int64_t n, const double* h_d, int32_t K, double b0, double bK,
+                      int32_t max_sweeps, double* h_bounds, int32_t* h_counts, int32_t* h_k_out,
+                      int32_t* h_sweeps);
+
+/* ------------------------------------------------------------------------ */
+/* Outer bounds of the wanted eigenvalues i0 .. i0+nev-1 of the band from the */
+/* previous matrix's eigenvalues h_prev[nprev] (ascending) (Section 3.2,      */
+/* Algorithm 4 and the lower-bound search described beside it): bK starts at  */
+/* d = h_prev[i0+nev-1] plus step = max(|alpha d|, m_hat (d - h_prev[i0+nev-2]))*/
+/* and grows by step until the inertia count below it is >= i0 + nev; b0     */
+/* starts at h_prev[i0] minus max(|alpha d'|, m_hat (h_prev[i0+1] - d')) and  */
+/* shrinks until the count below it is <= i0 (a zero step becomes 2^-40 of   */
+/* the value).  At most max_it counts each; h_iters[2] (optional) = the       */
+/* counts taken for b0 and bK.  Synchronous.  Workspace:                      */
+/* pdeshep_outer_bounds_workspace_size(n, b, is_complex).                     */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_outer_bounds_workspace_size(int64_t n, int32_t b, int32_t is_complex);
+int pdeshep_outer_bounds(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                         int64_t nprev, const double* h_prev, int64_t i0, int64_t nev, double alpha,
+                         double m_hat, int32_t max_it, double* h_b0, double* h_bK, int32_t* h_iters,
+                         void* d_work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Tall block products of the Rayleigh-Ritz step (Section 2.2: the Gram      */
 /* matrix Q^H Q of the orthonormalisation, the projection Q^H (B Q) and the  */
 /* basis update Q W) on a batch of column blocks of n rows.  Block t of d_a   */

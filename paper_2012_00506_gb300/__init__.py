@@ -30,6 +30,9 @@ RR_TENSOR = 2
 GEMM_AHB = 0
 GEMM_GRAM = 1
 GEMM_UPDATE = 2
+PART_KMEANS = 0
+PART_EQUAL_COUNT = 1
+PART_EQUAL_WIDTH = 2
 REFINE_NONE = 0
 REFINE_RESIDUAL = 1
 
@@ -53,6 +56,7 @@ EXPORTED = [
     "pdeshep_propose_workspace_size", "pdeshep_propose_slices", "pdeshep_tune_reset",
     "pdeshep_block_gemm_workspace_size", "pdeshep_block_gemm",
     "pdeshep_band_matmul_tc_workspace_size", "pdeshep_band_matmul_tc",
+    "pdeshep_partition", "pdeshep_outer_bounds_workspace_size", "pdeshep_outer_bounds",
 ]
 
 
@@ -142,6 +146,10 @@ def load(path: str = LIB_PATH):
         "pdeshep_block_gemm": (C.c_int, [i32, i32, i64, i32, i32, P, P, P, P, P, sz, P]),
         "pdeshep_band_matmul_tc_workspace_size": (sz, [i64, i32, i32, i32]),
         "pdeshep_band_matmul_tc": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P, sz, P]),
+        "pdeshep_partition": (C.c_int, [i32, i64, P, i32, dbl, dbl, i32, P, P, P, P]),
+        "pdeshep_outer_bounds_workspace_size": (sz, [i64, i32, i32]),
+        "pdeshep_outer_bounds": (C.c_int, [i64, i32, i32, P, i64, i64, P, i64, i64, dbl, dbl, i32, P, P, P, P, sz,
+                                           P]),
         "pdeshep_eigh": (C.c_int, [i32, i32, P, P, P, P, P, sz, P]),
         "pdeshep_workspace_size": (sz, [i64, i32, i32, i32, P, i32, C.POINTER(Opts)]),
         "pdeshep_band_slice": (C.c_int, [i64, i32, i32, P, i64, i32, P, i32, P, P, P, P, P, sz,
@@ -334,6 +342,39 @@ def cholqr(Q, sizes, passes=2, stream=None):
         out.append(R[off: off + mt * mt].reshape(mt, mt).T)  # column-major -> (row, col)
         off += mt * mt
     return Q, out
+
+
+def partition(evals, K, b0, bK, method=PART_KMEANS, max_sweeps=1000):
+    """Slices for the next matrix of a sequence from the previous eigenvalues (host only):
+    returns (bounds, counts, sweeps); see ``pdeshep_partition``."""
+    lib = load()
+    d = np.ascontiguousarray(np.sort(np.asarray(evals, dtype=np.float64)))
+    bounds = np.zeros(int(K) + 1)
+    counts = np.zeros(int(K), dtype=np.int32)
+    kout = C.c_int32()
+    sweeps = C.c_int32()
+    st = lib.pdeshep_partition(int(method), d.size, _np_ptr(d), int(K), float(b0), float(bK), int(max_sweeps),
+                               _np_ptr(bounds), _np_ptr(counts), C.byref(kout), C.byref(sweeps))
+    _check("pdeshep_partition", st)
+    k = kout.value
+    return bounds[: k + 1].copy(), counts[:k].copy(), int(sweeps.value)
+
+
+def outer_bounds(band, prev, i0, nev, alpha=1e-3, m_hat=6.0, max_it=64, b=None, stream=None):
+    """(b0, bK, (counts taken for b0, for bK)) enclosing the wanted eigenvalues i0..i0+nev-1
+    of the band, searched from the previous eigenvalues ``prev`` (Algorithm 4)."""
+    lib = load()
+    n, b, cplx, ldab = _band_args(band, b)
+    d = np.ascontiguousarray(np.sort(np.asarray(prev, dtype=np.float64)))
+    b0 = C.c_double()
+    bK = C.c_double()
+    iters = np.zeros(2, dtype=np.int32)
+    ws = _workspace(lib.pdeshep_outer_bounds_workspace_size(n, b, cplx), band.device)
+    st = lib.pdeshep_outer_bounds(n, b, cplx, _ptr(band), ldab, d.size, _np_ptr(d), int(i0), int(nev), float(alpha),
+                                  float(m_hat), int(max_it), C.byref(b0), C.byref(bK), _np_ptr(iters), _ptr(ws),
+                                  ws.numel(), _stream(stream))
+    _check("pdeshep_outer_bounds", st)
+    return b0.value, bK.value, (int(iters[0]), int(iters[1]))
 
 
 def band_matmul_tc(band, X, b=None, stream=None):

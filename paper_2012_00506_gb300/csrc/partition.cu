@@ -1,0 +1,187 @@
+// partition.cu -- re-slicing the spectrum from the eigenvalues of the previous
+// matrix of a sequence (Section 3.1 of arXiv 2012.00506), and the outer bounds
+// of the wanted part of the spectrum (Section 3.2, Algorithm 4).
+//
+// The partitions are host work: one pass (or a few sweeps) over the sorted
+// eigenvalues of the previous step, microseconds for the tens of thousands of
+// values a call handles, while the counts that validate them come from the
+// inertia kernel.  Groups are defined by value, G_i = {d : b_{i-1} <= d < b_i},
+// so a group and the slice [b_{i-1}, b_i) of pdeshep_band_slice count the same
+// eigenvalues and ties never straddle a boundary.
+//
+//  * equal counts ("Approach-1"): K groups of floor(n/K) or floor(n/K)+1 points
+//    (the first n mod K groups hold the extra point), boundaries at the midpoints
+//    of the gaps between consecutive groups;
+//  * equal widths ("Approach-2"): [b0, bK] cut into K equal pieces;
+//  * simplified one-dimensional k-means (Algorithm 3): from the equal-count
+//    start, every inner boundary in turn moves to the midpoint of the gap that
+//    follows the midpoint of its two groups' centroids (a group's centroid is the
+//    mean of its extreme points); the sweeps repeat until no boundary moves, and
+//    groups that become empty are merged away, so K may shrink.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pdeshep {
+namespace {
+
+// first index with d[k] >= x / d[k] > x
+int64_t lower_idx(const double* d, int64_t n, double x) { return std::lower_bound(d, d + n, x) - d; }
+int64_t upper_idx(const double* d, int64_t n, double x) { return std::upper_bound(d, d + n, x) - d; }
+
+void dedup(std::vector<double>& b) {
+  std::vector<double> out;
+  out.reserve(b.size());
+  for (double v : b)
+    if (out.empty() || v != out.back()) out.push_back(v);
+  b.swap(out);
+}
+
+std::vector<double> equal_counts(const double* d, int64_t n, int K, double b0, double bK) {
+  const int64_t q = n / K, r = n % K;
+  std::vector<double> b(1, b0);
+  int64_t end = 0;
+  for (int i = 1; i < K; ++i) {
+    end += q + (i <= r ? 1 : 0);
+    if (end <= 0)
+      b.push_back(b0);
+    else if (end >= n)
+      b.push_back(bK);
+    else
+      b.push_back(0.5 * (d[end - 1] + d[end]));
+  }
+  b.push_back(bK);
+  dedup(b);
+  return b;
+}
+
+std::vector<double> equal_widths(int K, double b0, double bK) {
+  std::vector<double> b;
+  for (int i = 0; i < K; ++i) b.push_back(b0 + (bK - b0) * (double)i / (double)K);
+  b.push_back(bK);
+  dedup(b);
+  return b;
+}
+
+int kmeans(const double* d, int64_t n, int K, double b0, double bK, int max_sweeps, std::vector<double>& b) {
+  b = equal_counts(d, n, K, b0, bK);
+  int sweeps = 0;
+  while (sweeps < max_sweeps) {
+    ++sweeps;
+    const std::vector<double> old = b;
+    for (size_t i = 1; i + 1 < b.size(); ++i) {
+      const int64_t l0 = lower_idx(d, n, b[i - 1]), l1 = lower_idx(d, n, b[i]), l2 = lower_idx(d, n, b[i + 1]);
+      if (l1 <= l0 || l2 <= l1) continue;  // an empty neighbour: merged away below
+      const double c_left = 0.5 * (d[l0] + d[l1 - 1]);
+      const double c_right = 0.5 * (d[l1] + d[l2 - 1]);
+      const double t = 0.5 * (c_left + c_right);
+      const int64_t ell = upper_idx(d, n, t);  // d[ell-1] <= t < d[ell]; c_left < t < c_right keeps 1 <= ell < n
+      b[i] = 0.5 * (d[ell] + d[ell - 1]);
+    }
+    dedup(b);
+    if (b == old) break;
+  }
+  return sweeps;
+}
+
+}  // namespace
+}  // namespace pdeshep
+
+using namespace pdeshep;
+
+extern "C" int pdeshep_partition(int32_t method, int64_t n, const double* h_d, int32_t K, double b0, double bK,
+                                 int32_t max_sweeps, double* h_bounds, int32_t* h_counts, int32_t* h_k_out,
+                                 int32_t* h_sweeps) {
+  if (method < PDESHEP_PART_KMEANS || method > PDESHEP_PART_EQUAL_WIDTH) return -1;
+  if (n < 1) return -2;
+  if (!h_d) return -3;
+  for (int64_t k = 1; k < n; ++k)
+    if (!(h_d[k - 1] <= h_d[k])) return -3;  // ascending, no NaN
+  if (K < 1) return -4;
+  if (!(b0 <= h_d[0])) return -5;
+  if (!(h_d[n - 1] < bK)) return -6;
+  if (method == PDESHEP_PART_KMEANS && max_sweeps < 1) return -7;
+  if (!h_bounds) return -8;
+  if (!h_counts) return -9;
+  if (!h_k_out) return -10;
+  std::vector<double> b;
+  int sweeps = 0;
+  if (method == PDESHEP_PART_KMEANS)
+    sweeps = kmeans(h_d, n, K, b0, bK, max_sweeps, b);
+  else if (method == PDESHEP_PART_EQUAL_COUNT)
+    b = equal_counts(h_d, n, K, b0, bK);
+  else
+    b = equal_widths(K, b0, bK);
+  const int kout = (int)b.size() - 1;
+  for (int i = 0; i <= kout; ++i) h_bounds[i] = b[i];
+  for (int i = 0; i < kout; ++i)
+    h_counts[i] = (int32_t)(lower_idx(h_d, n, b[i + 1]) - lower_idx(h_d, n, b[i]));
+  *h_k_out = kout;
+  if (h_sweeps) *h_sweeps = sweeps;
+  return 0;
+}
+
+extern "C" size_t pdeshep_outer_bounds_workspace_size(int64_t n, int32_t b, int32_t is_complex) {
+  return pdeshep_inertia_workspace_size(n, b, is_complex, 1);
+}
+
+extern "C" int pdeshep_outer_bounds(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                                    int64_t nprev, const double* h_prev, int64_t i0, int64_t nev, double alpha,
+                                    double m_hat, int32_t max_it, double* h_b0, double* h_bK, int32_t* h_iters,
+                                    void* d_work, size_t work_bytes, void* stream) {
+  if (n <= 0) return -1;
+  if (b < 0 || b >= n) return -2;
+  if (!d_band) return -4;
+  if (ldab < b + 1) return -5;
+  if (!h_prev) return -7;
+  if (nprev < 1) return -6;
+  for (int64_t k = 1; k < nprev; ++k)
+    if (!(h_prev[k - 1] <= h_prev[k])) return -7;
+  if (i0 < 0 || i0 >= nprev) return -8;
+  if (nev < 1 || i0 + nev > nprev || i0 + nev > n) return -9;
+  if (!(m_hat >= 0.0) || !std::isfinite(alpha)) return -11;
+  if (max_it < 1) return -12;
+  if (!h_b0 || !h_bK) return -13;
+  if (!d_work) return -16;
+  auto count_below = [&](double sigma, int64_t* neg) -> int {
+    return pdeshep_inertia(n, b, is_complex, d_band, ldab, 1, &sigma, neg, nullptr, d_work, work_bytes, stream);
+  };
+  // upper bound (Algorithm 4): stop once every wanted eigenvalue lies below it
+  const double du = h_prev[i0 + nev - 1];
+  const double delta = nev >= 2 ? du - h_prev[i0 + nev - 2] : 0.0;
+  double step = std::max(fabs(alpha * du), m_hat * delta);
+  if (!(step > 0.0)) step = ldexp(1.0, -40) * std::max(1.0, fabs(du));
+  double bK = du + step;
+  int it_hi = 1;
+  for (;;) {
+    int64_t neg = 0;
+    PD_TRY(count_below(bK, &neg));
+    if (neg >= i0 + nev || it_hi >= max_it) break;
+    bK = bK + step;
+    ++it_hi;
+  }
+  // lower bound: stop once no wanted eigenvalue lies below it
+  const double dl = h_prev[i0];
+  const double delta2 = i0 + 1 < nprev ? h_prev[i0 + 1] - dl : 0.0;
+  double step2 = std::max(fabs(alpha * dl), m_hat * delta2);
+  if (!(step2 > 0.0)) step2 = ldexp(1.0, -40) * std::max(1.0, fabs(dl));
+  double b0 = dl - step2;
+  int it_lo = 1;
+  for (;;) {
+    int64_t neg = 0;
+    PD_TRY(count_below(b0, &neg));
+    if (neg <= i0 || it_lo >= max_it) break;
+    b0 = b0 - step2;
+    ++it_lo;
+  }
+  *h_b0 = b0;
+  *h_bK = bK;
+  if (h_iters) {
+    h_iters[0] = it_lo;
+    h_iters[1] = it_hi;
+  }
+  return 0;
+}

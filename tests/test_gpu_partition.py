@@ -1,0 +1,51 @@
+"""Outer bounds of the wanted eigenvalues (Section 3.2, Algorithm 4) on the GPU's inertia
+counts against the oracle's search on its own inertia: identical bounds and step counts (the
+host arithmetic is the same and the counts are bit-identical), and the enclosure checked
+against a closed-form spectrum."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import dev, to_dev
+from oracle import partition_oracle as po
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def device():
+    return dev()
+
+
+@pytest.mark.parametrize("i0,nev,shift", [(0, 40, 0.05), (0, 25, -0.02), (30, 50, 0.01)])
+def test_outer_bounds_laplacian(device, i0, nev, shift):
+    import paper_2012_00506_gb300 as pk
+    m, k = 13, 11
+    ab = synth.laplacian_2d_band(m, k)
+    i = np.arange(1, m + 1)[:, None]
+    j = np.arange(1, k + 1)[None, :]
+    ev = np.sort((4 - 2 * np.cos(i * np.pi / (m + 1)) - 2 * np.cos(j * np.pi / (k + 1))).ravel())
+    prev = ev - shift
+    b0, bK, (it_lo, it_hi) = pk.outer_bounds(to_dev(ab, device), prev, i0, nev)
+    ob0, obK, oit_lo, oit_hi = po.outer_bounds(ab, prev, i0, nev, alpha=1e-3, m_hat=6)
+    assert (b0, bK, it_lo, it_hi) == (ob0, obK, oit_lo, oit_hi)
+    assert np.sum(ev < bK) >= i0 + nev and np.sum(ev < b0) <= i0
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_outer_bounds_sequence_step(device, cplx):
+    """The previous eigenvalues come from the previous matrix of an SCF-like sequence
+    (B_prev = B - 1e-3 E)."""
+    import paper_2012_00506_gb300 as pk
+    n, b = 300, 8
+    ab = synth.random_band(n, b, 91 + cplx, cplx)
+    g = np.random.default_rng(92)
+    E = g.standard_normal(ab.shape) + (1j * g.standard_normal(ab.shape) if cplx else 0)
+    E[:, 0] = E[:, 0].real
+    prev = np.linalg.eigvalsh(synth.band_to_dense(ab - 1e-3 * E))
+    for i0, nev in ((0, 60), (100, 30)):
+        b0, bK, its = pk.outer_bounds(to_dev(ab, device), prev, i0, nev)
+        ob0, obK, oit_lo, oit_hi = po.outer_bounds(ab, prev, i0, nev)
+        assert (b0, bK, its) == (ob0, obK, (oit_lo, oit_hi))
+        assert oracle.inertia(ab, bK) >= i0 + nev and oracle.inertia(ab, b0) <= i0
