@@ -245,6 +245,12 @@ int pdeshep_gershgorin(int64_t n, int32_t b, int32_t is_complex, const void* d_b
 /* ------------------------------------------------------------------------ */
 int pdeshep_contour_rule(int32_t ne, double lo, double hi, double rho, pdeshep_c128* h_z,
                          pdeshep_c128* h_w);
+/* The midpoint trapezoid rule on the same half ellipse (Section 2.2 cites it beside Gauss         */
+/* quadrature): t_k = pi (k + 1/2)/ne, w_k = (r/(2 ne))(rho cos t_k + i sin t_k), same filter      */
+/* convention; for rho = 1 the filter is 1/(1 + ((x-c)/r)^(2 ne)).  Pass the nodes and weights to */
+/* pdeshep_band_slice through h_nodes / h_weights.  Host only.                                    */
+int pdeshep_contour_rule_trapezoid(int32_t ne, double lo, double hi, double rho, pdeshep_c128* h_z,
+                                   pdeshep_c128* h_w);
 
 /* ------------------------------------------------------------------------ */
 /* Shifted band solves of eq. (10): for each shift z_s, factor z_s I - B by   */

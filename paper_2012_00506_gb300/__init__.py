@@ -47,7 +47,7 @@ EXPORTED = [
     "pdeshep_kernel_launches",
     "pdeshep_inertia_workspace_size", "pdeshep_inertia", "pdeshep_inertia_noalloc",
     "pdeshep_bisect_workspace_size",
-    "pdeshep_bisect", "pdeshep_gershgorin", "pdeshep_contour_rule",
+    "pdeshep_bisect", "pdeshep_gershgorin", "pdeshep_contour_rule", "pdeshep_contour_rule_trapezoid",
     "pdeshep_shifted_solve_workspace_size", "pdeshep_shifted_solve", "pdeshep_band_matmul",
     "pdeshep_cholqr_workspace_size", "pdeshep_cholqr", "pdeshep_eigh_workspace_size",
     "pdeshep_eigh", "pdeshep_workspace_size", "pdeshep_band_slice",
@@ -136,6 +136,7 @@ def load(path: str = LIB_PATH):
         "pdeshep_bisect": (C.c_int, [i64, i32, i32, P, i64, i32, P, dbl, i32, P, P, P, sz, P]),
         "pdeshep_gershgorin": (C.c_int, [i64, i32, i32, P, i64, P, P, P, sz, P]),
         "pdeshep_contour_rule": (C.c_int, [i32, dbl, dbl, dbl, P, P]),
+        "pdeshep_contour_rule_trapezoid": (C.c_int, [i32, dbl, dbl, dbl, P, P]),
         "pdeshep_shifted_solve_workspace_size": (sz, [i64, i32, i32, i32, i32]),
         "pdeshep_shifted_solve": (C.c_int, [i64, i32, i32, P, i64, i32, P, i32, P, i32, i32, P, P, P, sz, P]),
         "pdeshep_band_matmul": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P]),
@@ -280,13 +281,15 @@ def gershgorin(band, b=None, stream=None):
     return lo.value, hi.value
 
 
-def contour_rule(ne, lo, hi, rho=0.3):
-    """Gauss-Legendre nodes/weights on the upper half ellipse (host computation)."""
+def contour_rule(ne, lo, hi, rho=0.3, kind="gauss"):
+    """Nodes/weights on the upper half ellipse (host computation): Gauss-Legendre
+    (``kind="gauss"``, the default rule of ``band_slice``) or the midpoint trapezoid rule
+    (``kind="trapezoid"``; pass it to ``band_slice`` as ``nodes`` / ``weights``)."""
     lib = load()
     z = np.zeros(ne, dtype=np.complex128)
     w = np.zeros(ne, dtype=np.complex128)
-    _check("pdeshep_contour_rule", lib.pdeshep_contour_rule(int(ne), float(lo), float(hi), float(rho),
-                                                            _np_ptr(z), _np_ptr(w)))
+    fn = {"gauss": "pdeshep_contour_rule", "trapezoid": "pdeshep_contour_rule_trapezoid"}[kind]
+    _check(fn, getattr(lib, fn)(int(ne), float(lo), float(hi), float(rho), _np_ptr(z), _np_ptr(w)))
     return z, w
 
 

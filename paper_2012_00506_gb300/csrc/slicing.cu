@@ -77,6 +77,22 @@ void contour_rule(int ne, double lo, double hi, double rho, pdeshep_c128* z, pde
   }
 }
 
+// Midpoint trapezoid rule on the same half ellipse (the rule of Sakurai and Sugiura that the
+// paper cites beside Gauss quadrature, Section 2.2): t_k = pi (k + 1/2) / ne, weights
+// (1/(2 pi i)) z'(t_k) pi/ne = (r / (2 ne)) (rho cos t_k + i sin t_k).  On a circle (rho = 1)
+// the filter is 1 / (1 + ((x - c)/r)^(2 ne)) for real x.
+void contour_rule_trapezoid(int ne, double lo, double hi, double rho, pdeshep_c128* z, pdeshep_c128* w) {
+  const double c = 0.5 * (lo + hi), r = 0.5 * (hi - lo);
+  for (int k = 0; k < ne; ++k) {
+    const double th = M_PI * (k + 0.5) / ne;
+    const double ct = cos(th), st = sin(th);
+    z[k].re = c + r * ct;
+    z[k].im = r * rho * st;
+    w[k].re = r / (2.0 * ne) * rho * ct;
+    w[k].im = r / (2.0 * ne) * st;
+  }
+}
+
 // Batched bisection: enclosures [lo_t, hi_t) of eigenvalue idx_t with
 // count(lo) <= idx < count(hi).  Each round evaluates `fanout` interior
 // points per unfinished enclosure in one inertia launch.
@@ -209,6 +225,17 @@ extern "C" int pdeshep_contour_rule(int32_t ne, double lo, double hi, double rho
   if (!h_z) return -5;
   if (!h_w) return -6;
   contour_rule(ne, lo, hi, rho, h_z, h_w);
+  return 0;
+}
+
+extern "C" int pdeshep_contour_rule_trapezoid(int32_t ne, double lo, double hi, double rho, pdeshep_c128* h_z,
+                                              pdeshep_c128* h_w) {
+  if (ne < 1 || ne > 256) return -1;
+  if (!(lo < hi)) return -2;
+  if (!(rho > 0.0)) return -4;
+  if (!h_z) return -5;
+  if (!h_w) return -6;
+  contour_rule_trapezoid(ne, lo, hi, rho, h_z, h_w);
   return 0;
 }
 
