@@ -315,6 +315,18 @@ int pdeshep_partition(int32_t method, int64_t n, const double* h_d, int32_t K, d
                       int32_t max_sweeps, double* h_bounds, int32_t* h_counts, int32_t* h_k_out,
                       int32_t* h_sweeps);
 
+/* Start vectors after a re-slicing (Section 3.1: when a slice grows the     */
+/* previous vectors are interlaced with random ones, when it shrinks some are */
+/* removed).  h_prev_vals[nprev]: Ritz value of each previous column.  For    */
+/* new slice i the block of h_m0[i] entries of h_src (blocks in slice order)  */
+/* lists the previous columns with values in [b_i, b_{i+1}) -- the h_m0[i]    */
+/* nearest to the slice centre if there are more -- in ascending value (ties  */
+/* by column), then (mode 1) the nearest columns outside the slice, and -1    */
+/* for each remaining column (a random start vector).  Host only.             */
+/* ------------------------------------------------------------------------ */
+int pdeshep_restart_plan(int64_t nprev, const double* h_prev_vals, int32_t K, const double* h_bounds,
+                         const int32_t* h_m0, int32_t mode, int64_t* h_src);
+
 /* ------------------------------------------------------------------------ */
 /* Outer bounds of the wanted eigenvalues i0 .. i0+nev-1 of the band from the */
 /* previous matrix's eigenvalues h_prev[nprev] (ascending) (Section 3.2,      */

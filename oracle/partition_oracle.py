@@ -12,6 +12,9 @@ loops over the sorted eigenvalues, following the paper's steps in order:
 * ``equal_count_slices``  "Approach-1" of Section 3.1: the starting partition of
                           Algorithm 3 (equal counts, boundaries at gap midpoints).
 * ``equal_width_slices``  "Approach-2" of Section 3.1: K equal pieces of [b0, bK].
+* ``restart_plan``        start vectors after a re-slicing (Section 3.1: previous
+                          vectors interlaced with random ones when a slice grows,
+                          some removed when it shrinks).
 * ``outer_bounds``        the bound search of Algorithm 4 (Section 3.2) and its
                           lower-bound counterpart described in the text: step away
                           from the previous extreme wanted eigenvalues by
@@ -158,3 +161,33 @@ def min_boundary_gap(d, bounds):
     into a cluster; objective 1 of Section 3.1 wants it large)."""
     d = np.asarray(d, dtype=float)
     return float(min(np.min(np.abs(d - b)) for b in bounds[1:-1])) if len(bounds) > 2 else float("inf")
+
+
+def restart_plan(prev_vals, bounds, m0_new, mode=0):
+    """Start vectors for the next matrix of a sequence when the slices change (Section 3.1:
+    when a slice's count grows, the previous vectors are interlaced with random ones; when it
+    shrinks, some are removed).  ``prev_vals[c]`` is the Ritz value of previous column c.
+    For new slice i (block of m0_new[i] columns): the previous columns whose values lie in
+    [b_i, b_{i+1}) -- the m0_new[i] nearest to the slice centre if there are more -- in
+    ascending value (ties by column); then, with mode 1, the nearest columns outside the slice
+    (by distance to the interval; ties by value, then column); the rest -1 (a random vector).
+    Returns one list per slice."""
+    v = [float(x) for x in prev_vals]
+    out = []
+    for i in range(len(bounds) - 1):
+        lo, hi = bounds[i], bounds[i + 1]
+        c = 0.5 * (lo + hi)
+        m = int(m0_new[i])
+        inside = [k for k in range(len(v)) if lo <= v[k] < hi]
+        if len(inside) > m:
+            inside = sorted(inside, key=lambda k: (abs(v[k] - c), k))[:m]
+        inside = sorted(inside, key=lambda k: (v[k], k))
+        pick = list(inside)
+        if mode == 1 and len(pick) < m:
+            outside = [k for k in range(len(v)) if not (lo <= v[k] < hi)]
+            dist = lambda k: (lo - v[k]) if v[k] < lo else (v[k] - hi)
+            outside = sorted(outside, key=lambda k: (dist(k), v[k], k))
+            pick += outside[: m - len(pick)]
+        pick += [-1] * (m - len(pick))
+        out.append(pick)
+    return out

@@ -57,6 +57,7 @@ EXPORTED = [
     "pdeshep_block_gemm_workspace_size", "pdeshep_block_gemm",
     "pdeshep_band_matmul_tc_workspace_size", "pdeshep_band_matmul_tc",
     "pdeshep_partition", "pdeshep_outer_bounds_workspace_size", "pdeshep_outer_bounds",
+    "pdeshep_restart_plan",
 ]
 
 
@@ -148,6 +149,7 @@ def load(path: str = LIB_PATH):
         "pdeshep_band_matmul_tc_workspace_size": (sz, [i64, i32, i32, i32]),
         "pdeshep_band_matmul_tc": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P, sz, P]),
         "pdeshep_partition": (C.c_int, [i32, i64, P, i32, dbl, dbl, i32, P, P, P, P]),
+        "pdeshep_restart_plan": (C.c_int, [i64, P, i32, P, P, i32, P]),
         "pdeshep_outer_bounds_workspace_size": (sz, [i64, i32, i32]),
         "pdeshep_outer_bounds": (C.c_int, [i64, i32, i32, P, i64, i64, P, i64, i64, dbl, dbl, i32, P, P, P, P, sz,
                                            P]),
@@ -361,6 +363,19 @@ def partition(evals, K, b0, bK, method=PART_KMEANS, max_sweeps=1000):
     _check("pdeshep_partition", st)
     k = kout.value
     return bounds[: k + 1].copy(), counts[:k].copy(), int(sweeps.value)
+
+
+def restart_plan(prev_vals, bounds, m0, mode=0):
+    """Previous columns (or -1 = random) for the start block of every new slice (host only);
+    returns one array per slice.  See ``pdeshep_restart_plan``."""
+    lib = load()
+    v = np.ascontiguousarray(np.asarray(prev_vals, dtype=np.float64))
+    bd = np.ascontiguousarray(np.asarray(bounds, dtype=np.float64))
+    m = np.ascontiguousarray(np.asarray(m0, dtype=np.int32))
+    src = np.zeros(int(m.astype(np.int64).sum()), dtype=np.int64)
+    st = lib.pdeshep_restart_plan(v.size, _np_ptr(v), m.size, _np_ptr(bd), _np_ptr(m), int(mode), _np_ptr(src))
+    _check("pdeshep_restart_plan", st)
+    return np.split(src, np.cumsum(m)[:-1])
 
 
 def outer_bounds(band, prev, i0, nev, alpha=1e-3, m_hat=6.0, max_it=64, b=None, stream=None):

@@ -18,6 +18,12 @@
 //    follows the midpoint of its two groups' centroids (a group's centroid is the
 //    mean of its extreme points); the sweeps repeat until no boundary moves, and
 //    groups that become empty are merged away, so K may shrink.
+//
+// After a re-slicing the start vectors of the next call come from the previous
+// call's vectors whose Ritz values fall in each new slice (the paper interlaces
+// random vectors when a slice grows and removes some when it shrinks):
+// pdeshep_restart_plan lists, per new slice, the previous columns to copy and the
+// number of random ones.
 #include <math.h>
 
 #include <algorithm>
@@ -121,6 +127,55 @@ extern "C" int pdeshep_partition(int32_t method, int64_t n, const double* h_d, i
     h_counts[i] = (int32_t)(lower_idx(h_d, n, b[i + 1]) - lower_idx(h_d, n, b[i]));
   *h_k_out = kout;
   if (h_sweeps) *h_sweeps = sweeps;
+  return 0;
+}
+
+extern "C" int pdeshep_restart_plan(int64_t nprev, const double* h_prev_vals, int32_t K, const double* h_bounds,
+                                    const int32_t* h_m0, int32_t mode, int64_t* h_src) {
+  if (nprev < 0) return -1;
+  if (nprev > 0 && !h_prev_vals) return -2;
+  for (int64_t k = 0; k < nprev; ++k)
+    if (!std::isfinite(h_prev_vals[k])) return -2;
+  if (K < 1) return -3;
+  if (!h_bounds) return -4;
+  for (int i = 0; i < K; ++i)
+    if (!(h_bounds[i] < h_bounds[i + 1])) return -4;
+  if (!h_m0) return -5;
+  for (int i = 0; i < K; ++i)
+    if (h_m0[i] < 0) return -5;
+  if (mode != 0 && mode != 1) return -6;
+  if (!h_src) return -7;
+  const double* v = h_prev_vals;
+  int64_t off = 0;
+  for (int i = 0; i < K; ++i) {
+    const double lo = h_bounds[i], hi = h_bounds[i + 1], c = 0.5 * (lo + hi);
+    const int64_t m = h_m0[i];
+    std::vector<int64_t> inside, outside;
+    for (int64_t k = 0; k < nprev; ++k) (lo <= v[k] && v[k] < hi ? inside : outside).push_back(k);
+    if ((int64_t)inside.size() > m) {  // keep the m nearest to the centre
+      std::stable_sort(inside.begin(), inside.end(), [&](int64_t a, int64_t b) {
+        const double da = fabs(v[a] - c), db = fabs(v[b] - c);
+        return da < db || (da == db && a < b);
+      });
+      inside.resize(m);
+    }
+    std::stable_sort(inside.begin(), inside.end(),
+                     [&](int64_t a, int64_t b) { return v[a] < v[b] || (v[a] == v[b] && a < b); });
+    int64_t q = 0;
+    for (int64_t k : inside) h_src[off + q++] = k;
+    if (mode == 1 && q < m) {  // then the nearest columns outside the slice
+      auto dist = [&](int64_t k) { return v[k] < lo ? lo - v[k] : v[k] - hi; };
+      std::stable_sort(outside.begin(), outside.end(), [&](int64_t a, int64_t b) {
+        const double da = dist(a), db = dist(b);
+        if (da != db) return da < db;
+        if (v[a] != v[b]) return v[a] < v[b];
+        return a < b;
+      });
+      for (size_t t = 0; t < outside.size() && q < m; ++t) h_src[off + q++] = outside[t];
+    }
+    for (; q < m; ++q) h_src[off + q] = -1;  // a random start vector
+    off += m;
+  }
   return 0;
 }
 

@@ -103,3 +103,29 @@ def test_outer_bounds_against_closed_form_spectrum(i0, nev, shift):
     dl = prev[i0]
     step2 = max(abs(1e-3 * dl), 6 * (prev[i0 + 1] - dl))
     assert (dl - it_lo * step2) <= ev[i0] and (dl - (it_lo - 1) * step2 > ev[i0] or it_lo == 1)
+
+
+def test_restart_plan_invariants():
+    """Start vectors after a re-slicing: unchanged slices keep their own vectors; a grown slice
+    keeps every previous vector inside it and fills with random ones (mode 0) or with its nearest
+    outside neighbours (mode 1); a shrunk slice keeps the ones nearest its centre."""
+    g = np.random.default_rng(4)
+    vals = np.sort(g.uniform(0, 1, 60))
+    old_b = [0.0, 0.3, 0.6, 1.0]
+    counts = [int(np.sum((vals >= lo) & (vals < hi))) for lo, hi in zip(old_b[:-1], old_b[1:])]
+    plan = po.restart_plan(vals, old_b, counts)
+    for (lo, hi), p in zip(zip(old_b[:-1], old_b[1:]), plan):
+        assert list(p) == [k for k in range(vals.size) if lo <= vals[k] < hi]
+    # a slice that grows by 5: every inside vector, then 5 random (mode 0) / 5 neighbours (mode 1)
+    new_b = [0.0, 0.3, 0.6, 1.0]
+    m = [counts[0] + 5, counts[1], counts[2]]
+    p0 = po.restart_plan(vals, new_b, m, mode=0)[0]
+    assert p0[-5:] == [-1] * 5 and all(vals[k] < 0.3 for k in p0[:-5])
+    p1 = po.restart_plan(vals, new_b, m, mode=1)[0]
+    nearest_above = [k for k in range(vals.size) if vals[k] >= 0.3][:5]
+    assert p1[-5:] == nearest_above
+    # a slice that shrinks: the kept vectors are the ones nearest the centre, in ascending order
+    p = po.restart_plan(vals, [0.2, 0.5], [6])[0]
+    inside = [k for k in range(vals.size) if 0.2 <= vals[k] < 0.5]
+    expect = sorted(sorted(inside, key=lambda k: abs(vals[k] - 0.35))[:6])
+    assert p == expect and len(inside) > 6

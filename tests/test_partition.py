@@ -70,3 +70,21 @@ def test_kmeans_sweep_cap_and_arguments(pk):
     assert args(b0=float(x[0]) + 1e-9) == -5
     assert args(bK=float(x[-1])) == -6                         # the last point must lie below bK
     assert args(ms=0) == -7
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_restart_plan_matches_oracle(pk, mode):
+    g = np.random.default_rng(12 + mode)
+    vals = g.uniform(-1, 1, 300)                  # previous Ritz values, column order
+    vals[50:55] = 0.125                            # ties
+    bounds = np.sort(np.r_[-1.2, g.uniform(-1, 1, 6), 1.2])
+    m0 = g.integers(0, 90, bounds.size - 1).astype(np.int32)
+    plan = pk.restart_plan(vals, bounds, m0, mode)
+    oplan = po.restart_plan(vals, list(bounds), list(m0), mode)
+    assert [list(p) for p in plan] == oplan
+    lib = pk.load()
+    src = np.zeros(int(m0.sum()), dtype=np.int64)
+    assert lib.pdeshep_restart_plan(vals.size, vals.ctypes.data, m0.size, bounds[::-1].copy().ctypes.data,
+                                    m0.ctypes.data, mode, src.ctypes.data) == -4   # bounds not ascending
+    assert lib.pdeshep_restart_plan(vals.size, vals.ctypes.data, m0.size, bounds.ctypes.data, m0.ctypes.data, 2,
+                                    src.ctypes.data) == -6
