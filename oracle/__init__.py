@@ -23,6 +23,11 @@ Every function states the passage of arXiv 2012.00506 it follows:
 * ``feast_slice``        Algorithm 1 on one slice.
 * ``m0_rule``            m_i^(0) = max(1.3 m_i, m_i + 10) (Section 3.2).
 * ``orth``               Orth = ||X^H X - I||_max / n (Section 4, Example 2).
+
+Submodules (plain Python/NumPy): ``partition_oracle`` (Algorithms 3 and 4, the
+restart plan), ``rules_oracle`` (the trapezoid rule), ``reduction_oracle``
+(Steps (I) and (III): dense -> band reduction and backtransform),
+``slicer_oracle`` (the proposer's features and network).
 """
 from __future__ import annotations
 

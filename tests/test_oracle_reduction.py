@@ -1,0 +1,42 @@
+"""Pins of the Step (I)/(III) oracle (dense -> band reduction D = U A U^H by block Householder
+transformations, backtransform X = U^H X_hat; Section 2.1 and Algorithm 2 of the paper) against
+LAPACK eigenvalues and the defining identities."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import reduction_oracle as ro
+
+
+def _herm(n, cplx, seed):
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((n, n)) + (1j * g.standard_normal((n, n)) if cplx else 0)
+    return 0.5 * (A + A.conj().T)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n,b", [(50, 4), (37, 5), (20, 1), (64, 16), (33, 32)])
+def test_reduction_identities(cplx, n, b):
+    A = _herm(n, cplx, 100 + n + b)
+    nrm = np.linalg.norm(A, 2)
+    D, W = ro.dense_to_band(A, b)
+    # W unitary, D = W^H A W exactly banded (the product recomputed here, not the oracle's D)
+    assert np.max(np.abs(W.conj().T @ W - np.eye(n))) < 1e-14 * n
+    F = W.conj().T @ A @ W
+    for k in range(b + 1, n):
+        assert np.max(np.abs(np.diag(F, -k))) < 1e-14 * nrm * n
+    assert np.max(np.abs(F - D)) < 1e-14 * nrm * n
+    # same spectrum as A (LAPACK)
+    assert np.max(np.abs(np.linalg.eigvalsh(D) - np.linalg.eigvalsh(A))) < 1e-13 * nrm
+    # Step (III): eigenvectors of the band mapped back are eigenvectors of A
+    lam, Xh = np.linalg.eigh(D)
+    X = ro.backtransform(W, Xh)
+    assert np.max(np.linalg.norm(A @ X - X * lam, axis=0)) < 1e-13 * nrm * np.sqrt(n)
+    # band storage is the FEAST input layout
+    assert np.array_equal(synth.band_to_dense(ro.to_lower_band(D, b)), D)
+
+
+def test_reduction_trivial_bandwidth():
+    A = _herm(12, True, 7)
+    D, W = ro.dense_to_band(A, 11)
+    assert np.array_equal(W, np.eye(12)) and np.array_equal(D, 0.5 * (A + A.conj().T))
