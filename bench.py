@@ -227,6 +227,18 @@ def good_pairs(res, m0):
     return int(sum(int(res.nfound[i]) for i in range(len(m0)) if res.nfound[i] == res.counts[i]))
 
 
+def reduce_over_ranks(dist, torch, dev, t_s, pairs):
+    """Whole-job numbers of the replicas: the slowest rank's time and the pairs of all ranks
+    (every rank runs its own copy of the workload; no collective inside the timed region)."""
+    if not dist:
+        return t_s, pairs
+    t = torch.tensor([t_s], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    pt = torch.tensor([float(pairs)], device=dev, dtype=torch.float64)
+    dist.all_reduce(pt, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(pt.item())
+
+
 def run_gpu(args):
     import torch
     import paper_2012_00506_gb300 as pk
@@ -292,15 +304,7 @@ def run_gpu(args):
     launches = pk.kernel_launches() - l0
     clk = clocks.stop()
     t_s = e0.elapsed_time(e1) / 1e3
-    if dist:
-        t = torch.tensor([t_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_s = float(t.item())
-        pt = torch.tensor([float(pairs)], device=dev, dtype=torch.float64)
-        dist.all_reduce(pt, op=dist.ReduceOp.SUM)
-        pairs_all = int(pt.item())
-    else:
-        pairs_all = pairs
+    t_s, pairs_all = reduce_over_ranks(dist, torch, dev, t_s, pairs)
     value = pairs_all / t_s
 
     # dominant kernel group and its roofline: the inertia counts run on a side stream under the
