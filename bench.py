@@ -349,6 +349,8 @@ def run_gpu(args):
         out["e2e"] = e2e_leg(pk, torch, seq, inputs[: max(1, min(K, args.e2e_steps))], stream)
     if rank == 0 and not args.no_proposal:
         out["slice_proposal"] = proposal_leg(pk, torch, dev)
+    if rank == 0:
+        out["partition_report"] = partition_report(pk, r, seq)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(seq.host, seq.bounds0, seq.m0, seq.bnorm[0])
     if dist:
@@ -378,6 +380,35 @@ def plain_leg(pk, torch, seq, inputs, stream, precision=None, dtype="c128+f64", 
     return {"value": round(pairs / t, 2), "unit": "eigenpairs/s", "steps": len(inputs),
             "ms_per_step": round(t * 1e3 / len(inputs), 3), "iterations_per_step": iters,
             "dtype": dtype}
+
+
+def partition_report(pk, res, seq):
+    """The paper's re-slicing (Algorithm 3, simplified 1-D k-means) against the equal-count
+    re-slicing the sequence uses, on the eigenvalues of the last timed step (host work only):
+    counts per slice, the distance from the inner boundaries to the nearest eigenvalue in units
+    of the median spacing, sweeps and host time."""
+    try:
+        ev = res.evals.cpu().numpy()
+        vals, off = [], 0
+        for i in range(NSLICE):
+            k = int(res.nfound[i])
+            vals.append(ev[off:off + k])
+            off += int(seq.m0[i])
+        lam = np.sort(np.concatenate(vals))
+        spacing = float(np.median(np.diff(lam)))
+        b0, bK = float(lam[0] - spacing), float(lam[-1] + spacing)
+        out = {"eigenvalues": int(lam.size), "slices": NSLICE}
+        for name, method in (("equal_counts", pk.PART_EQUAL_COUNT), ("kmeans", pk.PART_KMEANS)):
+            t0 = time.perf_counter()
+            b, c, sweeps = pk.partition(lam, NSLICE, b0, bK, method=method)
+            us = (time.perf_counter() - t0) * 1e6
+            gaps = [float(np.min(np.abs(lam - x))) / spacing for x in b[1:-1]]
+            out[name] = {"counts_min": int(c.min()), "counts_max": int(c.max()),
+                         "min_gap_spacings": round(min(gaps), 3), "median_gap_spacings": round(float(np.median(gaps)), 3),
+                         "sweeps": sweeps, "host_us": round(us, 1)}
+        return out
+    except Exception as e:  # a report only: never let it break the bench line
+        return {"error": repr(e)}
 
 
 def proposal_leg(pk, torch, dev):
