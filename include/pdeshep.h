@@ -322,7 +322,10 @@ int pdeshep_partition(int32_t method, int64_t n, const double* h_d, int32_t K, d
 /* lists the previous columns with values in [b_i, b_{i+1}) -- the h_m0[i]    */
 /* nearest to the slice centre if there are more -- in ascending value (ties  */
 /* by column), then (mode 1) the nearest columns outside the slice, and -1    */
-/* for each remaining column (a random start vector).  Host only.             */
+/* for each remaining column (a random start vector).  Offer the previous    */
+/* call's converged pairs (distinct eigenvectors): its unconverged extra      */
+/* columns approximate the neighbouring slices' vectors, and mixing both can  */
+/* make a start block numerically rank-deficient.  Host only.                */
 /* ------------------------------------------------------------------------ */
 int pdeshep_restart_plan(int64_t nprev, const double* h_prev_vals, int32_t K, const double* h_bounds,
                          const int32_t* h_m0, int32_t mode, int64_t* h_src);

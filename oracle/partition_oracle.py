@@ -171,6 +171,7 @@ def restart_plan(prev_vals, bounds, m0_new, mode=0):
     [b_i, b_{i+1}) -- the m0_new[i] nearest to the slice centre if there are more -- in
     ascending value (ties by column); then, with mode 1, the nearest columns outside the slice
     (by distance to the interval; ties by value, then column); the rest -1 (a random vector).
+    The columns offered should be the previous converged pairs (distinct eigenvectors).
     Returns one list per slice."""
     v = [float(x) for x in prev_vals]
     out = []
