@@ -14,7 +14,7 @@ from oracle import partition_oracle as po
 from oracle import rules_oracle as ro
 
 
-def _sequence(method, rule_kind, n=800, b=8, nev=160, K=8, steps=4, ne=8, seed=5):
+def _sequence(method, rule_kind, n=800, b=8, nev=160, K=8, steps=4, ne=8, seed=5, outer="dense"):
     B = synth.random_band(n, b, seed, True, off_sigma=0.1)
     g = np.random.default_rng(seed + 1)
     totals, maxima = [], []
@@ -22,9 +22,13 @@ def _sequence(method, rule_kind, n=800, b=8, nev=160, K=8, steps=4, ne=8, seed=5
     dense_ev = np.linalg.eigvalsh(synth.band_to_dense(B))
     for step in range(steps):
         ref = dense_ev[:nev] if step == 0 else lam
-        spacing = float(np.median(np.diff(ref)))
-        b0 = float(ref[0] - 2 * spacing)
-        bK = float(0.5 * (dense_ev[nev - 1] + dense_ev[nev]))   # previous matrix: excludes eigenvalue nev
+        if outer == "alg4" and step > 0:
+            # Algorithm 4 on the current matrix from the previous eigenvalues (Section 3.2)
+            b0, bK, _, _ = po.outer_bounds(B, lam, 0, nev)
+        else:
+            spacing = float(np.median(np.diff(ref)))
+            b0 = float(ref[0] - 2 * spacing)
+            bK = float(0.5 * (dense_ev[nev - 1] + dense_ev[nev]))   # previous matrix: excludes eigenvalue nev
         if method == "equal":
             bounds, _ = po.equal_count_slices(ref, K, b0, bK)
         else:
@@ -57,8 +61,11 @@ def _sequence(method, rule_kind, n=800, b=8, nev=160, K=8, steps=4, ne=8, seed=5
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("method,rule", [("equal", "gauss"), ("kmeans", "gauss"), ("kmeans", "trapezoid")])
-def test_sequence_with_reslicing(method, rule):
-    totals, maxima = _sequence(method, rule)
-    print(f"\n{method:6s} {rule:9s} slice iterations per step {totals}, slowest slice per step {maxima}")
+@pytest.mark.parametrize("method,rule,outer", [("equal", "gauss", "dense"), ("kmeans", "gauss", "dense"),
+                                               ("kmeans", "trapezoid", "dense"), ("kmeans", "gauss", "alg4")])
+def test_sequence_with_reslicing(method, rule, outer):
+    """outer = "alg4": the outer bounds of every warm step come from Algorithm 4 on the current
+    matrix instead of the previous matrix's dense spectrum (the loop of the paper's Algorithm 2)."""
+    totals, maxima = _sequence(method, rule, outer=outer)
+    print(f"\n{method:6s} {rule:9s} {outer:5s} slice iterations per step {totals}, slowest slice per step {maxima}")
     assert all(m <= 6 for m in maxima[1:])            # warm-started steps converge in a few iterations
