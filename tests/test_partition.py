@@ -88,3 +88,30 @@ def test_restart_plan_matches_oracle(pk, mode):
                                     m0.ctypes.data, mode, src.ctypes.data) == -4   # bounds not ascending
     assert lib.pdeshep_restart_plan(vals.size, vals.ctypes.data, m0.size, bounds.ctypes.data, m0.ctypes.data, 2,
                                     src.ctypes.data) == -6
+
+
+def test_randomized_parity(pk):
+    """300 random inputs (uniform, many ties, tight clusters, growing gaps; K from 1 to 19, also
+    above n): boundaries, counts and sweeps identical to the oracle for all three methods."""
+    g = np.random.default_rng(0)
+    for trial in range(300):
+        n = int(g.integers(1, 60))
+        kind = trial % 4
+        if kind == 0:
+            d = g.uniform(-1, 1, n)
+        elif kind == 1:
+            d = np.round(g.uniform(0, 1, n) * 5) / 5
+        elif kind == 2:
+            d = np.concatenate([c + 1e-9 * g.standard_normal(int(g.integers(1, 5)))
+                                for c in g.uniform(0, 3, max(1, n // 3))])
+        else:
+            d = np.cumsum(g.exponential(1.0, n)) ** 2
+        d = np.sort(d)
+        K = int(g.integers(1, 20))
+        b0, bK = float(d[0] - g.uniform(0.01, 1)), float(d[-1] + g.uniform(0.01, 1))
+        b, c, sw = pk.partition(d, K, b0, bK, method=pk.PART_KMEANS)
+        ob, oc, osw = po.kmeans_slices(d, K, b0, bK)
+        assert np.array_equal(b, np.asarray(ob)) and list(c) == oc and sw == osw
+        b, c, _ = pk.partition(d, K, b0, bK, method=pk.PART_EQUAL_COUNT)
+        ob, oc = po.equal_count_slices(d, K, b0, bK)
+        assert np.array_equal(b, np.asarray(ob)) and list(c) == oc
