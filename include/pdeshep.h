@@ -71,8 +71,15 @@ typedef struct {
                               autotuned width when autotune is on */
   double ellipse_ratio;    /* vertical / horizontal semi-axis of the contour; default 0.3 */
   double bnorm;            /* ||B||_2 for the residual; <= 0: computed by the library */
-  uint64_t seed;           /* reserved for library-drawn start vectors */
-  size_t hbm_cap_bytes;    /* cap on factor storage per wave; 0 = whole workspace */
+  uint64_t seed;           /* start vectors drawn by the library when d_x0 is NULL (see
+                              pdeshep_random_start); default 0 */
+  size_t hbm_cap_bytes;    /* cap on the factor storage (factors and per-system solve outputs) of
+                              one group of slices; 0 = whatever the workspace holds.  Slices run
+                              in consecutive groups whose factors all stay resident within the
+                              cap and the workspace, each group iterating to convergence on
+                              factors computed once (a call that fits is one group); a single
+                              slice whose factors exceed it streams them in waves every
+                              iteration */
   int32_t autotune;        /* 0 off; 1 use the tuned choice for this problem shape, measuring
                               it on first use; 2 measure again.  Tuned: the solve column block
                               (16/32/64, unless rhs_chunk is set) and the split count of the
@@ -85,13 +92,20 @@ typedef struct {
                               and small products float-float.  PDESHEP_RR_FLOATFLOAT: all products
                               float-float.  In both, iterations after the third run the
                               float-float products in FP64.  PDESHEP_RR_FP64: all products FP64 */
-  int32_t pad0;
+  int32_t m0_resize;       /* 1: the subspace rule of Section 3.2 in the library.  The exact counts
+                              m_i are taken first; a slice whose h_m0[i] is below m_i + 10 runs
+                              with max(ceil(1.3 m_i), m_i + 10) columns, at most m0_cap.  The
+                              blocks of d_x0 / d_evals / d_evecs are then m0_cap columns each
+                              (slice i at column i * m0_cap; its start vectors are the first m0
+                              columns of its block).  COUNT_MISMATCH only if m_i > m0_cap.
+                              0 (default): h_m0 as given, COUNT_MISMATCH if below m_i */
   const char* tune_cache;  /* file that keeps tuned choices across processes; NULL = in-process */
   int32_t graphs;          /* 1: with resident factors, each filter pass (right-hand sides,
                               weights, both solves, accumulation) is captured once per set of
                               active slices as a CUDA graph and replayed; needs a stream other
                               than the legacy default stream.  0 (default): direct launches */
-  int32_t pad1;
+  int32_t m0_cap;          /* column capacity of each slice's block when m0_resize = 1 */
+  int32_t* h_m0_used;      /* optional host output (nslices): the m0 each slice ran with */
 } pdeshep_opts;
 
 /* Arithmetic of the Rayleigh-Ritz products (Gram, projection, basis update,   */
@@ -204,9 +218,11 @@ int pdeshep_inertia(int64_t n, int32_t b, int32_t is_complex, const void* d_band
 /*  Limits: nsigma <= 1024 (else -6) and the LDL^T window must fit in shared */
 /*  memory: real b <= 141, complex b <= 105 (else -2); the reason is then in */
 /*  pdeshep_last_error().                                                    */
-/*  The first call on a device looks up the array's device address for that */
-/*  device (cudaGetSymbolAddress), so make that first call before any stream */
-/*  capture.  All calls share the one array and it keeps the last call's     */
+/*  Every call looks up the array's device address on the current device    */
+/*  (cudaGetSymbolAddress); the first call on a device may load the library's */
+/*  device code there, so make that first call before any stream capture.    */
+/*  A negative b is refused with -2 as well.  All calls share the one array  */
+/*  and it keeps the last call's                                             */
 /*  contents (each call clears and rewrites what it uses): calls that may    */
 /*  overlap on the GPU -- concurrent streams, or host threads on the same    */
 /*  device -- race on it and must be serialised by the caller.  Synchronous: */
@@ -339,7 +355,10 @@ int pdeshep_restart_plan(int64_t nprev, const double* h_prev_vals, int32_t K, co
 /* starts at h_prev[i0] minus max(|alpha d'|, m_hat (h_prev[i0+1] - d')) and  */
 /* shrinks until the count below it is <= i0 (a zero step becomes 2^-40 of   */
 /* the value).  At most max_it counts each; h_iters[2] (optional) = the       */
-/* counts taken for b0 and bK.  Synchronous.  Workspace:                      */
+/* counts taken for b0 and bK.  Returns PDESHEP_NOT_CONVERGED (outputs still  */
+/* written) when a search spent its max_it counts without reaching its       */
+/* target, i.e. the bounds do not enclose the wanted eigenvalues.            */
+/* Synchronous.  Workspace:                                                  */
 /* pdeshep_outer_bounds_workspace_size(n, b, is_complex).                     */
 /* ------------------------------------------------------------------------ */
 size_t pdeshep_outer_bounds_workspace_size(int64_t n, int32_t b, int32_t is_complex);
@@ -404,13 +423,18 @@ int pdeshep_eigh(int32_t is_complex, int32_t nblk, const int32_t* h_m, void* d_a
 /*  h_m0[i]: subspace size of slice i (must be >= the slice's exact count;    */
 /*    Section 3.2 suggests max(1.3 m_i, m_i + 10)).                            */
 /*  d_x0: n x sum(m0) start vectors (slice-major column blocks), same type as */
-/*    the band; e.g. random vectors or the previous SCF step's eigenvectors.  */
+/*    the band; e.g. random vectors or the previous SCF step's eigenvectors;  */
+/*    NULL: drawn by the library from opts.seed (pdeshep_random_start's       */
+/*    columns, numbered by the output column of each slice block).          */
 /*  Outputs: d_evals[sum(m0)], d_evecs n x sum(m0) (same type as the band);   */
 /*    in slice block i the first h_nfound[i] pairs are the converged in-slice  */
 /*    eigenpairs (ascending), then the other Ritz pairs (ascending).          */
 /*    h_counts[i] = exact inertia count of slice i.  h_stats optional.         */
 /* Returns PDESHEP_NOT_CONVERGED if some slice did not converge (its outputs  */
 /* are the last Ritz pairs; converged slices are valid).                     */
+/* Workspace: pdeshep_workspace_size with the same opts (its plan of slice   */
+/* groups depends on hbm_cap_bytes, m0_resize and m0_cap).  Statistics of a  */
+/* grouped call are summed over the groups (iterations: the maximum).        */
 /* ------------------------------------------------------------------------ */
 size_t pdeshep_workspace_size(int64_t n, int32_t b, int32_t is_complex, int32_t nslices,
                               const int32_t* h_m0, int32_t ne, const pdeshep_opts* opts);
@@ -420,6 +444,19 @@ int pdeshep_band_slice(int64_t n, int32_t b, int32_t is_complex, const void* d_b
                        const int32_t* h_m0, const void* d_x0, void* d_work, size_t work_bytes,
                        const pdeshep_opts* opts, double* d_evals, void* d_evecs, int32_t* h_counts,
                        int32_t* h_nfound, pdeshep_stats* h_stats);
+
+/* ------------------------------------------------------------------------ */
+/* Start vectors drawn by the library (the "random vectors" of Algorithm 1's */
+/* first iteration, for callers that pass d_x0 = NULL): columns col0 ..      */
+/* col0+ncols-1 of a counter-based stream, n x ncols column-major into d_x.  */
+/* Entry (i, c) uses word k = (col0 + c) n + i: real bands x = u(seed + k),  */
+/* complex bands x = u(seed + 2k) + i u(seed + 2k + 1), u(w) = (top 53 bits  */
+/* of splitmix64(w)) 2^-52 - 1, uniform in [-1, 1) (splitmix64: Vigna's     */
+/* generator, golden-ratio increment 0x9e3779b97f4a7c15, then the mixer).    */
+/* Asynchronous.                                                             */
+/* ------------------------------------------------------------------------ */
+int pdeshep_random_start(int64_t n, int32_t is_complex, int64_t col0, int32_t ncols, uint64_t seed, void* d_x,
+                         void* stream);
 
 /* ======================================================================== */
 /* Slice proposal.  The paper slices the spectrum by inertia counts          */
@@ -475,6 +512,23 @@ int pdeshep_mlp_grad(const float* d_params, int32_t batch, const float* d_x, con
 int pdeshep_mlp_train_step(float* d_params, float* d_adam_m, float* d_adam_v, int32_t step, float lr,
                            int32_t batch, const float* d_x, const float* d_target, float* d_loss,
                            void* d_work, size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Training labels of the proposal network (its regression targets): for k =  */
+/* 1..nslices-1, t_k = floor(k n / nslices + 1/2) clipped to [1, n-1]; the    */
+/* eigenvalues t_k - 1 and t_k (0-based, ascending) are enclosed by bisection */
+/* on inertia to relative width rtol (pdeshep_bisect, `fanout` points per    */
+/* enclosure per launch), and h_targets[k-1] = clip((s_k - lo)/(hi - lo), 0,  */
+/* 1) in FP32, s_k the midpoint of the two enclosures' midpoints and [lo, hi] */
+/* the Gershgorin interval (pdeshep_gershgorin).  The equal-count partition   */
+/* is one of the paper's partition objectives (Section 3.1); counts by        */
+/* inertia (Section 3.2).  Synchronous.                                       */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_equal_count_targets_workspace_size(int64_t n, int32_t b, int32_t is_complex, int32_t nslices,
+                                                  int32_t fanout);
+int pdeshep_equal_count_targets(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                                int32_t nslices, double rtol, int32_t fanout, float* h_targets, void* d_work,
+                                size_t work_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Propose nslices slices holding equal shares of the eigenvalues with       */

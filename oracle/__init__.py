@@ -22,7 +22,13 @@ Every function states the passage of arXiv 2012.00506 it follows:
 * ``jacobi_eig``         A_q W_q = W_q Lambda_q (Section 2.2).
 * ``feast_slice``        Algorithm 1 on one slice.
 * ``m0_rule``            m_i^(0) = max(1.3 m_i, m_i + 10) (Section 3.2).
-* ``orth``               Orth = ||X^H X - I||_max / n (Section 4, Example 2).
+* ``random_start``       the random start vectors of Algorithm 1 from a
+                         counter-based SplitMix64 stream (the generator both
+                         sides implement from its published definition).
+* ``orth``               Orth = ||X^H X - I||_max / n (Section 4, Example 2);
+                         ``orth_max`` the same without the 1/n.
+* ``subspace_sin_angle`` sine of the largest principal angle between two
+                         column spans (the eigenvector criterion of the tests).
 
 Submodules (plain Python/NumPy): ``partition_oracle`` (Algorithms 3 and 4, the
 restart plan), ``rules_oracle`` (the trapezoid rule), ``reduction_oracle``
@@ -317,6 +323,33 @@ def feast_slice(ab: np.ndarray, lo: float, hi: float, Y0: np.ndarray, *, ne: int
                 bnorm=float(bnorm))
 
 
+# ----------------------------------------------------------------------------- start vectors
+def _splitmix64_array(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 of each uint64 state (Vigna: add 0x9e3779b97f4a7c15, then the mixer),
+    arithmetic modulo 2^64."""
+    z = x.astype(np.uint64) + np.uint64(0x9E3779B97F4A7C15)
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def random_start(n: int, ncols: int, is_complex: bool, seed: int = 0, col0: int = 0) -> np.ndarray:
+    """Start vectors drawn from a counter-based stream (the "random vectors" that start
+    Algorithm 1): entry (i, c) uses word k = (col0 + c) n + i; u(w) = (top 53 bits of
+    splitmix64(w)) 2^-52 - 1 in [-1, 1); real: u(seed + k); complex: u(seed + 2k) + i u(seed + 2k + 1).
+    Returns an n x ncols array (column-major meaning: column c is X[:, c])."""
+    i = np.arange(n, dtype=np.uint64)[:, None]
+    c = np.arange(ncols, dtype=np.uint64)[None, :]
+    k = (np.uint64(col0) + c) * np.uint64(n) + i
+    sd = np.uint64(seed & 0xFFFFFFFFFFFFFFFF)
+    with np.errstate(over="ignore"):
+        def u(w):
+            return (_splitmix64_array(w) >> np.uint64(11)).astype(np.float64) * 2.0 ** -52 - 1.0
+        if not is_complex:
+            return u(sd + k)
+        return u(sd + np.uint64(2) * k) + 1j * u(sd + np.uint64(2) * k + np.uint64(1))
+
+
 # ----------------------------------------------------------------------------- metrics
 def residuals(ab: np.ndarray, lam: np.ndarray, X: np.ndarray, bnorm: float) -> np.ndarray:
     """||B x_i - lambda_i x_i||_2 / (bnorm ||x_i||_2) per column."""
@@ -330,6 +363,14 @@ def orth(X: np.ndarray) -> float:
     X = np.asarray(X)
     G = X.conj().T @ X
     return float(np.max(np.abs(G - np.eye(G.shape[0]))) / X.shape[0])
+
+
+def orth_max(X: np.ndarray) -> float:
+    """||X^H X - I||_max without the 1/n of the paper's Orth: the largest entrywise departure
+    of the Gram matrix from the identity (a validity check that does not shrink with n)."""
+    X = np.asarray(X)
+    G = X.conj().T @ X
+    return float(np.max(np.abs(G - np.eye(G.shape[0]))))
 
 
 def subspace_sin_angle(Xa: np.ndarray, Xb: np.ndarray) -> float:

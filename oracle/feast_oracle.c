@@ -214,7 +214,12 @@ void or_gershgorin(int64_t n, int64_t b, const double* abz, int64_t ldab, double
     double r = 0.0;
     int64_t j0 = i - b < 0 ? 0 : i - b, j1 = i + b > n - 1 ? n - 1 : i + b;
     for (int64_t j = j0; j <= j1; ++j)
-      if (j != i) r += zabs(band_get(ab, ldab, b, i, j));
+      if (j != i) {
+        /* |b_ij| as sqrt(re^2 + im^2) (correctly rounded square root, no FMA), summed in */
+        /* ascending column order: the interval is then a fixed function of the band's bits */
+        const zc v = band_get(ab, ldab, b, i, j);
+        r += sqrt(v.re * v.re + v.im * v.im);
+      }
     double c = ab[i * ldab].re;
     if (c - r < lo) lo = c - r;
     if (c + r > hi) hi = c + r;

@@ -117,7 +117,9 @@ def outer_bounds(ab, d_prev, i0, nev, alpha=1e-3, m_hat=6, max_it=64, inertia=No
 
     d_prev: sorted eigenvalues of the previous matrix of the sequence, covering indices
     i0 .. i0+nev-1 (and one neighbour on each side when they exist).  Returns
-    (b0, bK, it_lo, it_hi): n_-(b0) <= i0 and n_-(bK) >= i0 + nev for the band ``ab``."""
+    (b0, bK, it_lo, it_hi, ok): n_-(b0) <= i0 and n_-(bK) >= i0 + nev for the band ``ab``
+    when ok; ok is False when a search stopped at max_it with its count still short of the
+    target (the bounds then do not enclose the wanted eigenvalues)."""
     if inertia is None:
         from oracle import inertia as _inertia
         inertia = _inertia
@@ -129,9 +131,11 @@ def outer_bounds(ab, d_prev, i0, nev, alpha=1e-3, m_hat=6, max_it=64, inertia=No
         step = 2.0 ** -40 * max(1.0, abs(du))
     bK = du + step
     it_hi = 1
-    while inertia(ab, bK) < i0 + nev and it_hi < max_it:
+    hi_ok = inertia(ab, bK) >= i0 + nev
+    while not hi_ok and it_hi < max_it:
         bK = bK + step
         it_hi += 1
+        hi_ok = inertia(ab, bK) >= i0 + nev
     dl = d[i0]
     delta2 = d[i0 + 1] - dl if i0 + 1 < len(d) else 0.0
     step2 = max(abs(alpha * dl), m_hat * delta2)
@@ -139,10 +143,12 @@ def outer_bounds(ab, d_prev, i0, nev, alpha=1e-3, m_hat=6, max_it=64, inertia=No
         step2 = 2.0 ** -40 * max(1.0, abs(dl))
     b0 = dl - step2
     it_lo = 1
-    while inertia(ab, b0) > i0 and it_lo < max_it:
+    lo_ok = inertia(ab, b0) <= i0
+    while not lo_ok and it_lo < max_it:
         b0 = b0 - step2
         it_lo += 1
-    return b0, bK, it_lo, it_hi
+        lo_ok = inertia(ab, b0) <= i0
+    return b0, bK, it_lo, it_hi, bool(hi_ok and lo_ok)
 
 
 def kmeans_objective(d, bounds):

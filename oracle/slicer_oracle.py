@@ -165,3 +165,26 @@ def adam_step(p, g, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999,
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def equal_count_targets(ab: np.ndarray, nslices: int = 64) -> np.ndarray:
+    """The proposer's regression targets from the exact spectrum (dense eigvalsh of the
+    band): boundary k (k = 1..nslices-1) is the midpoint of eigenvalues t-1 and t,
+    t = floor(k n / nslices + 1/2) clipped to [1, n-1], normalised to the Gershgorin
+    interval and clipped to [0, 1]."""
+    n, ldab = ab.shape
+    A = np.zeros((n, n), dtype=ab.dtype)
+    for d in range(ldab):                       # lower band storage: ab[j, d] = B(j + d, j)
+        j = np.arange(n - d)
+        A[j + d, j] = ab[: n - d, d]
+        if d:
+            A[j, j + d] = np.conj(ab[: n - d, d])
+    ev = np.linalg.eigvalsh(A)
+    lo, hi = gershgorin(ab)
+    span = hi - lo if hi > lo else 1.0
+    out = np.zeros(nslices - 1)
+    for k in range(1, nslices):
+        t = min(max((2 * k * n + nslices) // (2 * nslices), 1), n - 1)
+        out[k - 1] = min(max((0.5 * (ev[t - 1] + ev[t]) - lo) / span, 0.0), 1.0)
+    return out
+

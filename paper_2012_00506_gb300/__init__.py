@@ -57,7 +57,8 @@ EXPORTED = [
     "pdeshep_block_gemm_workspace_size", "pdeshep_block_gemm",
     "pdeshep_band_matmul_tc_workspace_size", "pdeshep_band_matmul_tc",
     "pdeshep_partition", "pdeshep_outer_bounds_workspace_size", "pdeshep_outer_bounds",
-    "pdeshep_restart_plan",
+    "pdeshep_restart_plan", "pdeshep_random_start", "pdeshep_equal_count_targets_workspace_size",
+    "pdeshep_equal_count_targets",
 ]
 
 
@@ -71,8 +72,8 @@ class Opts(C.Structure):
         ("refine_policy", C.c_int32), ("rhs_chunk", C.c_int32), ("ellipse_ratio", C.c_double),
         ("bnorm", C.c_double), ("seed", C.c_uint64), ("hbm_cap_bytes", C.c_size_t),
         ("autotune", C.c_int32), ("verbose", C.c_int32), ("stream", C.c_void_p),
-        ("rr_arith", C.c_int32), ("pad0", C.c_int32), ("tune_cache", C.c_char_p),
-        ("graphs", C.c_int32), ("pad1", C.c_int32),
+        ("rr_arith", C.c_int32), ("m0_resize", C.c_int32), ("tune_cache", C.c_char_p),
+        ("graphs", C.c_int32), ("m0_cap", C.c_int32), ("h_m0_used", C.c_void_p),
     ]
 
 
@@ -150,6 +151,9 @@ def load(path: str = LIB_PATH):
         "pdeshep_band_matmul_tc": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P, sz, P]),
         "pdeshep_partition": (C.c_int, [i32, i64, P, i32, dbl, dbl, i32, P, P, P, P]),
         "pdeshep_restart_plan": (C.c_int, [i64, P, i32, P, P, i32, P]),
+        "pdeshep_random_start": (C.c_int, [i64, i32, i64, i32, C.c_uint64, P, P]),
+        "pdeshep_equal_count_targets_workspace_size": (sz, [i64, i32, i32, i32, i32]),
+        "pdeshep_equal_count_targets": (C.c_int, [i64, i32, i32, P, i64, i32, dbl, i32, P, P, sz, P]),
         "pdeshep_outer_bounds_workspace_size": (sz, [i64, i32, i32]),
         "pdeshep_outer_bounds": (C.c_int, [i64, i32, i32, P, i64, i64, P, i64, i64, dbl, dbl, i32, P, P, P, P, sz,
                                            P]),
@@ -379,8 +383,9 @@ def restart_plan(prev_vals, bounds, m0, mode=0):
 
 
 def outer_bounds(band, prev, i0, nev, alpha=1e-3, m_hat=6.0, max_it=64, b=None, stream=None):
-    """(b0, bK, (counts taken for b0, for bK)) enclosing the wanted eigenvalues i0..i0+nev-1
-    of the band, searched from the previous eigenvalues ``prev`` (Algorithm 4)."""
+    """(b0, bK, (counts taken for b0, for bK), ok) enclosing the wanted eigenvalues
+    i0..i0+nev-1 of the band, searched from the previous eigenvalues ``prev`` (Algorithm 4);
+    ok is False when a search stopped at max_it short of its target (PDESHEP_NOT_CONVERGED)."""
     lib = load()
     n, b, cplx, ldab = _band_args(band, b)
     d = np.ascontiguousarray(np.sort(np.asarray(prev, dtype=np.float64)))
@@ -391,8 +396,9 @@ def outer_bounds(band, prev, i0, nev, alpha=1e-3, m_hat=6.0, max_it=64, b=None, 
     st = lib.pdeshep_outer_bounds(n, b, cplx, _ptr(band), ldab, d.size, _np_ptr(d), int(i0), int(nev), float(alpha),
                                   float(m_hat), int(max_it), C.byref(b0), C.byref(bK), _np_ptr(iters), _ptr(ws),
                                   ws.numel(), _stream(stream))
-    _check("pdeshep_outer_bounds", st)
-    return b0.value, bK.value, (int(iters[0]), int(iters[1]))
+    if st != 1:
+        _check("pdeshep_outer_bounds", st)
+    return b0.value, bK.value, (int(iters[0]), int(iters[1])), st == 0
 
 
 def band_matmul_tc(band, X, b=None, stream=None):
@@ -491,21 +497,41 @@ class SliceResult:
     nfound: np.ndarray
     stats: dict = field(default_factory=dict)
     m0: np.ndarray = None
+    block: int = 0        # columns per slice block (m0_resize mode); 0: blocks of m0[i] columns
+
+    def offset(self, i):
+        """First row of slice i's block in evals / evecs."""
+        return i * self.block if self.block else int(np.sum(self.m0[:i]))
 
     def slice_pairs(self, i):
         """(eigenvalues, eigenvectors (k, n)) of the converged pairs of slice i."""
-        off = int(np.sum(self.m0[:i]))
+        off = self.offset(i)
         k = int(self.nfound[i])
         return self.evals[off: off + k], self.evecs[off: off + k]
+
+
+def random_start(n, ncols, is_complex, seed=0, col0=0, device=None, stream=None):
+    """Columns col0 .. col0+ncols-1 of the library's start-vector stream, as a tensor (ncols, n)
+    (the vectors pdeshep_band_slice draws when it is given no start vectors)."""
+    torch = _torch()
+    lib = load()
+    dt = torch.complex128 if is_complex else torch.float64
+    x = torch.empty((ncols, n), dtype=dt, device=device)
+    st = lib.pdeshep_random_start(int(n), int(bool(is_complex)), int(col0), int(ncols), C.c_uint64(seed), _ptr(x),
+                                  _stream(stream))
+    _check("pdeshep_random_start", st)
+    return x
 
 
 def band_slice(band, bounds, m0, x0, ne=8, nodes=None, weights=None, workspace=None, stream=None,
                b=None, raise_on_error=True, **opts) -> SliceResult:
     """FEAST on every slice [bounds[i], bounds[i+1]) (Algorithm 1 per slice).
 
-    ``x0``: start vectors, tensor (sum(m0), n) of the band's dtype.  Options:
-    any ``Opts`` field (tol, max_iter, precision, refine_policy, ellipse_ratio, bnorm,
-    hbm_cap_bytes, ...).
+    ``x0``: start vectors, tensor (sum(m0), n) of the band's dtype, or None (drawn by the
+    library from ``seed``).  With ``m0_resize=1`` and ``m0_cap``: blocks of ``m0_cap`` columns
+    per slice (x0 of shape (K * m0_cap, n)), m0 enlarged by the library where the exact count
+    asks for it; the m0 used is in ``result.m0``.  Options: any ``Opts`` field (tol, max_iter,
+    precision, refine_policy, ellipse_ratio, bnorm, hbm_cap_bytes, seed, ...).
     """
     torch = _torch()
     lib = load()
@@ -516,8 +542,12 @@ def band_slice(band, bounds, m0, x0, ne=8, nodes=None, weights=None, workspace=N
     assert m.size == K
     o = default_opts(**opts)
     o.stream = _stream(stream).value
-    x0 = x0.to(band.dtype).contiguous()
-    assert x0.shape == (int(m.sum()), n)
+    m_used = np.zeros(K, dtype=np.int32)
+    o.h_m0_used = m_used.ctypes.data
+    ncol = K * int(o.m0_cap) if o.m0_resize else int(m.sum())
+    if x0 is not None:
+        x0 = x0.to(band.dtype).contiguous()
+        assert x0.shape == (ncol, n)
     if nodes is not None:
         nz = np.ascontiguousarray(np.asarray(nodes, dtype=np.complex128).reshape(-1))
         nw = np.ascontiguousarray(np.asarray(weights, dtype=np.complex128).reshape(-1))
@@ -526,16 +556,20 @@ def band_slice(band, bounds, m0, x0, ne=8, nodes=None, weights=None, workspace=N
         nz = nw = None
     if workspace is None:
         workspace = _workspace(lib.pdeshep_workspace_size(n, b, cplx, K, _np_ptr(m), ne, C.byref(o)), band.device)
-    evals = torch.empty(int(m.sum()), dtype=torch.float64, device=band.device)
-    evecs = torch.empty_like(x0)
+    evals = torch.empty(ncol, dtype=torch.float64, device=band.device)
+    evecs = torch.empty((ncol, n), dtype=band.dtype, device=band.device)
     counts = np.zeros(K, dtype=np.int32)
     nfound = np.zeros(K, dtype=np.int32)
     stats = Stats()
     st = lib.pdeshep_band_slice(n, b, cplx, _ptr(band), ldab, K, _np_ptr(bnd), int(ne),
                                 _np_ptr(nz) if nz is not None else None,
-                                _np_ptr(nw) if nw is not None else None, _np_ptr(m), _ptr(x0),
+                                _np_ptr(nw) if nw is not None else None, _np_ptr(m),
+                                _ptr(x0) if x0 is not None else None,
                                 _ptr(workspace), workspace.numel(), C.byref(o), _ptr(evals), _ptr(evecs),
                                 _np_ptr(counts), _np_ptr(nfound), C.byref(stats))
     if st != 0 and (raise_on_error and st not in (1,)):
         _check("pdeshep_band_slice", st)
-    return SliceResult(st, evals, evecs, counts, nfound, stats.as_dict(), m)
+    res = SliceResult(st, evals, evecs, counts, nfound, stats.as_dict(), m_used if st >= 0 else m)
+    if o.m0_resize:
+        res.block = int(o.m0_cap)
+    return res

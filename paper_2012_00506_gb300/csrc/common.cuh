@@ -53,6 +53,22 @@ unsigned long long launches_so_far();
 // workspace arena: carves 256-byte aligned sub-buffers out of the caller's
 // device workspace.  With base == nullptr it only measures.
 // ----------------------------------------------------------------------------
+// SplitMix64 (Vigna): the state advanced by the golden-ratio increment, then
+// mixed.  Counter-based use: value k of a stream is splitmix64(seed + k).
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  uint64_t z = x;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Uniform double in [-1, 1) from the top 53 bits of a 64-bit word (exact: the
+// 53-bit integer times 2^-52 minus 1 rounds nowhere).
+__host__ __device__ inline double uniform_pm1(uint64_t v) {
+  return (double)(int64_t)(v >> 11) * 0x1p-52 - 1.0;
+}
+
 struct Arena {
   char* base;
   size_t cap;

@@ -50,10 +50,11 @@ size_t bisect_ws_bytes(int b, int cplx, int nidx, int fanout);
 
 // Column block of one slice in the n x sum(m0) arrays.
 struct SliceDesc {
-  int64_t col_off;
+  int64_t col_off;  // first column of the slice in the internal n x M arrays
   int m0;
   int slice;
   double lo, hi;
+  int64_t io_off;   // first column of the slice's block in d_x0 / d_evals / d_evecs
 };
 
 // Node range [j0, j1) of one slice inside a wave of systems.
@@ -89,6 +90,27 @@ __global__ void make_rhs_kernel(int64_t n, const SliceDesc* sd, const S* __restr
       v.y = (typename real_of<C>::type)(a.y * s);
     }
     Y[i + c * n] = v;
+  }
+}
+
+// Library-drawn start vectors: entry (i, c) of the slice block whose output
+// column is io_off + c takes word k = (io_off + c) n + i of the SplitMix64
+// stream: real bands uniform_pm1(splitmix64(seed + k)); complex bands
+// re = uniform_pm1(splitmix64(seed + 2k)), im = uniform_pm1(splitmix64(seed + 2k + 1)).
+template <typename S>
+__global__ void random_start_kernel(int64_t n, const SliceDesc* sd, uint64_t seed, S* __restrict__ X) {
+  const SliceDesc d = sd[blockIdx.y];
+  const int64_t total = n * d.m0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / n, i = e % n;
+    const uint64_t k = (uint64_t)((d.io_off + c) * n + i);
+    if constexpr (std::is_same<S, double>::value) {
+      X[i + (d.col_off + c) * n] = uniform_pm1(splitmix64(seed + k));
+    } else {
+      X[i + (d.col_off + c) * n] =
+          make_double2(uniform_pm1(splitmix64(seed + 2 * k)), uniform_pm1(splitmix64(seed + 2 * k + 1)));
+    }
   }
 }
 
@@ -314,7 +336,7 @@ __global__ void nconv_kernel(const SliceDesc* sd, const double* lam, const doubl
 
 // destination of each Ritz pair: converged in-slice pairs first (ascending), then the rest.
 __global__ void order_kernel(const SliceDesc* sd, const double* lam, const double* res, double tol,
-                             int* dest) {
+                             int64_t* dest) {
   const SliceDesc d = sd[blockIdx.x];
   int ngood = 0;
   for (int c = 0; c < d.m0; ++c) {
@@ -330,12 +352,12 @@ __global__ void order_kernel(const SliceDesc* sd, const double* lam, const doubl
       const int g2 = (l2 >= d.lo && l2 < d.hi && res[d.col_off + c2] <= tol);
       before += (g2 == good);
     }
-    dest[d.col_off + c] = (int)d.col_off + (good ? before : ngood + before);
+    dest[d.col_off + c] = d.io_off + (good ? before : ngood + before);
   }
 }
 
 template <typename S>
-__global__ void scatter_out_kernel(int64_t n, int64_t M, const int* dest, const double* lam, const S* X,
+__global__ void scatter_out_kernel(int64_t n, int64_t M, const int64_t* dest, const double* lam, const S* X,
                                    double* evals, S* evecs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * M;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -382,7 +404,7 @@ struct Plan {
   int* sweeps;     // K
   int* sweeps32;   // K
   int* nconv;      // K
-  int* dest;       // M
+  int64_t* dest;   // M (output column of each Ritz pair)
   int* sys_status; // max systems
   double* jscratch;// K * 2 * 16
   SliceDesc* d_sd; // K
@@ -495,6 +517,7 @@ struct Feast {
   std::vector<int> m0;
   std::vector<int64_t> col_off;
   std::vector<int64_t> small_off;
+  std::vector<int64_t> io_col;  // first column of each slice's block in d_x0 / d_evals / d_evecs
   int64_t M, Msq;
   int max_m0;
   const pdeshep_opts* o;
@@ -542,7 +565,7 @@ struct Feast {
     q.sweeps = a.take<int>(K);
     q.sweeps32 = a.take<int>(K);
     q.nconv = a.take<int>(K);
-    q.dest = a.take<int>(M);
+    q.dest = a.take<int64_t>(M);
     q.sys_status = a.take<int>((size_t)K * ne);
     q.jscratch = a.take<double>((size_t)K * 2 * 16);
     q.d_sd = a.take<SliceDesc>(K);
@@ -635,7 +658,7 @@ struct FeastRun : Feast<S, C> {
     this->h_small.resize(na);
     for (int a = 0; a < na; ++a) {
       const int s = active[a];
-      h_sd[a] = SliceDesc{col_off[s], m0[s], s, bounds[s], bounds[s + 1]};
+      h_sd[a] = SliceDesc{col_off[s], m0[s], s, bounds[s], bounds[s + 1], this->io_col[s]};
       this->h_small[a] = SmallDesc{small_off[s], col_off[s], m0[s], 0};
     }
     PD_CK(cudaMemcpyAsync(p.d_sd, h_sd.data(), sizeof(SliceDesc) * na, cudaMemcpyHostToDevice, st));
@@ -1220,9 +1243,15 @@ using namespace pdeshep;
 
 namespace {
 
+// One batch of slices whose factors are planned together (all resident in the
+// workspace, or streamed in waves when they do not fit).  h_io_col[s]: first
+// column of slice s's block in d_x0 / d_evals / d_evecs (NULL: packed by m0).
+// h_known_neg: exact counts below h_bounds[0..K] when the caller already has
+// them (NULL: counted here on a side stream beside the first filter pass).
 template <typename S, typename C>
 int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int K, const double* h_bounds,
                 int ne, const pdeshep_c128* h_nodes, const pdeshep_c128* h_weights, const int32_t* h_m0,
+                const int64_t* h_io_col, const int64_t* h_known_neg,
                 const void* d_x0, void* d_work, size_t work_bytes, const pdeshep_opts* o, double* d_evals,
                 void* d_evecs, int32_t* h_counts, int32_t* h_nfound, pdeshep_stats* h_stats, size_t* size_only) {
   FeastRun<S, C> F;
@@ -1254,6 +1283,7 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   }
   F.M = acc;
   F.Msq = accs;
+  F.io_col = h_io_col ? std::vector<int64_t>(h_io_col, h_io_col + K) : F.col_off;
   memset(&F.stats, 0, sizeof(F.stats));
   F.setup_tuning();
   // workspace plan
@@ -1298,14 +1328,16 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   // filter pass and are read back with the first Rayleigh-Ritz results; a slice
   // whose subspace is smaller than its count is reported after that pass.
   SideStream side;
-  PD_TRY(side.fork(st));
   const int64_t* d_neg = nullptr;
   const int* d_bad = nullptr;
-  PD_CK(cudaEventRecord(side.t0, side.s));
-  PD_TRY(inertia_counts_async(n, b, cplx, band, ldab, K + 1, h_bounds, F.p.inertia_ws, F.p.inertia_bytes, side.s,
-                              &d_neg, &d_bad));
-  PD_CK(cudaEventRecord(side.t1, side.s));
-  PD_TRY(side.join(st));
+  if (!h_known_neg) {
+    PD_TRY(side.fork(st));
+    PD_CK(cudaEventRecord(side.t0, side.s));
+    PD_TRY(inertia_counts_async(n, b, cplx, band, ldab, K + 1, h_bounds, F.p.inertia_ws, F.p.inertia_bytes,
+                                side.s, &d_neg, &d_bad));
+    PD_CK(cudaEventRecord(side.t1, side.s));
+    PD_TRY(side.join(st));
+  }
   const long long inertia_launches = 2;
   if (F.ff()) {
     PD_TRY(F.kt.begin(PDESHEP_KG_BANDMM));
@@ -1321,6 +1353,16 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   bool counts_ready = false;
   auto read_counts = [&]() -> int {
     if (counts_ready) return 0;
+    if (h_known_neg) {
+      counts_ready = true;
+      for (int s = 0; s < K; ++s) {
+        F.counts[s] = (int)(h_known_neg[s + 1] - h_known_neg[s]);
+        if (h_counts) h_counts[s] = F.counts[s];
+      }
+      for (int s = 0; s < K; ++s)
+        if (F.m0[s] < F.counts[s]) return PDESHEP_COUNT_MISMATCH;
+      return 0;
+    }
     std::vector<int64_t> neg(K + 1);
     int bad = 0;
     PD_CK(cudaStreamWaitEvent(st, side.done, 0));
@@ -1363,11 +1405,25 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
       }
     PD_CK(cudaMemcpyAsync(F.p.zw, zw.data(), sizeof(double2) * zw.size(), cudaMemcpyHostToDevice, st));
   }
-  PD_CK(cudaMemcpyAsync(F.p.Xt, d_x0, sizeof(S) * (size_t)(n * F.M), cudaMemcpyDeviceToDevice, st));
   F.mode = (o->precision == PDESHEP_MIXED && o->refine_policy == PDESHEP_REFINE_RESIDUAL) ? 1 : 0;
   std::vector<int> done(K, 0);
   F.active.clear();
   for (int s = 0; s < K; ++s) F.active.push_back(s);
+  // start vectors: the caller's blocks, or drawn here (counter-based SplitMix64 stream)
+  bool packed = true;
+  for (int s = 0; s < K; ++s) packed = packed && F.io_col[s] == F.io_col[0] + F.col_off[s];
+  if (d_x0 && packed) {
+    PD_CK(cudaMemcpyAsync(F.p.Xt, (const S*)d_x0 + F.io_col[0] * n, sizeof(S) * (size_t)(n * F.M),
+                          cudaMemcpyDeviceToDevice, st));
+  } else if (d_x0) {
+    for (int s = 0; s < K; ++s)
+      PD_CK(cudaMemcpyAsync((S*)F.p.Xt + F.col_off[s] * n, (const S*)d_x0 + F.io_col[s] * n,
+                            sizeof(S) * (size_t)(n * F.m0[s]), cudaMemcpyDeviceToDevice, st));
+  } else {
+    PD_TRY(F.upload_active());
+    random_start_kernel<S><<<dim3(grid1(n * F.max_m0), K), 256, 0, st>>>(n, F.p.d_sd, o->seed, (S*)F.p.Xt);
+    PD_CK_LAUNCH();
+  }
   int status = 0;
   double ms_filter = 0, ms_rr = 0;
   auto timed = [&](double& acc_ms, auto&& fn) -> int {
@@ -1486,9 +1542,162 @@ int check_slice_args(int64_t n, int32_t b, const void* d_band, int64_t ldab, int
             (o->rhs_chunk != 0 && o->rhs_chunk != 16 && o->rhs_chunk != 32 && o->rhs_chunk != 64) ||
             (o->rr_arith != PDESHEP_RR_FLOATFLOAT && o->rr_arith != PDESHEP_RR_FP64 &&
              o->rr_arith != PDESHEP_RR_TENSOR) || o->autotune < 0 ||
-            o->autotune > 2))
+            o->autotune > 2 || (o->m0_resize != 0 && o->m0_resize != 1)))
     return -15;
+  if (o && o->m0_resize) {
+    if (o->m0_cap < 1 || o->m0_cap > n || o->m0_cap > 4096) return -15;
+    for (int s = 0; s < K; ++s)
+      if (h_m0[s] > o->m0_cap) return -11;
+  }
   return 0;
+}
+
+void merge_stats(pdeshep_stats& t, const pdeshep_stats& g) {
+  t.iterations = std::max(t.iterations, g.iterations);
+  t.waves += g.waves;
+  t.factorizations += g.factorizations;
+  t.rhs_sweeps += g.rhs_sweeps;
+  t.ms_inertia += g.ms_inertia;
+  t.ms_factor += g.ms_factor;
+  t.ms_solve += g.ms_solve;
+  t.ms_rr += g.ms_rr;
+  t.ms_total += g.ms_total;
+  t.max_residual = std::max(t.max_residual, g.max_residual);
+  for (int i = 0; i < PDESHEP_KG_COUNT; ++i) {
+    t.kg_ms[i] += g.kg_ms[i];
+    t.kg_launches[i] += g.kg_launches[i];
+    t.kg_flops[i] += g.kg_flops[i];
+  }
+  t.rhs_columns += g.rhs_columns;
+  t.cluster_ctas = std::max(t.cluster_ctas, g.cluster_ctas);
+  t.jacobi_sweeps64 += g.jacobi_sweeps64;
+  t.jacobi_sweeps32 += g.jacobi_sweeps32;
+  t.rr_calls += g.rr_calls;
+  t.eig_refine_steps += g.eig_refine_steps;
+  t.eig_clusters += g.eig_clusters;
+  t.eig_max_cluster = std::max(t.eig_max_cluster, g.eig_max_cluster);
+  t.eig_fallback_unconverged += g.eig_fallback_unconverged;
+  t.eig_fallback_wide += g.eig_fallback_wide;
+  t.rhs_chunk_used = g.rhs_chunk_used;
+  t.gram_splits_used = g.gram_splits_used;
+  t.tuned += g.tuned;
+  t.graph_launches += g.graph_launches;
+  t.cholqr_shifted += g.cholqr_shifted;
+  t.gram_fp64 += g.gram_fp64;
+  if (g.rr_fp64_from && (!t.rr_fp64_from || g.rr_fp64_from < t.rr_fp64_from)) t.rr_fp64_from = g.rr_fp64_from;
+}
+
+// The whole call.  (1) With opts.m0_resize, the exact counts m_i come first and
+// a slice whose m0 is below m_i + 10 runs with max(ceil(1.3 m_i), m_i + 10)
+// columns (at most opts.m0_cap), the subspace rule of Section 3.2 applied by
+// the library instead of a failed run and a rerun.  (2) The slices are run in
+// consecutive groups whose factorizations all stay resident in the workspace
+// (and, with hbm_cap_bytes, within that cap), each group iterating to
+// convergence on factors computed once: the paper's level L1 (slices) becomes
+// the sequence of groups.  A call that fits whole is one group.  A slice whose
+// own factors exceed the budget forms a group that streams its factors in
+// waves every iteration.
+template <typename S, typename C>
+int band_slice_run(int64_t n, int b, int cplx, const void* band, int64_t ldab, int K, const double* h_bounds,
+                   int ne, const pdeshep_c128* h_nodes, const pdeshep_c128* h_weights, const int32_t* h_m0,
+                   const void* d_x0, void* d_work, size_t work_bytes, const pdeshep_opts* o, double* d_evals,
+                   void* d_evecs, int32_t* h_counts, int32_t* h_nfound, pdeshep_stats* h_stats, size_t* size_only) {
+  const bool resize = o->m0_resize != 0;
+  cudaStream_t st = (cudaStream_t)o->stream;
+  std::vector<int32_t> m0(h_m0, h_m0 + K);
+  std::vector<int64_t> io(K, 0);
+  for (int s = 1; s < K; ++s) io[s] = resize ? (int64_t)s * o->m0_cap : io[s - 1] + m0[s - 1];
+  std::vector<int64_t> neg;
+  if (resize) {
+    if (size_only) {
+      for (int s = 0; s < K; ++s) m0[s] = o->m0_cap;  // the largest subspaces the call may use
+    } else {
+      neg.assign(K + 1, 0);
+      if (work_bytes < inertia_ws_bytes(b, cplx, K + 1)) return PDESHEP_WORKSPACE_TOO_SMALL;
+      bool bad = false;
+      PD_TRY(inertia_counts(n, b, cplx, band, ldab, K + 1, h_bounds, neg.data(), nullptr, d_work, work_bytes, st,
+                            &bad));
+      if (bad) return PDESHEP_NONFINITE_INPUT;
+      bool short_cap = false;
+      for (int s = 0; s < K; ++s) {
+        const int64_t m = neg[s + 1] - neg[s];
+        if (h_counts) h_counts[s] = (int32_t)m;
+        if (m0[s] < m + 10) m0[s] = (int32_t)std::max<int64_t>((13 * m + 9) / 10, m + 10);
+        m0[s] = std::min(m0[s], o->m0_cap);
+        if (m0[s] < m) short_cap = true;
+      }
+      if (o->h_m0_used)
+        for (int s = 0; s < K; ++s) o->h_m0_used[s] = m0[s];
+      if (short_cap) return PDESHEP_COUNT_MISMATCH;
+    }
+  } else if (o->h_m0_used && !size_only) {
+    for (int s = 0; s < K; ++s) o->h_m0_used[s] = m0[s];
+  }
+  // workspace of a group of slices [s0, s1) with all factors resident
+  auto resident_bytes = [&](int s0, int s1) -> size_t {
+    pdeshep_opts og = *o;
+    og.hbm_cap_bytes = 0;
+    size_t sz = 0;
+    feast_entry<S, C>(n, b, cplx, nullptr, ldab, s1 - s0, nullptr, ne, nullptr, nullptr, m0.data() + s0, nullptr,
+                      nullptr, nullptr, nullptr, 0, &og, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
+    return sz;
+  };
+  const FactorGeom g = make_geom(n, b);
+  const size_t fb = factor_bytes(g, sizeof(C));
+  auto sys_bytes = [&](int s0, int s1) -> size_t {
+    size_t t = 0;
+    for (int s = s0; s < s1; ++s)
+      t += (size_t)ne * (fb + (((size_t)n * m0[s] * (cplx ? 2 : 1) * sizeof(C) + 255) & ~size_t(255)));
+    return t;
+  };
+  const size_t cap = o->hbm_cap_bytes;
+  const size_t budget = size_only ? ~size_t(0) : work_bytes;
+  auto fits = [&](int s0, int s1) {
+    return (cap == 0 || sys_bytes(s0, s1) <= cap) && resident_bytes(s0, s1) <= budget;
+  };
+  std::vector<std::pair<int, int>> groups;
+  if (fits(0, K)) {
+    groups.push_back({0, K});
+  } else {
+    int s0 = 0;
+    while (s0 < K) {
+      int s1 = s0 + 1;
+      if (fits(s0, s1))
+        while (s1 < K && fits(s0, s1 + 1)) ++s1;
+      groups.push_back({s0, s1});
+      s0 = s1;
+    }
+  }
+  if (size_only) {
+    size_t mx = 0;
+    for (auto& gr : groups) {
+      size_t sz = 0;
+      PD_TRY((feast_entry<S, C>(n, b, cplx, nullptr, ldab, gr.second - gr.first, nullptr, ne, nullptr, nullptr,
+                                m0.data() + gr.first, nullptr, nullptr, nullptr, nullptr, 0, o, nullptr, nullptr,
+                                nullptr, nullptr, nullptr, &sz)));
+      mx = std::max(mx, sz);
+    }
+    *size_only = std::max(mx, resize ? inertia_ws_bytes(b, cplx, K + 1) : size_t(0));
+    return 0;
+  }
+  pdeshep_stats total;
+  memset(&total, 0, sizeof(total));
+  int status = 0;
+  for (auto& gr : groups) {
+    const int s0 = gr.first, kg = gr.second - gr.first;
+    pdeshep_stats gs;
+    const int r = feast_entry<S, C>(n, b, cplx, band, ldab, kg, h_bounds + s0, ne,
+                                    h_nodes ? h_nodes + (size_t)s0 * ne : nullptr,
+                                    h_weights ? h_weights + (size_t)s0 * ne : nullptr, m0.data() + s0,
+                                    io.data() + s0, resize ? neg.data() + s0 : nullptr, d_x0, d_work, work_bytes, o,
+                                    d_evals, d_evecs, h_counts ? h_counts + s0 : nullptr,
+                                    h_nfound ? h_nfound + s0 : nullptr, h_stats ? &gs : nullptr, nullptr);
+    if (r != 0 && r != PDESHEP_NOT_CONVERGED) return r;
+    if (r) status = r;
+    if (h_stats) merge_stats(total, gs);
+  }
+  if (h_stats) *h_stats = total;
+  return status;
 }
 
 }  // namespace
@@ -1499,22 +1708,23 @@ extern "C" size_t pdeshep_workspace_size(int64_t n, int32_t b, int32_t is_comple
   pdeshep_opts_default(&def);
   const pdeshep_opts* o = opts ? opts : &def;
   if (n <= 0 || b < 0 || nslices <= 0 || !h_m0 || ne < 1) return 0;
+  if (o->m0_resize && (o->m0_cap < 1 || o->m0_cap > 4096)) return 0;
   size_t sz = 0;
   int r;
   if (is_complex) {
     if (o->precision == PDESHEP_MIXED)
-      r = feast_entry<double2, float2>(n, b, 1, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
-                                       nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
+      r = band_slice_run<double2, float2>(n, b, 1, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
+                                          nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
     else
-      r = feast_entry<double2, double2>(n, b, 1, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
-                                        nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
+      r = band_slice_run<double2, double2>(n, b, 1, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
+                                           nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
   } else {
     if (o->precision == PDESHEP_MIXED)
-      r = feast_entry<double, float2>(n, b, 0, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
-                                      nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
+      r = band_slice_run<double, float2>(n, b, 0, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
+                                         nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
     else
-      r = feast_entry<double, double2>(n, b, 0, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
-                                       nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
+      r = band_slice_run<double, double2>(n, b, 0, nullptr, b + 1, nslices, nullptr, ne, nullptr, nullptr, h_m0,
+                                          nullptr, nullptr, 0, o, nullptr, nullptr, nullptr, nullptr, nullptr, &sz);
   }
   return r ? 0 : sz;
 }
@@ -1529,22 +1739,56 @@ extern "C" int pdeshep_band_slice(int64_t n, int32_t b, int32_t is_complex, cons
   const pdeshep_opts* o = opts ? opts : &def;
   int r = check_slice_args(n, b, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0, opts);
   if (r) return r;
-  if (!d_x0) return -12;
   if (!d_work) return -13;
   if (!d_evals) return -16;
   if (!d_evecs) return -17;
   if (is_complex) {
     if (o->precision == PDESHEP_MIXED)
-      return feast_entry<double2, float2>(n, b, 1, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0,
-                                          d_x0, d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound, h_stats,
-                                          nullptr);
-    return feast_entry<double2, double2>(n, b, 1, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0,
-                                         d_x0, d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound, h_stats,
-                                         nullptr);
+      return band_slice_run<double2, float2>(n, b, 1, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0,
+                                             d_x0, d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound,
+                                             h_stats, nullptr);
+    return band_slice_run<double2, double2>(n, b, 1, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0,
+                                            d_x0, d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound,
+                                            h_stats, nullptr);
   }
   if (o->precision == PDESHEP_MIXED)
-    return feast_entry<double, float2>(n, b, 0, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0, d_x0,
-                                       d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound, h_stats, nullptr);
-  return feast_entry<double, double2>(n, b, 0, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0, d_x0,
-                                      d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound, h_stats, nullptr);
+    return band_slice_run<double, float2>(n, b, 0, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0,
+                                          d_x0, d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound, h_stats,
+                                          nullptr);
+  return band_slice_run<double, double2>(n, b, 0, d_band, ldab, nslices, h_bounds, ne, h_nodes, h_weights, h_m0,
+                                         d_x0, d_work, work_bytes, o, d_evals, d_evecs, h_counts, h_nfound, h_stats,
+                                         nullptr);
+}
+
+namespace {
+template <typename S>
+__global__ void random_block_kernel(int64_t n, int64_t col0, int ncols, uint64_t seed, S* __restrict__ X) {
+  const int64_t total = n * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / n, i = e % n;
+    const uint64_t k = (uint64_t)((col0 + c) * n + i);
+    if constexpr (std::is_same<S, double>::value)
+      X[e] = uniform_pm1(splitmix64(seed + k));
+    else
+      X[e] = make_double2(uniform_pm1(splitmix64(seed + 2 * k)), uniform_pm1(splitmix64(seed + 2 * k + 1)));
+  }
+}
+}  // namespace
+
+extern "C" int pdeshep_random_start(int64_t n, int32_t is_complex, int64_t col0, int32_t ncols, uint64_t seed,
+                                    void* d_x, void* stream) {
+  if (n <= 0) return -1;
+  if (col0 < 0) return -3;
+  if (ncols < 0) return -4;
+  if (!d_x && ncols > 0) return -6;
+  if (ncols == 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = grid1(n * ncols);
+  if (is_complex)
+    random_block_kernel<double2><<<blocks, 256, 0, st>>>(n, col0, ncols, seed, (double2*)d_x);
+  else
+    random_block_kernel<double><<<blocks, 256, 0, st>>>(n, col0, ncols, seed, (double*)d_x);
+  PD_CK_LAUNCH();
+  return 0;
 }

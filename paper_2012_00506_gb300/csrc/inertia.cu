@@ -18,7 +18,6 @@
 // and only the real part applied on the diagonal.
 #include <float.h>
 
-#include <mutex>
 
 #include "common.cuh"
 
@@ -309,28 +308,29 @@ __global__ void gershgorin_kernel(int64_t n, int b, int cplx, const double* __re
   double lo = INFINITY, hi = -INFINITY;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
+    // Row i of the Hermitian band in ascending column order, |b_ij| = sqrt(re^2 + im^2)
+    // rounded step by step (no FMA): the interval is a fixed function of the band's bits,
+    // so bin decisions taken against it (the proposer's histogram) are reproducible.
     double r = 0.0;
-    // entries below the diagonal in column i: B(i+d, i), d = 1..b
-    for (int d = 1; d <= b && i + d < n; ++d) {
+    const int64_t j0 = i - b < 0 ? 0 : i - b, j1 = i + b > n - 1 ? n - 1 : i + b;
+    for (int64_t j = j0; j <= j1; ++j) {
+      if (j == i) continue;
+      // B(i, j) for j < i is stored in column j at row offset i - j; for j > i it is
+      // conj(B(j, i)), stored in column i at offset j - i (the modulus ignores the conjugate)
+      const int64_t e = j < i ? (i - j) + j * ldab : (j - i) + i * ldab;
+      double a;
       if (cplx) {
-        const double* p = band + 2 * (d + i * ldab);
-        r += hypot(p[0], p[1]);
+        const double re = band[2 * e], im = band[2 * e + 1];
+        a = __dsqrt_rn(__dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im)));
       } else {
-        r += fabs(band[d + i * ldab]);
+        const double re = band[e];
+        a = __dsqrt_rn(__dmul_rn(re, re));
       }
-    }
-    // entries left of the diagonal in row i: B(i, i-d) stored in column i-d
-    for (int d = 1; d <= b && i - d >= 0; ++d) {
-      if (cplx) {
-        const double* p = band + 2 * (d + (i - d) * ldab);
-        r += hypot(p[0], p[1]);
-      } else {
-        r += fabs(band[d + (i - d) * ldab]);
-      }
+      r = __dadd_rn(r, a);
     }
     double c = cplx ? band[2 * (i * ldab)] : band[i * ldab];
-    lo = fmin(lo, c - r);
-    hi = fmax(hi, c + r);
+    lo = fmin(lo, __dsub_rn(c, r));
+    hi = fmax(hi, __dadd_rn(c, r));
   }
   __shared__ double slo[32], shi[32];
   for (int o = 16; o > 0; o >>= 1) {
@@ -381,30 +381,18 @@ size_t gershgorin_ws_doubles() { return 2 * kGershBlocks; }
 // the shifts and the counts) lives in a fixed device array that every GPU
 // loading this library holds until the process exits; the LDL^T window must
 // then fit in shared memory.  Host code cannot use the array's name as a
-// device address, so the address is looked up once per device with
-// cudaGetSymbolAddress (on the first call made on that device).
+// device address, so every call looks the address up on the current device
+// with cudaGetSymbolAddress (cheap next to the synchronous inertia launch; no
+// cached pointer can outlive a cudaDeviceReset or a change of context).
 // ---------------------------------------------------------------------------
 constexpr int kNoAllocMaxSigma = 1024;
 constexpr size_t kNoAllocBytes = 20 * 1024;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[256] = {};
-
 static int noalloc_scratch_address(void** out) {
-  int dev = 0;
-  PD_CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 256) {
-    set_last_error_msg("pdeshep_inertia_noalloc: device ordinal out of range");
-    return PDESHEP_CUDA_ERROR;
-  }
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    PD_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_addr[dev] = p;
-  }
-  *out = g_noalloc_addr[dev];
+  void* p = nullptr;
+  PD_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  *out = p;
   return 0;
 }
 
@@ -417,7 +405,11 @@ extern "C" int pdeshep_inertia_noalloc(int64_t n, int32_t b, int32_t is_complex,
                                        int64_t* h_neg, void* stream) {
   if (n < 0) return -1;
   const int cplx = is_complex ? 1 : 0;
-  if (b < 0 || !window_in_smem(b, cplx)) {
+  if (b < 0) {
+    set_last_error_msg("pdeshep_inertia_noalloc: negative semi-bandwidth");
+    return -2;
+  }
+  if (!window_in_smem(b, cplx)) {
     set_last_error_msg("pdeshep_inertia_noalloc: band too wide for the shared-memory window "
                        "(real b <= 141, complex b <= 105)");
     return -2;

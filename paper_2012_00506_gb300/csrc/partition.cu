@@ -211,10 +211,12 @@ extern "C" int pdeshep_outer_bounds(int64_t n, int32_t b, int32_t is_complex, co
   if (!(step > 0.0)) step = ldexp(1.0, -40) * std::max(1.0, fabs(du));
   double bK = du + step;
   int it_hi = 1;
+  bool hi_ok = false;
   for (;;) {
     int64_t neg = 0;
     PD_TRY(count_below(bK, &neg));
-    if (neg >= i0 + nev || it_hi >= max_it) break;
+    hi_ok = neg >= i0 + nev;
+    if (hi_ok || it_hi >= max_it) break;
     bK = bK + step;
     ++it_hi;
   }
@@ -225,10 +227,12 @@ extern "C" int pdeshep_outer_bounds(int64_t n, int32_t b, int32_t is_complex, co
   if (!(step2 > 0.0)) step2 = ldexp(1.0, -40) * std::max(1.0, fabs(dl));
   double b0 = dl - step2;
   int it_lo = 1;
+  bool lo_ok = false;
   for (;;) {
     int64_t neg = 0;
     PD_TRY(count_below(b0, &neg));
-    if (neg <= i0 || it_lo >= max_it) break;
+    lo_ok = neg <= i0;
+    if (lo_ok || it_lo >= max_it) break;
     b0 = b0 - step2;
     ++it_lo;
   }
@@ -238,5 +242,7 @@ extern "C" int pdeshep_outer_bounds(int64_t n, int32_t b, int32_t is_complex, co
     h_iters[0] = it_lo;
     h_iters[1] = it_hi;
   }
-  return 0;
+  // a search that used its max_it counts without reaching its target leaves bounds
+  // that do not enclose the wanted eigenvalues
+  return hi_ok && lo_ok ? 0 : PDESHEP_NOT_CONVERGED;
 }

@@ -54,13 +54,6 @@ constexpr int kNParams =
 constexpr int kChebBlocks = 64;
 constexpr int kMaxSlices = 1024;
 
-__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
-  x += 0x9e3779b97f4a7c15ull;
-  uint64_t z = x;
-  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-  return z ^ (z >> 31);
-}
 
 // ---------------------------------------------------------------------------
 // features
@@ -812,5 +805,59 @@ extern "C" int pdeshep_propose_slices(int64_t n, int32_t b, int32_t is_complex, 
                  count_tol, fanout, h_bounds, h_counts, &used, &evals, h_proposed_counts, iw, iws, st));
   if (h_used_fallback) *h_used_fallback = used;
   if (h_inertia_evals) *h_inertia_evals = evals;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Training labels of the proposer: the equal-count boundaries, each the
+// midpoint between eigenvalues t_k - 1 and t_k (t_k = round(k n / nslices),
+// k = 1..nslices-1, clipped to [1, n-1]) enclosed by bisection on inertia,
+// normalised to the Gershgorin interval [lo, hi] and clipped to [0, 1].
+// ---------------------------------------------------------------------------
+extern "C" size_t pdeshep_equal_count_targets_workspace_size(int64_t n, int32_t b, int32_t is_complex,
+                                                             int32_t nslices, int32_t fanout) {
+  if (nslices < 2 || fanout < 1) return 0;
+  const size_t bis = pdeshep_bisect_workspace_size(n, b, is_complex, 2 * (nslices - 1), fanout);
+  return std::max(bis, sizeof(double) * gershgorin_ws_doubles());
+}
+
+extern "C" int pdeshep_equal_count_targets(int64_t n, int32_t b, int32_t is_complex, const void* d_band, int64_t ldab,
+                                           int32_t nslices, double rtol, int32_t fanout, float* h_targets,
+                                           void* d_work, size_t work_bytes, void* stream) {
+  if (n < 2) return -1;
+  if (b < 0) return -2;
+  if (!d_band) return -4;
+  if (ldab < b + 1) return -5;
+  if (nslices < 2 || nslices > 65536) return -6;
+  if (!(rtol > 0.0)) return -7;
+  if (fanout < 1 || fanout > 64) return -8;
+  if (!h_targets) return -9;
+  if (!d_work || work_bytes < pdeshep_equal_count_targets_workspace_size(n, b, is_complex, nslices, fanout))
+    return -10;
+  double lo = 0.0, hi = 0.0;
+  PD_TRY(pdeshep_gershgorin(n, b, is_complex, d_band, ldab, &lo, &hi, d_work, work_bytes, stream));
+  const int nb = nslices - 1;
+  std::vector<int64_t> t(nb), idx;
+  for (int k = 1; k <= nb; ++k) {
+    int64_t v = (2 * (int64_t)k * n + nslices) / (2 * (int64_t)nslices);
+    t[k - 1] = std::min<int64_t>(std::max<int64_t>(v, 1), n - 1);
+    idx.push_back(t[k - 1] - 1);
+    idx.push_back(t[k - 1]);
+  }
+  std::sort(idx.begin(), idx.end());
+  idx.erase(std::unique(idx.begin(), idx.end()), idx.end());
+  std::vector<double> elo(idx.size()), ehi(idx.size());
+  PD_TRY(pdeshep_bisect(n, b, is_complex, d_band, ldab, (int32_t)idx.size(), idx.data(), rtol, fanout, elo.data(),
+                        ehi.data(), d_work, work_bytes, stream));
+  auto mid = [&](int64_t k) {
+    const size_t p = std::lower_bound(idx.begin(), idx.end(), k) - idx.begin();
+    return 0.5 * (elo[p] + ehi[p]);
+  };
+  const double span = hi > lo ? hi - lo : 1.0;
+  for (int k = 0; k < nb; ++k) {
+    const double sig = 0.5 * (mid(t[k] - 1) + mid(t[k]));
+    const double u = (sig - lo) / span;
+    h_targets[k] = (float)(u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u));
+  }
   return 0;
 }

@@ -7,8 +7,8 @@ maps cheap band statistics (diagonal histogram, Gershgorin interval, KPM
 Chebyshev moments) to the equal-count slice boundaries; the library validates
 each boundary with an exact inertia count and re-places the misses by
 multisection.  Everything numeric runs in ``libpdeshep.so``; this module
-marshals tensors, initialises parameters, builds training labels with the
-library's inertia bisection and stores weights.
+marshals tensors, initialises parameters, asks the library for the training
+labels (pdeshep_equal_count_targets) and stores weights.
 
 Weights file: ``<path>.bin`` holds the raw little-endian float32 parameter
 vector, ``<path>.json`` a header with the architecture and training metadata.
@@ -135,21 +135,18 @@ class Trainer:
         return self.loss
 
 
-def equal_count_targets(band, nslices: int = N_OUT, rtol: float = 1e-7, b=None, stream=None):
-    """Training labels: the equal-count boundaries k n / nslices (k = 1..nslices-1),
-    each the midpoint of the enclosures of eigenvalues t-1 and t (t = round(k n / nslices)),
-    found by inertia bisection and normalised to the Gershgorin interval."""
-    from . import bisect, gershgorin
-    n = band.shape[0]
-    lo, hi = gershgorin(band, b=b, stream=stream)
-    t = np.array([(2 * k * n + nslices) // (2 * nslices) for k in range(1, nslices)], dtype=np.int64)
-    t = np.clip(t, 1, n - 1)
-    idx = np.unique(np.concatenate([t - 1, t]))
-    elo, ehi = bisect(band, idx, rtol=rtol, fanout=8, b=b, stream=stream)
-    mid = dict(zip(idx.tolist(), (0.5 * (elo + ehi)).tolist()))
-    sig = np.array([0.5 * (mid[int(k) - 1] + mid[int(k)]) for k in t])
-    span = hi - lo if hi > lo else 1.0
-    return np.clip((sig - lo) / span, 0.0, 1.0).astype(np.float32)
+def equal_count_targets(band, nslices: int = N_OUT, rtol: float = 1e-7, b=None, stream=None, fanout: int = 8):
+    """Training labels: the equal-count boundaries k n / nslices (k = 1..nslices-1), each the
+    midpoint of the enclosures of eigenvalues t-1 and t (t = round(k n / nslices)), found by
+    inertia bisection and normalised to the Gershgorin interval (pdeshep_equal_count_targets)."""
+    lib = load()
+    n, b, cplx, ldab = _band_args(band, b)
+    out = np.zeros(nslices - 1, dtype=np.float32)
+    ws = _workspace(lib.pdeshep_equal_count_targets_workspace_size(n, b, cplx, nslices, fanout), band.device)
+    st = lib.pdeshep_equal_count_targets(n, b, cplx, _ptr(band), ldab, int(nslices), float(rtol), int(fanout),
+                                         _np_ptr(out), _ptr(ws), ws.numel(), _stream(stream))
+    _check("pdeshep_equal_count_targets", st)
+    return out
 
 
 def train(bands, steps: int = 2000, batch: int = 64, lr: float = 1e-3, seed: int = 0, params=None,

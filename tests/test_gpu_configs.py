@@ -5,10 +5,12 @@
   in mixed precision with float-float (arith 0) and tensor-core (arith 2) Rayleigh-Ritz products.
   Configs 2 and 3 run with both Rayleigh-Ritz arithmetics.
 * Config 2 (complex n = 8192, b = 64, 8 slices over the lowest 20 %, m0 = 267, mixed
-  precision): what the oracle can compute one by one -- the exact counts at every boundary, the
-  residual of every converged pair, orthogonality, and sampled eigenvalues by bisection.
+  precision): the exact counts at every boundary, the residual of every converged pair,
+  orthogonality, sampled eigenvalues by bisection, and (tensor-core Rayleigh-Ritz) slice 0
+  element by element against the oracle's FEAST from the same start vectors.
 * Config 3 (real clustered n = 32768, b = 128, 64 slices of 40-400 eigenvalues, Ne = 16, 1024
-  factorizations streamed in capped waves): sampled counts and residuals against the oracle.
+  factorizations in slice groups under a 100 GB factor cap): the exact counts at all 65
+  boundaries and the residuals of sampled slices against the oracle.
 """
 import numpy as np
 import pytest
@@ -47,6 +49,7 @@ def test_config1_full_size_against_oracle(device, precision, arith):
     assert oracle.subspace_sin_angle(Xg, o["evecs"][:, :100]) <= 1e-8
     assert np.max(oracle.residuals(ab, lg, Xg, bnorm)) <= 1e-10
     assert oracle.orth(Xg) < 1e-13
+    assert oracle.orth_max(Xg) <= 1e-13
 
 
 @pytest.mark.parametrize("arith", [0, 2])
@@ -81,6 +84,7 @@ def test_config2_full_size_properties(device, arith):
         assert np.all((li >= bounds[i]) & (li < bounds[i + 1]))
         assert np.max(oracle.residuals(ab, li, Xi, bnorm)) <= 1e-10
         assert oracle.orth(Xi) < 1e-13
+        assert oracle.orth_max(Xi) <= 1e-13
         found.append(li)
         off += m0[i]
     allev = np.sort(np.concatenate(found))
@@ -88,6 +92,13 @@ def test_config2_full_size_properties(device, arith):
     for k in (0, nev // 2, nev - 1):                      # sampled eigenvalues by bisection on inertia
         elo, ehi = oracle.eig_by_bisection(ab, k, tol=1e-13)
         assert abs(allev[k] - 0.5 * (elo + ehi)) <= 1e-10 * bnorm
+    if arith == 2:                                        # a whole slice against the oracle's FEAST
+        cnt = int(r.counts[0])
+        o = oracle.feast_slice(ab, bounds[0], bounds[1], X0[:, :m0[0]], ne=8, rho=0.3, tol=1e-10, bnorm=bnorm,
+                               max_iter=40, count=cnt)
+        assert o["status"] == 0 and o["nfound"] == cnt
+        assert np.max(np.abs(ev[:cnt] - o["evals"][:cnt])) <= 1e-10 * bnorm
+        assert oracle.subspace_sin_angle(V[:, :cnt], o["evecs"][:, :cnt]) <= 1e-8
 
 
 @pytest.mark.parametrize("arith", [0, 2])
@@ -111,11 +122,12 @@ def test_config3_uneven_slices_in_waves(device, arith):
     r = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), ne=ne, precision=pk.MIXED, bnorm=bnorm,
                       tol=1e-10, max_iter=40, hbm_cap_bytes=100 << 30, autotune=1, rr_arith=arith)
     assert r.status == 0
-    assert r.stats["waves"] >= 2                      # the 1024 factorizations did not fit one wave
+    assert r.stats["waves"] >= 2                      # the 1024 factorizations did not fit one group
+    assert r.stats["factorizations"] == nslice * ne   # every system factored once (groups, not re-streaming)
     assert list(r.counts) == [int(c) for c in sizes]
     assert list(r.nfound) == list(r.counts)
-    for i in (0, 17, 63):                              # exact counts at sampled boundaries
-        assert oracle.inertia(ab, bounds[i + 1]) - oracle.inertia(ab, bounds[i]) == sizes[i]
+    neg = [oracle.inertia(ab, s) for s in bounds]      # exact counts at all 65 boundaries
+    assert list(np.diff(neg)) == [int(c) for c in sizes] == list(r.counts)
     ev = r.evals.cpu().numpy()
     off = np.concatenate([[0], np.cumsum(m0)])
     for i in (5, 40):                                 # residuals of two whole slices through the oracle

@@ -46,6 +46,7 @@ def _run_compare(device, ab, ks, m0, precision, seed, ne=8, rho=0.3, tol=1e-10):
         assert oracle.subspace_sin_angle(Xg, o["evecs"][:, :cnt]) <= 1e-8
         assert np.max(oracle.residuals(ab, lg, Xg, bnorm)) <= tol
         assert oracle.orth(Xg) < 1e-13
+        assert oracle.orth_max(Xg) <= 1e-13            # entrywise, without the paper's 1/n
         off += m0[i]
     return r
 
@@ -251,3 +252,136 @@ def test_graph_replay_matches_direct_launches(device, cplx):
     assert outs[0].stats["iterations"] == outs[1].stats["iterations"]
     assert np.array_equal(outs[0].evals.cpu().numpy(), outs[1].evals.cpu().numpy())
     assert np.array_equal(outs[0].evecs.cpu().numpy(), outs[1].evecs.cpu().numpy())
+
+
+def test_random_start_matches_oracle_stream(device):
+    """pdeshep_random_start writes exactly the oracle's counter-based start vectors."""
+    import paper_2012_00506_gb300 as pk
+    for cplx in (False, True):
+        X = pk.random_start(300, 17, cplx, seed=99, col0=5, device=device)
+        ref = oracle.random_start(300, 17, cplx, seed=99, col0=5)
+        assert np.array_equal(block_from_dev(X), ref)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_library_drawn_start_vectors(device, cplx):
+    """d_x0 = NULL: the library draws the start vectors of Algorithm 1 itself.  The run gives the
+    same bits as one handed the oracle's copy of that stream, and matches the oracle's FEAST
+    started from those vectors."""
+    import paper_2012_00506_gb300 as pk
+    n, b = 500, 9
+    ab = synth.random_band(n, b, 301 + cplx, cplx)
+    ks = [60, 100, 130]
+    bounds = _bounds(ab, ks)
+    m0 = [oracle.m0_rule(40), oracle.m0_rule(30)]
+    bn = oracle.spectral_norm(ab)
+    band = to_dev(ab, device)
+    r0 = pk.band_slice(band, bounds, m0, None, seed=1234, bnorm=bn, max_iter=40)
+    X0 = oracle.random_start(n, sum(m0), cplx, seed=1234)
+    r1 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, max_iter=40)
+    assert r0.status == r1.status == 0
+    assert np.array_equal(r0.evals.cpu().numpy(), r1.evals.cpu().numpy())
+    assert np.array_equal(r0.evecs.cpu().numpy(), r1.evecs.cpu().numpy())
+    ev, V = r0.evals.cpu().numpy(), block_from_dev(r0.evecs)
+    off = 0
+    for i in range(2):
+        cnt = ks[i + 1] - ks[i]
+        assert r0.counts[i] == r0.nfound[i] == cnt
+        o = oracle.feast_slice(ab, bounds[i], bounds[i + 1], X0[:, off:off + m0[i]], ne=8, tol=1e-10, bnorm=bn,
+                               max_iter=40, count=cnt)
+        assert o["status"] == 0 and o["nfound"] == cnt
+        assert np.max(np.abs(ev[off:off + cnt] - o["evals"][:cnt])) <= 1e-10 * bn
+        assert oracle.subspace_sin_angle(V[:, off:off + cnt], o["evecs"][:, :cnt]) <= 1e-8
+        off += m0[i]
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_m0_resize_enlarges_small_subspaces(device, cplx):
+    """m0_resize (Section 3.2's subspace rule in the library): slice 0 is given 12 columns for
+    40 eigenvalues and runs with max(ceil(1.3 * 40), 40 + 10) = 52; slices whose m0 already
+    covers m_i + 10 keep theirs.  Every slice ends with its exact count and matches the oracle
+    started from the same columns.  Without the option the same call reports the mismatch, and
+    a capacity below a count is a mismatch too."""
+    import paper_2012_00506_gb300 as pk
+    n, b = 600, 10
+    ab = synth.random_band(n, b, 401 + cplx, cplx)
+    ks = [50, 90, 100, 160]
+    counts = [40, 10, 60]
+    bounds = _bounds(ab, ks)
+    bn = oracle.spectral_norm(ab)
+    band = to_dev(ab, device)
+    m0, cap = [12, 30, 70], 80
+    X0 = oracle.random_start(n, 3 * cap, cplx, seed=5)
+    r = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, m0_resize=1, m0_cap=cap, max_iter=40)
+    assert r.status == 0
+    assert list(r.m0) == [52, 30, 70]
+    assert list(r.counts) == counts and list(r.nfound) == counts
+    ev, V = r.evals.cpu().numpy(), block_from_dev(r.evecs)
+    for i in range(3):
+        off, cnt = i * cap, counts[i]
+        o = oracle.feast_slice(ab, bounds[i], bounds[i + 1], X0[:, off:off + int(r.m0[i])], ne=8, tol=1e-10,
+                               bnorm=bn, max_iter=40, count=cnt)
+        assert o["status"] == 0 and o["nfound"] == cnt
+        assert np.max(np.abs(ev[off:off + cnt] - o["evals"][:cnt])) <= 1e-10 * bn
+        assert oracle.subspace_sin_angle(V[:, off:off + cnt], o["evecs"][:, :cnt]) <= 1e-8
+    r2 = pk.band_slice(band, bounds, m0, None, bnorm=bn, raise_on_error=False)
+    assert r2.status == 2 and list(r2.counts) == counts
+    r3 = pk.band_slice(band, bounds, m0, None, bnorm=bn, m0_resize=1, m0_cap=35, raise_on_error=False)
+    assert r3.status == 2 and list(r3.counts) == counts and list(r3.m0) == [35, 30, 35]
+
+
+def test_slice_groups_match_one_batch(device):
+    """A factor cap that holds slices 0-1 but not slice 2 as well: the call runs as two groups,
+    each factoring its systems once and iterating on resident factors, with the results of the
+    single batch (and exact counts)."""
+    import paper_2012_00506_gb300 as pk
+    ab, bounds, m0, X0 = _small_problem(device, True, seed=82)
+    band = to_dev(ab, device)
+    bn = oracle.spectral_norm(ab)
+    r1 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, max_iter=30)
+    # per system (n = 1200, b = 16, complex64): 1.87 MB of factors + n m0 x 2 solve outputs;
+    # slices 0 + 1 need 61.9 MB for their 16 systems, slice 2 alone 66.9 MB
+    r2 = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), bnorm=bn, max_iter=30, hbm_cap_bytes=70_000_000)
+    assert r1.status == r2.status == 0
+    assert r1.stats["waves"] == 1 and r2.stats["waves"] == 2
+    assert r2.stats["factorizations"] == r1.stats["factorizations"] == 8 * 3
+    assert list(r2.counts) == list(r1.counts) and list(r2.nfound) == list(r1.nfound) == list(r1.counts)
+    e1, e2 = r1.evals.cpu().numpy(), r2.evals.cpu().numpy()
+    off = 0
+    for i, m in enumerate(m0):
+        k = int(r1.nfound[i])
+        assert np.max(np.abs(e1[off:off + k] - e2[off:off + k])) <= 1e-12 * bn
+        off += m
+
+
+def test_trapezoid_rule_through_gpu_feast(device):
+    """The midpoint trapezoid rule (Section 2.2 names it beside Gauss quadrature) passed as the
+    call's nodes and weights: the GPU FEAST matches the oracle's FEAST run with the same rule."""
+    import paper_2012_00506_gb300 as pk
+    from oracle import rules_oracle
+    n, b = 400, 8
+    ab = synth.random_band(n, b, 501, True)
+    ks = [100, 140, 175]
+    bounds = _bounds(ab, ks)
+    bn = oracle.spectral_norm(ab)
+    m0 = [oracle.m0_rule(40), oracle.m0_rule(35)]
+    rules = [rules_oracle.trapezoid_rule(8, bounds[i], bounds[i + 1], 0.3) for i in range(2)]
+    lib_rules = [pk.contour_rule(8, bounds[i], bounds[i + 1], 0.3, kind="trapezoid") for i in range(2)]
+    for (z, w), (zl, wl) in zip(rules, lib_rules):
+        assert np.allclose(z, zl, rtol=0, atol=1e-15) and np.allclose(w, wl, rtol=0, atol=1e-15)
+    X0 = synth.random_subspace(n, sum(m0), 502, True)
+    r = pk.band_slice(to_dev(ab, device), bounds, m0, block_to_dev(X0, device), bnorm=bn, max_iter=40,
+                      nodes=np.concatenate([z for z, _ in lib_rules]), weights=np.concatenate([w for _, w in lib_rules]))
+    assert r.status == 0
+    ev, V = r.evals.cpu().numpy(), block_from_dev(r.evecs)
+    off = 0
+    for i in range(2):
+        cnt = ks[i + 1] - ks[i]
+        assert r.counts[i] == r.nfound[i] == cnt
+        o = oracle.feast_slice(ab, bounds[i], bounds[i + 1], X0[:, off:off + m0[i]], tol=1e-10, bnorm=bn,
+                               max_iter=40, count=cnt, rule=rules[i])
+        assert o["status"] == 0 and o["nfound"] == cnt
+        assert np.max(np.abs(ev[off:off + cnt] - o["evals"][:cnt])) <= 1e-10 * bn
+        assert oracle.subspace_sin_angle(V[:, off:off + cnt], o["evecs"][:, :cnt]) <= 1e-8
+        assert oracle.orth_max(V[:, off:off + cnt]) <= 1e-13
+        off += m0[i]

@@ -74,6 +74,8 @@ def test_bisection_enclosures(device):
         assert lo[t] <= ev[k] < hi[t] + 1e-15
         assert hi[t] - lo[t] <= 1e-13 * max(1.0, abs(lo[t]), abs(hi[t]))
         assert oracle.inertia(ab, lo[t]) <= k < oracle.inertia(ab, hi[t])
-    glo, ghi = pk.gershgorin(to_dev(ab, device))
-    olo, ohi = oracle.gershgorin(ab)
-    assert abs(glo - olo) < 1e-12 and abs(ghi - ohi) < 1e-12
+    # same FP64 operations in the same order on both sides: identical bits
+    for ab2 in (ab, synth.random_band(301, 17, 98, False), synth.mixture_band(1000, 40, 97, is_complex=True)):
+        glo, ghi = pk.gershgorin(to_dev(ab2, device))
+        olo, ohi = oracle.gershgorin(ab2)
+        assert (glo, ghi) == (olo, ohi), (glo - olo, ghi - ohi)

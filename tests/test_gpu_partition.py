@@ -27,9 +27,9 @@ def test_outer_bounds_laplacian(device, i0, nev, shift):
     j = np.arange(1, k + 1)[None, :]
     ev = np.sort((4 - 2 * np.cos(i * np.pi / (m + 1)) - 2 * np.cos(j * np.pi / (k + 1))).ravel())
     prev = ev - shift
-    b0, bK, (it_lo, it_hi) = pk.outer_bounds(to_dev(ab, device), prev, i0, nev)
-    ob0, obK, oit_lo, oit_hi = po.outer_bounds(ab, prev, i0, nev, alpha=1e-3, m_hat=6)
-    assert (b0, bK, it_lo, it_hi) == (ob0, obK, oit_lo, oit_hi)
+    b0, bK, (it_lo, it_hi), ok = pk.outer_bounds(to_dev(ab, device), prev, i0, nev)
+    ob0, obK, oit_lo, oit_hi, ook = po.outer_bounds(ab, prev, i0, nev, alpha=1e-3, m_hat=6)
+    assert (b0, bK, it_lo, it_hi, ok) == (ob0, obK, oit_lo, oit_hi, ook) and ok
     assert np.sum(ev < bK) >= i0 + nev and np.sum(ev < b0) <= i0
 
 
@@ -45,7 +45,23 @@ def test_outer_bounds_sequence_step(device, cplx):
     E[:, 0] = E[:, 0].real
     prev = np.linalg.eigvalsh(synth.band_to_dense(ab - 1e-3 * E))
     for i0, nev in ((0, 60), (100, 30)):
-        b0, bK, its = pk.outer_bounds(to_dev(ab, device), prev, i0, nev)
-        ob0, obK, oit_lo, oit_hi = po.outer_bounds(ab, prev, i0, nev)
-        assert (b0, bK, its) == (ob0, obK, (oit_lo, oit_hi))
+        b0, bK, its, ok = pk.outer_bounds(to_dev(ab, device), prev, i0, nev)
+        ob0, obK, oit_lo, oit_hi, ook = po.outer_bounds(ab, prev, i0, nev)
+        assert (b0, bK, its, ok) == (ob0, obK, (oit_lo, oit_hi), ook) and ok
         assert oracle.inertia(ab, bK) >= i0 + nev and oracle.inertia(ab, b0) <= i0
+
+
+def test_outer_bounds_capped_search_reports_not_converged(device):
+    """max_it too small for the upper search: the library returns PDESHEP_NOT_CONVERGED with the
+    same (non-enclosing) bounds and counts as the oracle."""
+    import paper_2012_00506_gb300 as pk
+    m, k = 13, 11
+    ab = synth.laplacian_2d_band(m, k)
+    i = np.arange(1, m + 1)[:, None]
+    j = np.arange(1, k + 1)[None, :]
+    ev = np.sort((4 - 2 * np.cos(i * np.pi / (m + 1)) - 2 * np.cos(j * np.pi / (k + 1))).ravel())
+    prev = ev - 0.05
+    b0, bK, its, ok = pk.outer_bounds(to_dev(ab, device), prev, 30, 50, max_it=3)
+    ob0, obK, oit_lo, oit_hi, ook = po.outer_bounds(ab, prev, 30, 50, alpha=1e-3, m_hat=6, max_it=3)
+    assert (b0, bK, its, ok) == (ob0, obK, (oit_lo, oit_hi), ook)
+    assert not ok and its[1] == 3

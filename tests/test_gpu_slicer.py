@@ -26,9 +26,10 @@ def test_features_vs_oracle(device, n, b, cplx, seed):
     ab = synth.mixture_band(n, b, 40 + seed, is_complex=cplx, off_sigma=0.05)
     f = slicer.features(to_dev(ab, device), seed=1234 + seed).cpu().numpy().astype(np.float64)
     g = so.features(ab, 1234 + seed)
-    # histogram: bin decisions are taken in FP64 on both sides; only a value on a bin
-    # edge could move, by one bin
-    assert np.abs(f[:64] - g[:64]).sum() <= 2.0 / n + 1e-7
+    # histogram: the Gershgorin interval and every bin decision are the same FP64 operations
+    # in the same order on both sides, so the bin counts are identical
+    assert np.array_equal(f[:64].astype(np.float32), g[:64].astype(np.float32)), (f[:64] * n, g[:64] * n)
+    assert np.array_equal(np.rint(f[:64].astype(np.float64) * n), np.rint(g[:64] * n))
     assert np.allclose(f[64:66], g[64:66], rtol=1e-6, atol=1e-7)
     assert np.allclose(f[66:], g[66:], rtol=0, atol=2e-7), np.abs(f[66:] - g[66:]).max()
 
@@ -196,3 +197,16 @@ def test_proposal_full_size_complex(device, trained):
     for k in (1, 20, 47, 63):
         assert oracle.inertia(ab, pr.bounds[k]) == cum[k]
         assert abs(cum[k] - 16384 * k // 64) <= 16
+
+
+@pytest.mark.parametrize("n,b,cplx,nsl", [(400, 12, True, 64), (257, 5, False, 16)])
+def test_equal_count_targets_vs_oracle(device, n, b, cplx, nsl):
+    """The training labels come from the library (bisection on inertia, Gershgorin
+    normalisation): within rounding of the oracle's labels from the exact spectrum."""
+    from paper_2012_00506_gb300 import slicer
+    ab = synth.mixture_band(n, b, 70 + n, is_complex=cplx, off_sigma=0.03)
+    t = slicer.equal_count_targets(to_dev(ab, device), nslices=nsl, rtol=1e-12)
+    ref = so.equal_count_targets(ab, nsl)
+    assert t.dtype == np.float32 and t.shape == (nsl - 1,)
+    assert np.max(np.abs(t.astype(np.float64) - ref)) <= 2e-7
+    assert np.all(np.diff(t) >= 0)

@@ -93,7 +93,8 @@ def test_outer_bounds_against_closed_form_spectrum(i0, nev, shift):
     j = np.arange(1, k + 1)[None, :]
     ev = np.sort((4 - 2 * np.cos(i * np.pi / (m + 1)) - 2 * np.cos(j * np.pi / (k + 1))).ravel())
     prev = ev - shift
-    b0, bK, it_lo, it_hi = po.outer_bounds(ab, prev, i0, nev, alpha=1e-3, m_hat=6)
+    b0, bK, it_lo, it_hi, ok = po.outer_bounds(ab, prev, i0, nev, alpha=1e-3, m_hat=6)
+    assert ok
     below = lambda x: int(np.sum(ev < x))
     assert below(bK) >= i0 + nev and below(b0) <= i0
     du = prev[i0 + nev - 1]
@@ -129,3 +130,20 @@ def test_restart_plan_invariants():
     inside = [k for k in range(vals.size) if 0.2 <= vals[k] < 0.5]
     expect = sorted(sorted(inside, key=lambda k: abs(vals[k] - 0.35))[:6])
     assert p == expect and len(inside) > 6
+
+
+def test_outer_bounds_report_a_capped_search():
+    """A search that runs out of counts before its target is reported, not returned as if it
+    enclosed the wanted eigenvalues (Algorithm 4 with a small max_it)."""
+    m, k = 13, 11
+    ab = synth.laplacian_2d_band(m, k)
+    i = np.arange(1, m + 1)[:, None]
+    j = np.arange(1, k + 1)[None, :]
+    ev = np.sort((4 - 2 * np.cos(i * np.pi / (m + 1)) - 2 * np.cos(j * np.pi / (k + 1))).ravel())
+    prev = ev - 0.05                                     # every eigenvalue moved up by 0.05
+    i0, nev = 30, 50
+    full = po.outer_bounds(ab, prev, i0, nev, alpha=1e-3, m_hat=6)
+    assert full[4] and full[3] >= 4                      # the upper search needs several counts
+    capped = po.outer_bounds(ab, prev, i0, nev, alpha=1e-3, m_hat=6, max_it=3)
+    assert capped[3] == 3 and not capped[4]
+    assert np.sum(ev < capped[1]) < i0 + nev             # indeed not an enclosure

@@ -24,7 +24,8 @@ def _sequence(method, rule_kind, n=800, b=8, nev=160, K=8, steps=4, ne=8, seed=5
         ref = dense_ev[:nev] if step == 0 else lam
         if outer == "alg4" and step > 0:
             # Algorithm 4 on the current matrix from the previous eigenvalues (Section 3.2)
-            b0, bK, _, _ = po.outer_bounds(B, lam, 0, nev)
+            b0, bK, _, _, ok = po.outer_bounds(B, lam, 0, nev)
+            assert ok
         else:
             spacing = float(np.median(np.diff(ref)))
             b0 = float(ref[0] - 2 * spacing)

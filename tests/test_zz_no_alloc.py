@@ -4,16 +4,18 @@ Some callers cannot give the library any device memory: their device memory
 belongs to another allocator, or they run where they may only launch work on
 buffers they were handed.  For them the library offers an inertia call whose
 scratch is a fixed array inside the library.  This file checks, through the C
-ABI, that it returns exactly the counts of the workspace-based pdeshep_inertia
-on two calls in a row (the array keeps the previous call's contents, so the
-second call must not be affected by the first), and that requests beyond its
-limits are refused.  It is collected last on purpose.
+ABI, that it returns exactly the counts of the oracle's LDL^T inertia and of
+the workspace-based pdeshep_inertia on calls in a row (the array keeps the
+previous call's contents, so a call must not be affected by the one before),
+and that requests beyond its limits are refused.  It is collected last on
+purpose.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from gpu_util import dev, to_dev
 
@@ -46,6 +48,9 @@ def test_noalloc_inertia_matches_workspace_version():
         assert st == 0, st
         ref = pk.inertia(band, sig)
         assert np.array_equal(neg, ref), (call, neg, ref)
+        # the oracle's pivot-free LDL^T in the same operation order: identical counts
+        ora = np.array([oracle.inertia(ab, s, b=b) for s in sig[:: max(1, sig.size // 9)]])
+        assert np.array_equal(neg[:: max(1, sig.size // 9)], ora), (call, neg, ora)
 
 
 def test_noalloc_inertia_rejects_oversized_requests():
@@ -60,3 +65,9 @@ def test_noalloc_inertia_rejects_oversized_requests():
     wide = to_dev(synth.random_band(300, 106, 905, True), device)
     st, _ = _noalloc(lib, wide, 106, np.zeros(3), stream)
     assert st == -2 and b"shared-memory" in lib.pdeshep_last_error()
+    st, _ = _noalloc(lib, band, -1, np.zeros(3), stream)
+    assert st == -2 and b"negative" in lib.pdeshep_last_error()
+    # a refused call leaves the array usable: the next call is exact again
+    st, neg = _noalloc(lib, band, 4, np.array([-0.5, 0.0, 0.5]), stream)
+    ab = synth.random_band(200, 4, 904, False)
+    assert st == 0 and list(neg) == [oracle.inertia(ab, s) for s in (-0.5, 0.0, 0.5)]
