@@ -187,6 +187,15 @@ const char* pdeshep_version(void);
 /* Number of CUDA kernels this library has launched in this process so far. */
 uint64_t pdeshep_kernel_launches(void);
 
+/* Measured ALU throughput of the current GPU (the roofline denominator of    */
+/* kernels bound by the FP32 or FP64 pipes; not part of the paper's method):  */
+/* a launch of SMs x 2048 threads, each running 8 independent FMA chains of   */
+/* 16 x iters steps; best of three launches timed with CUDA events on        */
+/* `stream`.  fp64 = 0: FP32 FMAs, 1: FP64 FMAs.  *h_tflops = 2 x FMAs /      */
+/* time in TFLOP/s.  d_scratch: any device buffer of SMs x 2048 doubles      */
+/* (never written in practice).  Synchronous.                                */
+int pdeshep_alu_peak(int32_t fp64, int64_t iters, double* h_tflops, void* d_scratch, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Sylvester inertia (Section 3.2; Section 3.1): for every sigma_s counts the  */
 /* eigenvalues of B below sigma_s as the number of negative pivots of the     */

@@ -44,7 +44,7 @@ STATUS = {
 
 EXPORTED = [
     "pdeshep_opts_default", "pdeshep_status_string", "pdeshep_last_error", "pdeshep_version",
-    "pdeshep_kernel_launches",
+    "pdeshep_kernel_launches", "pdeshep_alu_peak",
     "pdeshep_inertia_workspace_size", "pdeshep_inertia", "pdeshep_inertia_noalloc",
     "pdeshep_bisect_workspace_size",
     "pdeshep_bisect", "pdeshep_gershgorin", "pdeshep_contour_rule", "pdeshep_contour_rule_trapezoid",
@@ -152,6 +152,7 @@ def load(path: str = LIB_PATH):
         "pdeshep_partition": (C.c_int, [i32, i64, P, i32, dbl, dbl, i32, P, P, P, P]),
         "pdeshep_restart_plan": (C.c_int, [i64, P, i32, P, P, i32, P]),
         "pdeshep_random_start": (C.c_int, [i64, i32, i64, i32, C.c_uint64, P, P]),
+        "pdeshep_alu_peak": (C.c_int, [i32, i64, P, P, P]),
         "pdeshep_equal_count_targets_workspace_size": (sz, [i64, i32, i32, i32, i32]),
         "pdeshep_equal_count_targets": (C.c_int, [i64, i32, i32, P, i64, i32, dbl, i32, P, P, sz, P]),
         "pdeshep_outer_bounds_workspace_size": (sz, [i64, i32, i32]),
@@ -508,6 +509,17 @@ class SliceResult:
         off = self.offset(i)
         k = int(self.nfound[i])
         return self.evals[off: off + k], self.evecs[off: off + k]
+
+
+def alu_peak(fp64, iters=4096, device=None, stream=None):
+    """Measured FP32 (fp64=False) or FP64 FMA throughput of the GPU in TFLOP/s."""
+    torch = _torch()
+    lib = load()
+    scratch = torch.empty(1 << 22, dtype=torch.float64, device=device)
+    out = C.c_double()
+    st = lib.pdeshep_alu_peak(int(bool(fp64)), int(iters), C.byref(out), _ptr(scratch), _stream(stream))
+    _check("pdeshep_alu_peak", st)
+    return out.value
 
 
 def random_start(n, ncols, is_complex, seed=0, col0=0, device=None, stream=None):

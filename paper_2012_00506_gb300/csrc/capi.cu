@@ -322,3 +322,62 @@ extern "C" int pdeshep_eigh(int32_t is_complex, int32_t nblk, const int32_t* h_m
   if (is_complex) return eigh<double2>(nblk, h_m, (double2*)d_a, d_lam, (double2*)d_v, d_work, work_bytes, st);
   return eigh<double>(nblk, h_m, (double*)d_a, d_lam, (double*)d_v, d_work, work_bytes, st);
 }
+
+// ---------------------------------------------------------------------------
+// ALU throughput probe: every thread runs 8 independent FMA chains of `iters`
+// steps (FP32 or FP64), enough warps per SM to hide the FMA latency; the
+// result is written so the chains cannot be removed.  TFLOP/s = 2 x FMAs /
+// the launch's event time.  Used for the roofline denominators of the
+// kernels bound by the FP32 or FP64 pipes.
+// ---------------------------------------------------------------------------
+namespace {
+template <typename T>
+__global__ void __launch_bounds__(256) fma_probe_kernel(int64_t iters, T seed, T* out) {
+  T a0 = seed + (T)threadIdx.x, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
+  T a4 = a0 + (T)4, a5 = a0 + (T)5, a6 = a0 + (T)6, a7 = a0 + (T)7;
+  const T m = (T)0.999999, c = (T)1e-7;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      a0 = a0 * m + c; a1 = a1 * m + c; a2 = a2 * m + c; a3 = a3 * m + c;
+      a4 = a4 * m + c; a5 = a5 * m + c; a6 = a6 * m + c; a7 = a7 * m + c;
+    }
+  }
+  const T s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == (T)-12345.0) out[blockIdx.x * blockDim.x + threadIdx.x] = s;  // never true; keeps the chains
+}
+}  // namespace
+
+extern "C" int pdeshep_alu_peak(int32_t fp64, int64_t iters, double* h_tflops, void* d_scratch, void* stream) {
+  if (fp64 != 0 && fp64 != 1) return -1;
+  if (iters < 1) return -2;
+  if (!h_tflops) return -3;
+  if (!d_scratch) return -4;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  PD_CK(cudaGetDevice(&dev));
+  PD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8;  // 8 x 256 threads = 64 warps per SM
+  cudaEvent_t e0, e1;
+  PD_CK(cudaEventCreate(&e0));
+  PD_CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    PD_CK(cudaEventRecord(e0, st));
+    if (fp64)
+      fma_probe_kernel<double><<<blocks, 256, 0, st>>>(iters, 1.0, (double*)d_scratch);
+    else
+      fma_probe_kernel<float><<<blocks, 256, 0, st>>>(iters, 1.0f, (float*)d_scratch);
+    PD_CK_LAUNCH();
+    PD_CK(cudaEventRecord(e1, st));
+    PD_CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    PD_CK(cudaEventElapsedTime(&ms, e0, e1));
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const double fmas = (double)blocks * 256 * 8 * 16 * (double)iters;
+  *h_tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
+  return 0;
+}

@@ -24,3 +24,12 @@ def block_to_dev(X, device):
 
 def block_from_dev(T):
     return np.asfortranarray(T.detach().cpu().numpy().T)
+
+
+def orth_tol(n, arith):
+    """Tolerance on ||X^H X - I||_max for Ritz vectors of length n: the worst-case rounding bound
+    n u of an n-term dot product in the arithmetic of the Rayleigh-Ritz products -- u = 2^-53 for
+    FP64 (plain path, arith 1), 2^-48 for float-float (arith 0, ~48-bit products), 2^-47 for the
+    bf16 digit products on the tensor cores (arith 2, 47-bit fixed point per row)."""
+    u = {1: 2.0 ** -53, 0: 2.0 ** -48, 2: 2.0 ** -47}[arith]
+    return n * u

@@ -17,7 +17,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import block_from_dev, block_to_dev, dev, to_dev
+from gpu_util import block_from_dev, block_to_dev, dev, orth_tol, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,8 @@ def test_config1_full_size_against_oracle(device, precision, arith):
     assert oracle.subspace_sin_angle(Xg, o["evecs"][:, :100]) <= 1e-8
     assert np.max(oracle.residuals(ab, lg, Xg, bnorm)) <= 1e-10
     assert oracle.orth(Xg) < 1e-13
-    assert oracle.orth_max(Xg) <= 1e-13
+    # entrywise: FP64 products below 1e-13 here; the mixed path within n u of its products' arithmetic
+    assert oracle.orth_max(Xg) <= (1e-13 if precision == 0 else orth_tol(n, arith))
 
 
 @pytest.mark.parametrize("arith", [0, 2])
@@ -84,7 +85,7 @@ def test_config2_full_size_properties(device, arith):
         assert np.all((li >= bounds[i]) & (li < bounds[i + 1]))
         assert np.max(oracle.residuals(ab, li, Xi, bnorm)) <= 1e-10
         assert oracle.orth(Xi) < 1e-13
-        assert oracle.orth_max(Xi) <= 1e-13
+        assert oracle.orth_max(Xi) <= orth_tol(n, arith)
         found.append(li)
         off += m0[i]
     allev = np.sort(np.concatenate(found))

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import block_from_dev, block_to_dev, dev, to_dev
+from gpu_util import block_from_dev, block_to_dev, dev, orth_tol, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -46,7 +46,9 @@ def _run_compare(device, ab, ks, m0, precision, seed, ne=8, rho=0.3, tol=1e-10):
         assert oracle.subspace_sin_angle(Xg, o["evecs"][:, :cnt]) <= 1e-8
         assert np.max(oracle.residuals(ab, lg, Xg, bnorm)) <= tol
         assert oracle.orth(Xg) < 1e-13
-        assert oracle.orth_max(Xg) <= 1e-13            # entrywise, without the paper's 1/n
+        # entrywise, without the 1/n: FP64 below 1e-13; mixed (tensor-core digit products by default)
+        # within n u of its products' arithmetic
+        assert oracle.orth_max(Xg) <= (1e-13 if precision == 0 else orth_tol(n, 2))
         off += m0[i]
     return r
 
@@ -326,8 +328,10 @@ def test_m0_resize_enlarges_small_subspaces(device, cplx):
         assert oracle.subspace_sin_angle(V[:, off:off + cnt], o["evecs"][:, :cnt]) <= 1e-8
     r2 = pk.band_slice(band, bounds, m0, None, bnorm=bn, raise_on_error=False)
     assert r2.status == 2 and list(r2.counts) == counts
-    r3 = pk.band_slice(band, bounds, m0, None, bnorm=bn, m0_resize=1, m0_cap=35, raise_on_error=False)
+    r3 = pk.band_slice(band, bounds, [12, 30, 30], None, bnorm=bn, m0_resize=1, m0_cap=35, raise_on_error=False)
     assert r3.status == 2 and list(r3.counts) == counts and list(r3.m0) == [35, 30, 35]
+    r4 = pk.band_slice(band, bounds, m0, None, bnorm=bn, m0_resize=1, m0_cap=35, raise_on_error=False)
+    assert r4.status == -11                              # a given m0 above the capacity is an argument error
 
 
 def test_slice_groups_match_one_batch(device):
@@ -383,5 +387,5 @@ def test_trapezoid_rule_through_gpu_feast(device):
         assert o["status"] == 0 and o["nfound"] == cnt
         assert np.max(np.abs(ev[off:off + cnt] - o["evals"][:cnt])) <= 1e-10 * bn
         assert oracle.subspace_sin_angle(V[:, off:off + cnt], o["evecs"][:, :cnt]) <= 1e-8
-        assert oracle.orth_max(V[:, off:off + cnt]) <= 1e-13
+        assert oracle.orth_max(V[:, off:off + cnt]) <= orth_tol(n, 2)
         off += m0[i]
