@@ -225,7 +225,7 @@ int pdeshep_inertia(int64_t n, int32_t b, int32_t is_complex, const void* d_band
 /* that array until the process exits.  It never allocates or frees device  */
 /* memory.                                                                   */
 /*  Limits: nsigma <= 1024 (else -6) and the LDL^T window must fit in shared */
-/*  memory: real b <= 141, complex b <= 105 (else -2); the reason is then in */
+/*  memory: real b <= 194, complex b <= 149 (else -2); the reason is then in */
 /*  pdeshep_last_error().                                                    */
 /*  Every call looks up the array's device address on the current device    */
 /*  (cudaGetSymbolAddress); the first call on a device may load the library's */

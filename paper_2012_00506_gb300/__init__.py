@@ -249,8 +249,8 @@ def inertia_noalloc(band, sigmas, b=None, stream=None):
     """Eigenvalue counts below each sigma without any device allocation.
 
     For callers that cannot give the library device memory: the scratch is a
-    fixed array inside the library (limits: at most 1024 shifts; real b <= 141,
-    complex b <= 105).  Calls that may overlap on the GPU share that array and
+    fixed array inside the library (limits: at most 1024 shifts; real b <= 194,
+    complex b <= 149).  Calls that may overlap on the GPU share that array and
     must be serialised by the caller.
     """
     lib = load()

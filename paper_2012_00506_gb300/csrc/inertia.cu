@@ -69,31 +69,45 @@ struct InertiaElem<true> {
   using T = double2;
 };
 
-// Load band column `col` into window slot `slot` (entries d = 0..b), shifted by -sigma.
+// The active window (rows and columns k..k+b at step k) is stored by
+// diagonals: diagonal d (d = i - j, 0..b) is a ring of R_d = b + 1 - d
+// entries, entry (i, j) at ring_base(d) + (j mod R_d).  At step k column j
+// = k + s of the window holds rows j..k+b, so diagonal d holds the columns
+// k..k+b-d: exactly R_d entries, (b+1)(b+2)/2 in all (half of a square
+// window).  After step k the entries of column k are dead; the row k+b+1 that
+// enters next lands in exactly those slots (its entry on diagonal d is column
+// k+b+1-d = k + R_d).
+__host__ __device__ __forceinline__ int ring_base(int d, int b) { return d * (b + 1) - d * (d - 1) / 2; }
+
+// Row r of B - sigma I (entries (r, j), j = max(0, r-b)..r) into the rings; h[d] = k mod R_d for the
+// step k that first uses the row (only the column index modulo R_d is needed: j mod R_d).
 template <bool CPLX>
-__device__ __forceinline__ void load_column(typename InertiaElem<CPLX>::T* W, int B1, int slot,
-                                            int64_t col, int64_t n, int b, const double* band,
-                                            int64_t ldab, double sigma) {
+__device__ __forceinline__ void load_row(typename InertiaElem<CPLX>::T* W, int b, int64_t r, int64_t k,
+                                         const int* h, const double* band, int64_t ldab, double sigma) {
   for (int d = threadIdx.x; d <= b; d += blockDim.x) {
+    const int64_t j = r - d;
+    if (j < 0 || j < k) continue;
+    // j - k = b - d' for the row r = k + b (window bottom row), so j mod R_d = h[d] + (j - k) wrapped
+    const int R = b + 1 - d;
+    int pos = h[d] + (int)(j - k);
+    if (pos >= R) pos -= R;
+    const int e = ring_base(d, b) + pos;
     if constexpr (CPLX) {
-      double2 v = make_double2(0.0, 0.0);
-      if (col + d < n) {
-        const double* p = band + 2 * (d + col * ldab);
-        v = make_double2(p[0], p[1]);
-      }
+      const double* p = band + 2 * (d + j * ldab);
+      double2 v = make_double2(p[0], p[1]);
       if (d == 0) v = make_double2(__dsub_rn(v.x, sigma), 0.0);
-      W[slot * B1 + d] = v;
+      W[e] = v;
     } else {
-      double v = 0.0;
-      if (col + d < n) v = band[d + col * ldab];
+      double v = band[d + j * ldab];
       if (d == 0) v = __dsub_rn(v, sigma);
-      W[slot * B1 + d] = v;
+      W[e] = v;
     }
   }
 }
 
 // One CTA per shift.  Shared memory: pair table (s,u) packed as int32, the
-// multipliers L[0..b], and (if `gwin` is null) the window W[(b+1)*(b+1)].
+// multipliers L[0..b], the ring heads h[0..b] and (if `gwin` is null) the
+// window rings W[(b+1)(b+2)/2].
 template <bool CPLX>
 __global__ void __launch_bounds__(256) inertia_kernel(int64_t n, int b, const double* __restrict__ band,
                                                       int64_t ldab, const double* __restrict__ sigmas,
@@ -107,7 +121,9 @@ __global__ void __launch_bounds__(256) inertia_kernel(int64_t n, int b, const do
   const int npairs = b * (b + 1) / 2;
   int* pairs = (int*)smem;
   T* L = (T*)(smem + (((size_t)npairs * 4 + 15) & ~size_t(15)));
-  T* W = gwin ? (T*)(gwin + gwin_stride * blockIdx.x) : (T*)((char*)L + sizeof(T) * B1);
+  int* h = (int*)(L + B1);
+  T* W = gwin ? (T*)(gwin + gwin_stride * blockIdx.x)
+              : (T*)((char*)h + (((size_t)B1 * sizeof(int) + 15) & ~size_t(15)));
 
   const int sid = blockIdx.x;
   const double sigma = sigmas[sid];
@@ -125,25 +141,44 @@ __global__ void __launch_bounds__(256) inertia_kernel(int64_t n, int b, const do
     }
     pairs[p] = (s << 16) | rem;
   }
-  for (int j = 0; j < B1 && j < n; ++j) load_column<CPLX>(W, B1, j, j, n, b, band, ldab, sigma);
+  for (int d = threadIdx.x; d < B1; d += blockDim.x) h[d] = 0;  // k = 0: 0 mod R_d
+  __syncthreads();
+  // rows 0..b of the first window: entry (r, j) of diagonal d = r - j at ring position j (j < R_d)
+  for (int64_t r = 0; r < B1 && r < n; ++r) {
+    for (int d = threadIdx.x; d <= b; d += blockDim.x) {
+      const int64_t j = r - d;
+      if (j < 0) continue;
+      const int e = ring_base(d, b) + (int)j;
+      if constexpr (CPLX) {
+        const double* pp = band + 2 * (d + j * ldab);
+        double2 v = make_double2(pp[0], pp[1]);
+        if (d == 0) v = make_double2(__dsub_rn(v.x, sigma), 0.0);
+        W[e] = v;
+      } else {
+        double v = band[d + j * ldab];
+        if (d == 0) v = __dsub_rn(v, sigma);
+        W[e] = v;
+      }
+    }
+  }
   __syncthreads();
 
   int64_t neg = 0;
-  int slot_k = 0;
   for (int64_t k = 0; k < n; ++k) {
     const int kmax = (int)((n - 1 - k) < b ? (n - 1 - k) : b);  // rows below k inside the matrix
+    // column k sits at ring position h[d] of every diagonal d
     double dk;
     if constexpr (CPLX)
-      dk = W[slot_k * B1].x;
+      dk = W[h[0]].x;
     else
-      dk = W[slot_k * B1];
+      dk = W[h[0]];
     if (dk == 0.0) dk = -pivmin;
     if (threadIdx.x == 0) {
       if (dk < 0.0) ++neg;
       if (piv_out) piv_out[(int64_t)sid * n + k] = dk;
     }
     for (int d = 1 + threadIdx.x; d <= kmax; d += blockDim.x) {
-      T a = W[slot_k * B1 + d];
+      T a = W[ring_base(d, b) + h[d]];
       if constexpr (CPLX)
         L[d] = make_double2(__ddiv_rn(a.x, dk), __ddiv_rn(a.y, dk));
       else
@@ -154,11 +189,13 @@ __global__ void __launch_bounds__(256) inertia_kernel(int64_t n, int b, const do
       const int pr = pairs[p];
       const int s = pr >> 16, u = pr & 0xffff;
       if (s + u > kmax) continue;
-      int slot_j = slot_k + s;
-      if (slot_j >= B1) slot_j -= B1;
-      T a = W[slot_k * B1 + s];
+      // W(k+s+u, k+s): diagonal u, column k+s -> position h[u] + s (mod R_u; s <= b - u < R_u)
+      int pos = h[u] + s;
+      const int R = B1 - u;
+      if (pos >= R) pos -= R;
+      T a = W[ring_base(s, b) + h[s]];  // W(k+s, k)
       T l = L[s + u];
-      T* e = &W[slot_j * B1 + u];
+      T* e = &W[ring_base(u, b) + pos];
       if constexpr (CPLX) {
         double p1 = __dmul_rn(l.x, a.x);
         double p2 = __dmul_rn(l.y, a.y);
@@ -179,23 +216,28 @@ __global__ void __launch_bounds__(256) inertia_kernel(int64_t n, int b, const do
       }
     }
     __syncthreads();
-    // column k is finished: its slot receives column k + b + 1
-    if (k + B1 < n) load_column<CPLX>(W, B1, slot_k, k + B1, n, b, band, ldab, sigma);
-    if (B1 == 1) __syncthreads();
-    slot_k = slot_k + 1 == B1 ? 0 : slot_k + 1;
+    // column k is finished: advance the ring heads to k + 1 and bring in row k + 1 + b
+    for (int d = threadIdx.x; d < B1; d += blockDim.x) {
+      const int R = B1 - d;
+      h[d] = h[d] + 1 == R ? 0 : h[d] + 1;
+    }
+    __syncthreads();
+    if (k + B1 < n) load_row<CPLX>(W, b, k + B1, k + 1, h, band, ldab, sigma);
+    __syncthreads();
   }
   if (threadIdx.x == 0) neg_out[sid] = neg;
 }
 
 static size_t window_bytes(int b, int cplx) {
-  return (size_t)(b + 1) * (b + 1) * (cplx ? 16 : 8);
+  return (size_t)(b + 1) * (b + 2) / 2 * (cplx ? 16 : 8);
 }
 static size_t inertia_smem_base(int b, int cplx) {
   size_t npairs = (size_t)b * (b + 1) / 2;
-  return ((npairs * 4 + 15) & ~size_t(15)) + (size_t)(b + 1) * (cplx ? 16 : 8);
+  return ((npairs * 4 + 15) & ~size_t(15)) + (size_t)(b + 1) * (cplx ? 16 : 8) +
+         (((size_t)(b + 1) * sizeof(int) + 15) & ~size_t(15));
 }
 static bool window_in_smem(int b, int cplx) {
-  return inertia_smem_base(b, cplx) + window_bytes(b, cplx) <= 200 * 1024;
+  return inertia_smem_base(b, cplx) + window_bytes(b, cplx) <= 226 * 1024;
 }
 
 // Workspace layout: amax bits, nonfinite flag, sigma[], neg[], global windows.
@@ -411,7 +453,7 @@ extern "C" int pdeshep_inertia_noalloc(int64_t n, int32_t b, int32_t is_complex,
   }
   if (!window_in_smem(b, cplx)) {
     set_last_error_msg("pdeshep_inertia_noalloc: band too wide for the shared-memory window "
-                       "(real b <= 141, complex b <= 105)");
+                       "(real b <= 194, complex b <= 149)");
     return -2;
   }
   if (!d_band && n > 0) return -4;

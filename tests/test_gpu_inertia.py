@@ -16,7 +16,11 @@ def device():
 
 
 CASES = [(1, 0, False, 1), (2, 1, True, 2), (37, 3, True, 3), (200, 7, False, 4), (257, 32, False, 5),
-         (300, 64, True, 6), (333, 128, True, 7), (150, 120, False, 8), (64, 63, True, 9), (500, 1, False, 10)]
+         (300, 64, True, 6), (333, 128, True, 7), (150, 120, False, 8), (64, 63, True, 9), (500, 1, False, 10),
+         # widest bands with the window in shared memory, and past it (window in the workspace)
+         (420, 149, True, 11), (450, 194, False, 12), (400, 150, True, 13), (460, 195, False, 14),
+         # n not above b: the window is the whole matrix
+         (100, 149, True, 15)]
 
 
 @pytest.mark.parametrize("n,b,cplx,seed", CASES)

@@ -39,7 +39,7 @@ def test_noalloc_inertia_matches_workspace_version():
     lib = pk.load()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     cases = [(synth.random_band(700, 24, 901, True), 24), (synth.random_band(513, 64, 902, False), 64),
-             (synth.random_band(300, 105, 903, True), 105)]
+             (synth.random_band(300, 149, 903, True), 149), (synth.random_band(400, 194, 906, False), 194)]
     for call, (ab, b) in enumerate(cases + cases[:1]):
         band = to_dev(ab, device)
         rng = np.random.default_rng(call)
@@ -62,8 +62,8 @@ def test_noalloc_inertia_rejects_oversized_requests():
     band = to_dev(synth.random_band(200, 4, 904, False), device)
     st, _ = _noalloc(lib, band, 4, np.zeros(1025), stream)
     assert st == -6 and b"1024" in lib.pdeshep_last_error()
-    wide = to_dev(synth.random_band(300, 106, 905, True), device)
-    st, _ = _noalloc(lib, wide, 106, np.zeros(3), stream)
+    wide = to_dev(synth.random_band(300, 150, 905, True), device)
+    st, _ = _noalloc(lib, wide, 150, np.zeros(3), stream)
     assert st == -2 and b"shared-memory" in lib.pdeshep_last_error()
     st, _ = _noalloc(lib, band, -1, np.zeros(3), stream)
     assert st == -2 and b"negative" in lib.pdeshep_last_error()
