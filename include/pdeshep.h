@@ -67,7 +67,10 @@ typedef struct {
   int32_t max_iter;        /* FEAST iterations per slice; default 20 */
   int32_t precision;       /* PDESHEP_FP64 or PDESHEP_MIXED; default PDESHEP_MIXED */
   int32_t refine_policy;   /* PDESHEP_REFINE_*; default PDESHEP_REFINE_RESIDUAL */
-  int32_t rhs_chunk;       /* right-hand sides per solve work item: 16, 32 or 64; 0 = 32, or the
+  int32_t rhs_chunk;       /* right-hand sides per solve work item: 16, 32 or 64 (a thread per
+                              row of a 32-row tile, the window in shared memory), or 128 (complex64
+                              factors only: a thread per right-hand side, the window in tensor
+                              memory, b <= 128); 0 = 128 where it applies, else 32, or the
                               autotuned width when autotune is on */
   double ellipse_ratio;    /* vertical / horizontal semi-axis of the contour; default 0.3 */
   double bnorm;            /* ||B||_2 for the residual; <= 0: computed by the library */
@@ -82,7 +85,7 @@ typedef struct {
                               iteration */
   int32_t autotune;        /* 0 off; 1 use the tuned choice for this problem shape, measuring
                               it on first use; 2 measure again.  Tuned: the solve column block
-                              (16/32/64, unless rhs_chunk is set) and the split count of the
+                              (16/32/64/128, unless rhs_chunk is set) and the split count of the
                               tall Gram products (2/4/8) */
   int32_t verbose;         /* 0 quiet */
   void* stream;            /* cudaStream_t */

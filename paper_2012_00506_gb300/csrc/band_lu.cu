@@ -23,6 +23,7 @@
 //   of a Hermitian band).  Factor tiles stream from L2/HBM through shared
 //   memory; each is reused by the 32 right-hand sides of the block.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "band_lu.cuh"
@@ -816,6 +817,12 @@ static int launch_solve_cw(const FactorGeom& g, int nitems, const SysDesc* d_sys
 template <typename C>
 int launch_solve_queued(const FactorGeom& g, int trans, int nitems, const SysDesc* d_sys, const char* factor_arena,
                         const C* rhs_arena, C* out_arena, int chunk, void* queue, cudaStream_t st) {
+  if (chunk == kTmChunk) {
+    if constexpr (std::is_same<C, float2>::value)
+      return launch_solve_tm(g, trans, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
+    set_last_error_msg("the 128-column tensor-memory solve is complex64 only");
+    return PDESHEP_CUDA_ERROR;
+  }
   switch (chunk * 2 + (trans ? 1 : 0)) {
     case 32: return launch_solve_cw<C, 16, 0>(g, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
     case 33: return launch_solve_cw<C, 16, 1>(g, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
@@ -835,8 +842,8 @@ int launch_solve(const FactorGeom& g, int trans, int nsys, const SysDesc* h_sys,
                  cudaStream_t st) {
   if (nsys <= 0) return 0;
   if (chunk <= 0) chunk = 32;
-  if (chunk != 16 && chunk != 32 && chunk != 64) {
-    set_last_error_msg("right-hand-side block width must be 16, 32 or 64");
+  if (chunk != 16 && chunk != 32 && chunk != 64 && chunk != kTmChunk) {
+    set_last_error_msg("right-hand-side block width must be 16, 32, 64 or 128");
     return PDESHEP_CUDA_ERROR;
   }
   int nitems = 0;

@@ -87,7 +87,8 @@ int launch_factor(const FactorGeom& g, int cplx, const void* band, int64_t ldab,
 
 // trans = 0: X = (zI-B)^{-1} Y;  trans = 1: X = (zI-B)^{-H} Y.  Y and X hold C.
 // h_sys: the same descriptors on the host (their column counts build the work
-// list).  chunk: right-hand sides per work item (16, 32 or 64; 0 = 32).
+// list).  chunk: right-hand sides per work item (16, 32 or 64; 0 = 32; 128 = the
+// tensor-memory kernel of solve_tm.cu, complex64 only).
 // queue: device scratch of solve_queue_bytes(nsys, max columns).
 template <typename C>
 int launch_solve(const FactorGeom& g, int trans, int nsys, const SysDesc* h_sys, const SysDesc* d_sys,
@@ -103,5 +104,13 @@ int launch_solve_queued(const FactorGeom& g, int trans, int nitems, const SysDes
 
 size_t solve_smem_bytes(const FactorGeom& g, int chunk, size_t es, int trans);
 size_t solve_queue_bytes(int nsys, int max_cols);
+
+// complex64 solves with one thread per right-hand side and the window in tensor memory
+// (solve_tm.cu): work items of kTmChunk columns; bands with bt <= 4 (b <= 128).
+constexpr int kTmChunk = 128;
+bool solve_tm_supported(const FactorGeom& g);
+size_t solve_tm_smem_bytes(const FactorGeom& g);
+int launch_solve_tm(const FactorGeom& g, int trans, int nitems, const SysDesc* d_sys, const char* factor_arena,
+                    const float2* rhs_arena, float2* out_arena, void* queue, cudaStream_t st);
 
 }  // namespace pdeshep

@@ -76,7 +76,9 @@ static int shifted_solve(int64_t n, int b, int cplx, const void* band, int64_t l
   PD_CK(cudaMemcpyAsync(w.sys, sd.data(), sizeof(SysDesc) * nshift, cudaMemcpyHostToDevice, st));
   PD_TRY(launch_cast<double2, C>(n * nrhs, d_rhs, (C*)w.rhs, st));
   PD_TRY(launch_factor<C>(g, cplx, band, ldab, nshift, w.sys, w.factors, w.status, d_ipiv, st));
-  PD_TRY(launch_solve<C>(g, trans, nshift, sd.data(), w.sys, w.factors, (const C*)w.rhs, (C*)w.out, 0, w.queue,
+  // complex64: the tensor-memory solve where its window fits (same arithmetic as the tiled one)
+  const int chunk = (sizeof(C) == sizeof(float2) && solve_tm_supported(g)) ? kTmChunk : 0;
+  PD_TRY(launch_solve<C>(g, trans, nshift, sd.data(), w.sys, w.factors, (const C*)w.rhs, (C*)w.out, chunk, w.queue,
                          st));
   PD_TRY(launch_cast<C, double2>(n * nrhs * nshift, (const C*)w.out, d_x, st));
   std::vector<int> status(nshift);

@@ -610,8 +610,12 @@ struct Feast {
   int gram_splits = 0;  // 0: heuristic
   bool tune_solve = false, tune_gram = false;
 
+  // the default solve: the tensor-memory kernel for complex64 factors when its window fits
+  int default_chunk() const {
+    return (o->precision == PDESHEP_MIXED && solve_tm_supported(g)) ? kTmChunk : 32;
+  }
   void setup_tuning() {
-    rhs_chunk = o->rhs_chunk > 0 ? o->rhs_chunk : 32;
+    rhs_chunk = o->rhs_chunk > 0 ? o->rhs_chunk : default_chunk();
     if (o->autotune <= 0) return;
     int v = 0;
     if (o->rhs_chunk <= 0) {
@@ -1019,9 +1023,11 @@ struct FeastRun : Feast<S, C> {
       PD_CK(cudaEventCreate(&t0));
       PD_CK(cudaEventCreate(&t1));
       float best = 1e30f;
-      int best_cw = 32;
-      for (int cw : {16, 32, 64}) {
-        if (solve_smem_bytes(g, cw, sizeof(C), 0) > 227 * 1024) continue;
+      int best_cw = this->default_chunk();
+      for (int cw : {16, 32, 64, kTmChunk}) {
+        if (cw == kTmChunk ? !(sizeof(C) == sizeof(float2) && solve_tm_supported(g))
+                           : solve_smem_bytes(g, cw, sizeof(C), 0) > 227 * 1024)
+          continue;
         PD_CK(cudaEventRecord(t0, st));
         PD_TRY(launch_solve<C>(g, 0, ns, sd.data(), p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, cw,
                                p.solve_queue, st));
@@ -1539,7 +1545,8 @@ int check_slice_args(int64_t n, int32_t b, const void* d_band, int64_t ldab, int
     if (h_m0[s] < 1 || h_m0[s] > n || h_m0[s] > 4096) return -11;
   if (o && (!(o->tol > 0.0) || o->max_iter < 0 || (o->precision != PDESHEP_FP64 && o->precision != PDESHEP_MIXED) ||
             !(o->ellipse_ratio > 0.0) ||
-            (o->rhs_chunk != 0 && o->rhs_chunk != 16 && o->rhs_chunk != 32 && o->rhs_chunk != 64) ||
+            (o->rhs_chunk != 0 && o->rhs_chunk != 16 && o->rhs_chunk != 32 && o->rhs_chunk != 64 &&
+             o->rhs_chunk != 128) ||
             (o->rr_arith != PDESHEP_RR_FLOATFLOAT && o->rr_arith != PDESHEP_RR_FP64 &&
              o->rr_arith != PDESHEP_RR_TENSOR) || o->autotune < 0 ||
             o->autotune > 2 || (o->m0_resize != 0 && o->m0_resize != 1)))

@@ -153,12 +153,14 @@ def _small_problem(device, cplx, seed=77, n=1200, b=16, ks=(40, 160, 200, 460)):
 @pytest.mark.parametrize("cplx", [False, True])
 def test_rhs_block_width_does_not_change_results(device, cplx):
     """The persistent solves give the same bits for work items of 16, 32 or 64
-    right-hand sides (each column's arithmetic is independent of the grouping)."""
+    right-hand sides (each column's arithmetic is independent of the grouping), and the
+    tensor-memory solve (128 columns, a thread per right-hand side) gives the same bits
+    again: every entry is the same sequence of FP32 FMAs."""
     import paper_2012_00506_gb300 as pk
     ab, bounds, m0, X0 = _small_problem(device, cplx)
     band = to_dev(ab, device)
     outs = []
-    for cw in (16, 32, 64):
+    for cw in (16, 32, 64, 128):
         r = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), precision=pk.MIXED,
                           bnorm=oracle.spectral_norm(ab), rhs_chunk=cw, max_iter=30)
         assert r.status == 0 and r.stats["rhs_chunk_used"] == cw
