@@ -43,7 +43,7 @@ def test_fp64_solve_matches_oracle(device, n, b, cplx, nrhs, trans):
 
 
 @pytest.mark.parametrize("n,b,cplx,nrhs", [(200, 16, True, 40), (300, 64, False, 70), (257, 128, True, 33),
-                                           (1000, 128, True, 300), (70, 100, False, 5), (31, 3, True, 129)])
+                                           (1000, 128, True, 300), (130, 100, False, 5), (31, 3, True, 129)])
 def test_mixed_solve_fp32_class(device, n, b, cplx, nrhs):
     import paper_2012_00506_gb300 as pk
     ab = synth.random_band(n, b, 3000 + n, cplx)
