@@ -156,31 +156,32 @@ __global__ void q_init_kernel(int64_t n, const SliceDesc* sd, const double* __re
 }
 
 // Q[:, slice cols] += sum_{j in [j0,j1)} coef_j X_j^N (+ conj(coef_j) X_j^C), or 2 Re(.) for real B.
+// The node sum runs in the precision of the solves (complex64 solves: FP32 sums, then added to the
+// FP64 subspace): it only adds up FP32-class solutions, and in the refined filter it is the
+// correction term, of the size of the residuals.
 template <typename S, typename C>
 __global__ void accumulate_kernel(int64_t n, const AccDesc* ad, const double2* __restrict__ coef,
                                   const C* __restrict__ X, S* __restrict__ Q, int cplx) {
+  using R = typename real_of<C>::type;
   const AccDesc d = ad[blockIdx.y];
   const int64_t total = n * d.m0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(e / n);
     const int64_t i = e % n;
-    double2 acc = make_double2(0.0, 0.0);
+    C acc = cmk<C>(R(0), R(0));
     for (int j = d.j0; j < d.j1; ++j) {
-      const double2 cf = coef[d.coef_off + (int64_t)j * d.m0 + c];
+      const double2 cd = coef[d.coef_off + (int64_t)j * d.m0 + c];
+      const C cf = cmk<C>((R)cd.x, (R)cd.y);
       const int64_t xo = d.xoff0 + (int64_t)(j - d.j0) * d.xstride + i + (int64_t)c * n;
-      const C xn = X[xo];
-      cfma(acc, cf, make_double2((double)xn.x, (double)xn.y));
-      if (cplx) {
-        const C xc = X[xo + n * (int64_t)d.m0];
-        cfma(acc, cconj(cf), make_double2((double)xc.x, (double)xc.y));
-      }
+      cfma(acc, cf, X[xo]);
+      if (cplx) cfma(acc, cconj(cf), X[xo + n * (int64_t)d.m0]);
     }
     S* q = Q + i + (d.col_off + c) * n;
     if constexpr (std::is_same<S, double>::value) {
-      *q += 2.0 * acc.x;
+      *q += 2.0 * (double)acc.x;
     } else {
-      *q = cadd(*q, acc);
+      *q = cadd(*q, make_double2((double)acc.x, (double)acc.y));
     }
   }
 }
