@@ -614,15 +614,17 @@ def e2e_leg(pk, torch, seq, inputs, stream):
     """Same metric through the C ABI with host buffers: pinned host band and start vectors copied in,
     eigenvalues and eigenvectors copied out, every step inside the timed region."""
     cfg = seq.cfg
-    cols = int(seq.col[cfg.group])
+    gcols = [int(seq.col[(g + 1) * cfg.group] - seq.col[g * cfg.group]) for g in range(cfg.groups)]
+    cols = max(gcols)
     hb = {k: torch.from_numpy(seq.host[k]).pin_memory() for k, _, _, _ in inputs}
     hx = [x0.cpu().pin_memory() if x0 is not None else None for _, _, x0, _ in inputs]
     dband = torch.empty_like(seq.bands[0])
     dx = torch.empty((cols, cfg.n), dtype=torch.complex128, device=seq.dev)
     ev_h = torch.empty(cols, dtype=torch.float64).pin_memory()
     vec_h = torch.empty((cols, cfg.n), dtype=torch.complex128).pin_memory()
-    h2d = hb[inputs[0][0]].numel() * 16 + (hx[0].numel() * 16 if hx[0] is not None else 0)
-    d2h = ev_h.numel() * 8 + vec_h.numel() * 16
+    c0 = gcols[inputs[0][1]]
+    h2d = hb[inputs[0][0]].numel() * 16 + (c0 * cfg.n * 16 if hx[0] is not None else 0)
+    d2h = c0 * 8 + c0 * cfg.n * 16
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -630,13 +632,14 @@ def e2e_leg(pk, torch, seq, inputs, stream):
     pairs = 0
     for i, (k, g, _, bounds) in enumerate(inputs):
         dband.copy_(hb[k], non_blocking=True)
+        cg = gcols[g]
         x0 = None
         if hx[i] is not None:
-            dx.copy_(hx[i], non_blocking=True)
-            x0 = dx
+            x0 = dx[:cg]
+            x0.copy_(hx[i], non_blocking=True)
         r = seq.call(k, g, x0, bounds, pk.MIXED, band=dband)
-        ev_h.copy_(r.evals, non_blocking=True)
-        vec_h.copy_(r.evecs, non_blocking=True)
+        ev_h[:cg].copy_(r.evals, non_blocking=True)
+        vec_h[:cg].copy_(r.evecs, non_blocking=True)
         pairs += good_pairs(r)
     e1.record(stream)
     torch.cuda.synchronize()

@@ -777,6 +777,7 @@ size_t solve_queue_bytes(int nsys, int max_cols) {
 // Work list of (system, first column) items of `chunk` right-hand sides into
 // the queue scratch (counter first, then the items).  Returns the item count.
 int upload_solve_items(int nsys, const SysDesc* h_sys, int chunk, void* queue, cudaStream_t st, int* nitems) {
+  if (chunk == kTcChunk) chunk = kTmChunk;  // the tensor-core solve also takes 128 right-hand sides per item
   std::vector<int2> it;
   for (int s = 0; s < nsys; ++s)
     for (int c = 0; c < h_sys[s].ncols; c += chunk) it.push_back(make_int2(s, c));
@@ -817,10 +818,13 @@ static int launch_solve_cw(const FactorGeom& g, int nitems, const SysDesc* d_sys
 template <typename C>
 int launch_solve_queued(const FactorGeom& g, int trans, int nitems, const SysDesc* d_sys, const char* factor_arena,
                         const C* rhs_arena, C* out_arena, int chunk, void* queue, cudaStream_t st) {
-  if (chunk == kTmChunk) {
-    if constexpr (std::is_same<C, float2>::value)
+  if (chunk == kTmChunk || chunk == kTcChunk) {
+    if constexpr (std::is_same<C, float2>::value) {
+      if (chunk == kTcChunk)
+        return launch_solve_tc(g, trans, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
       return launch_solve_tm(g, trans, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st);
-    set_last_error_msg("the 128-column tensor-memory solve is complex64 only");
+    }
+    set_last_error_msg("the tensor-memory and tensor-core solves are complex64 only");
     return PDESHEP_CUDA_ERROR;
   }
   switch (chunk * 2 + (trans ? 1 : 0)) {
@@ -842,8 +846,8 @@ int launch_solve(const FactorGeom& g, int trans, int nsys, const SysDesc* h_sys,
                  cudaStream_t st) {
   if (nsys <= 0) return 0;
   if (chunk <= 0) chunk = 32;
-  if (chunk != 16 && chunk != 32 && chunk != 64 && chunk != kTmChunk) {
-    set_last_error_msg("right-hand-side block width must be 16, 32, 64 or 128");
+  if (chunk != 16 && chunk != 32 && chunk != 64 && chunk != kTmChunk && chunk != kTcChunk) {
+    set_last_error_msg("right-hand-side block width must be 16, 32, 64, 128 or 256");
     return PDESHEP_CUDA_ERROR;
   }
   int nitems = 0;

@@ -110,7 +110,18 @@ size_t solve_queue_bytes(int nsys, int max_cols);
 constexpr int kTmChunk = 128;
 bool solve_tm_supported(const FactorGeom& g);
 size_t solve_tm_smem_bytes(const FactorGeom& g);
-int launch_solve_tm(const FactorGeom& g, int trans, int nitems, const SysDesc* d_sys, const char* factor_arena,
+// complex64 solves with the tile products on the tcgen05 tensor cores (solve_tc.cu; 3xTF32):
+// work items of kTmChunk columns, selected as the column block kTcChunk; b <= 128.
+constexpr int kTcChunk = 256;
+bool solve_tc_supported(const FactorGeom& g);
+size_t solve_tc_smem_bytes(const FactorGeom& g);
+int launch_solve_tc(const FactorGeom& g, int trans, int nitems, const SysDesc* d_sys, const char* factor_arena,
                     const float2* rhs_arena, float2* out_arena, void* queue, cudaStream_t st);
+// the error word of the tensor-core solve (a bounded wait gave up): read into *h_err (synchronous) and/or clear
+int solve_tc_error(int* h_err, int clear, cudaStream_t st);
+// sweep0/sweep1: the sweeps [sweep0, sweep1) of each item (0: forward, 1: backward; default both)
+int launch_solve_tm(const FactorGeom& g, int trans, int nitems, const SysDesc* d_sys, const char* factor_arena,
+                    const float2* rhs_arena, float2* out_arena, void* queue, cudaStream_t st, int sweep0 = 0,
+                    int sweep1 = 2);
 
 }  // namespace pdeshep

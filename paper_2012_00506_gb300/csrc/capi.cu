@@ -76,11 +76,17 @@ static int shifted_solve(int64_t n, int b, int cplx, const void* band, int64_t l
   PD_CK(cudaMemcpyAsync(w.sys, sd.data(), sizeof(SysDesc) * nshift, cudaMemcpyHostToDevice, st));
   PD_TRY(launch_cast<double2, C>(n * nrhs, d_rhs, (C*)w.rhs, st));
   PD_TRY(launch_factor<C>(g, cplx, band, ldab, nshift, w.sys, w.factors, w.status, d_ipiv, st));
-  // complex64: the tensor-memory solve where its window fits (same arithmetic as the tiled one)
-  const int chunk = (sizeof(C) == sizeof(float2) && solve_tm_supported(g)) ? kTmChunk : 0;
+  // complex64: the tensor-core solve where its window fits
+  const int chunk = (sizeof(C) == sizeof(float2) && solve_tc_supported(g)) ? kTcChunk : 0;
+  if (chunk) PD_TRY(solve_tc_error(nullptr, 1, st));
   PD_TRY(launch_solve<C>(g, trans, nshift, sd.data(), w.sys, w.factors, (const C*)w.rhs, (C*)w.out, chunk, w.queue,
                          st));
   PD_TRY(launch_cast<C, double2>(n * nrhs * nshift, (const C*)w.out, d_x, st));
+  if (chunk) {
+    int e = 0;
+    PD_TRY(solve_tc_error(&e, 1, st));
+    if (e) return PDESHEP_DEVICE_TIMEOUT;
+  }
   std::vector<int> status(nshift);
   PD_CK(cudaMemcpyAsync(status.data(), w.status, sizeof(int) * nshift, cudaMemcpyDeviceToHost, st));
   PD_CK(cudaStreamSynchronize(st));

@@ -1025,9 +1025,10 @@ struct FeastRun : Feast<S, C> {
       PD_CK(cudaEventCreate(&t1));
       float best = 1e30f;
       int best_cw = this->default_chunk();
-      for (int cw : {16, 32, 64, kTmChunk}) {
-        if (cw == kTmChunk ? !(sizeof(C) == sizeof(float2) && solve_tm_supported(g))
-                           : solve_smem_bytes(g, cw, sizeof(C), 0) > 227 * 1024)
+      for (int cw : {16, 32, 64, kTmChunk, kTcChunk}) {
+        if (cw == kTmChunk   ? !(sizeof(C) == sizeof(float2) && solve_tm_supported(g))
+            : cw == kTcChunk ? !(sizeof(C) == sizeof(float2) && solve_tc_supported(g))
+                             : solve_smem_bytes(g, cw, sizeof(C), 0) > 227 * 1024)
           continue;
         PD_CK(cudaEventRecord(t0, st));
         PD_TRY(launch_solve<C>(g, 0, ns, sd.data(), p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, cw,
@@ -1320,6 +1321,7 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   F.factored = false;
   cudaStream_t st = F.st;
   if (F.tc()) PD_TRY(tc_clear_error(F.p.tc, st));
+  if (o->precision == PDESHEP_MIXED) PD_TRY(solve_tc_error(nullptr, 1, st));
 
   cudaEvent_t e0, e1;
   PD_CK(cudaEventCreate(&e0));
@@ -1480,6 +1482,11 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   }
   PD_TRY(read_counts());
   if (F.tc()) PD_TRY(tc_read_error(F.p.tc, st));  // a tensor-core product whose bounded wait gave up
+  if (o->precision == PDESHEP_MIXED) {
+    int e = 0;
+    PD_TRY(solve_tc_error(&e, 0, st));
+    if (e) return PDESHEP_DEVICE_TIMEOUT;
+  }
   if (!F.active.empty()) status = PDESHEP_NOT_CONVERGED;
   // outputs for every slice
   F.active.clear();
@@ -1547,7 +1554,7 @@ int check_slice_args(int64_t n, int32_t b, const void* d_band, int64_t ldab, int
   if (o && (!(o->tol > 0.0) || o->max_iter < 0 || (o->precision != PDESHEP_FP64 && o->precision != PDESHEP_MIXED) ||
             !(o->ellipse_ratio > 0.0) ||
             (o->rhs_chunk != 0 && o->rhs_chunk != 16 && o->rhs_chunk != 32 && o->rhs_chunk != 64 &&
-             o->rhs_chunk != 128) ||
+             o->rhs_chunk != 128 && o->rhs_chunk != 256) ||
             (o->rr_arith != PDESHEP_RR_FLOATFLOAT && o->rr_arith != PDESHEP_RR_FP64 &&
              o->rr_arith != PDESHEP_RR_TENSOR) || o->autotune < 0 ||
             o->autotune > 2 || (o->m0_resize != 0 && o->m0_resize != 1)))

@@ -342,7 +342,8 @@ __device__ __forceinline__ void permute_window(Half& top, const float* old, SrcF
 template <int TRANS>
 __global__ void __launch_bounds__(kTmThreads, 1)
     solve_tm_kernel(FactorGeom g, const SysDesc* sys, const char* arena, const float2* rhs, float2* out,
-                    const int2* items, int nitems, int* counter, uint32_t tmem_cols, int max_tiles) {
+                    const int2* items, int nitems, int* counter, uint32_t tmem_cols, int max_tiles, int sweep0,
+                    int sweep1) {
   extern __shared__ __align__(16) char smem[];
   const int Pmax = (g.bt + 1) * kTile;
   float2* tbuf0 = (float2*)smem;                               // 2 buffers of max_tiles tiles
@@ -388,17 +389,17 @@ __global__ void __launch_bounds__(kTmThreads, 1)
     const bool valid = col < d.ncols;
     const float2* Y = rhs + d.rhs_off + (int64_t)(valid ? col : 0) * n;
     float2* X = out + (TRANS == 0 ? d.out_off : d.out2_off) + (int64_t)(valid ? col : 0) * n;
-    const int nsteps = 2 * Nb;
+    const int s_begin = sweep0 * Nb, nsteps = sweep1 * Nb;  // the sweeps [sweep0, sweep1) of the item
 
-    prefetch_step<TRANS>(g, f, 0, tbuf0, pbuf0);
-    if (TRANS == 0) {  // the first window of the forward sweep: blocks 0 .. min(bt, Nb-1) of Y
+    prefetch_step<TRANS>(g, f, s_begin, (s_begin & 1) ? tbuf1 : tbuf0, (s_begin & 1) ? pbuf1 : pbuf0);
+    if (TRANS == 0 && sweep0 == 0) {  // the first window of the forward sweep: blocks 0 .. min(bt, Nb-1) of Y
       Half y;
       for (int q = 0; q <= min(bt, Nb - 1); ++q) {
         half_from_global(y, Y, n, (int64_t)q * kTile + 16 * h, valid);
         half_to_tm(y, tb, blk_col(q, nslot_w), h);
       }
     }
-    for (int s = 0; s < nsteps; ++s) {
+    for (int s = s_begin; s < nsteps; ++s) {
       float2* tbs = (s & 1) ? tbuf1 : tbuf0;
       int16_t* pb = (s & 1) ? pbuf1 : pbuf0;
       asm volatile("cp.async.wait_group 0;\n" ::);
@@ -519,7 +520,7 @@ size_t solve_tm_smem_bytes(const FactorGeom& g) {
 }
 
 int launch_solve_tm(const FactorGeom& g, int trans, int nitems, const SysDesc* d_sys, const char* factor_arena,
-                    const float2* rhs_arena, float2* out_arena, void* queue, cudaStream_t st) {
+                    const float2* rhs_arena, float2* out_arena, void* queue, cudaStream_t st, int sweep0, int sweep1) {
   if (!nitems) return 0;
   if (!solve_tm_supported(g)) {
     set_last_error_msg("band too wide for the tensor-memory solve window");
@@ -540,11 +541,11 @@ int launch_solve_tm(const FactorGeom& g, int trans, int nitems, const SysDesc* d
   if (trans) {
     PD_CK(cudaFuncSetAttribute(solve_tm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     solve_tm_kernel<1><<<grid, kTmThreads, smem, st>>>(g, d_sys, factor_arena, rhs_arena, out_arena, d_items, nitems,
-                                                       counter, cols, max_tiles);
+                                                       counter, cols, max_tiles, sweep0, sweep1);
   } else {
     PD_CK(cudaFuncSetAttribute(solve_tm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     solve_tm_kernel<0><<<grid, kTmThreads, smem, st>>>(g, d_sys, factor_arena, rhs_arena, out_arena, d_items, nitems,
-                                                       counter, cols, max_tiles);
+                                                       counter, cols, max_tiles, sweep0, sweep1);
   }
   PD_CK_LAUNCH();
   return 0;
