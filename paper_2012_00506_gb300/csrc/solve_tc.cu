@@ -153,35 +153,57 @@ __device__ __forceinline__ void write_a_row(unsigned char* Ahi, unsigned char* A
   }
 }
 
-// Register prefetch of one factor tile: thread t holds T(i, j) for i = t % 32, j = 8 (t / 32) + jj.
+// Register prefetch of one factor tile as M = T (CT = false) or M = T^H (CT = true): thread t holds
+// M(r, c0..c0+7) with r = t % 32, c0 = 8 (t / 32) (for M = T the 32 lanes read 32 consecutive rows
+// of a column: coalesced).
 struct TileRegs {
   float2 v[8];
 };
-__device__ __forceinline__ void tile_fetch(TileRegs& r, const float2* __restrict__ T) {
-  const int i = threadIdx.x & 31, j0 = 8 * (threadIdx.x >> 5);
-#pragma unroll
-  for (int jj = 0; jj < 8; ++jj) r.v[jj] = T[i + 32 * (j0 + jj)];
-}
-// B (TF32 high and low parts) of the embedded tile: M = T (CT = false) or M = T^H (CT = true),
-// B[n][k] = s [[Mr, -Mi], [Mi, Mr]] with n = output row (re 0..31, im 32..63), k = input (re, im)
 template <bool CT>
-__device__ __forceinline__ void write_b(unsigned char* Bhi, unsigned char* Blo, const TileRegs& r, float s) {
-  const int i = threadIdx.x & 31, j0 = 8 * (threadIdx.x >> 5);
+__device__ __forceinline__ void tile_fetch(TileRegs& r, const float2* __restrict__ T) {
+  const int i = threadIdx.x & 31, c0 = 8 * (threadIdx.x >> 5);
 #pragma unroll
   for (int jj = 0; jj < 8; ++jj) {
-    const int row = CT ? j0 + jj : i, col = CT ? i : j0 + jj;  // M(row, col)
-    const float mr = s * r.v[jj].x, mi = s * (CT ? -r.v[jj].y : r.v[jj].y);
-    const float vals[4] = {mr, -mi, mi, mr};
-    const int ns[4] = {row, row, 32 + row, 32 + row};
-    const int ks[4] = {col, 32 + col, col, 32 + col};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const uint32_t h = tf32_hi(vals[e]);
-      const uint32_t l = tf32_hi(vals[e] - __uint_as_float(h));
-      const uint32_t off = sw_off(ns[e], ks[e], kBRows);
-      *(uint32_t*)(Bhi + off) = h;
-      *(uint32_t*)(Blo + off) = l;
+    if (CT) {
+      const float2 v = T[(c0 + jj) + 32 * i];
+      r.v[jj] = make_float2(v.x, -v.y);
+    } else {
+      r.v[jj] = T[i + 32 * (c0 + jj)];
     }
+  }
+}
+// four values -> TF32 high and low granules at byte offset off
+__device__ __forceinline__ void put_granule(unsigned char* Bhi, unsigned char* Blo, uint32_t off, float a, float b,
+                                            float c, float d) {
+  const float v[4] = {a, b, c, d};
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    h[e] = tf32_hi(v[e]);
+    l[e] = tf32_hi(v[e] - __uint_as_float(h[e]));
+  }
+  *(uint4*)(Bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *(uint4*)(Blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+// B (TF32 high and low parts) of the embedded tile: B[n][k] = s [[Mr, -Mi], [Mi, Mr]],
+// n = output row (re 0..31, im 32..63), k = input (re 0..31, im 32..63); 16-byte granules
+__device__ __forceinline__ void write_b(unsigned char* Bhi, unsigned char* Blo, const TileRegs& t, float s) {
+  const int r = threadIdx.x & 31, c0 = 8 * (threadIdx.x >> 5);
+  float mr[8], mi[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    mr[j] = s * t.v[j].x;
+    mi[j] = s * t.v[j].y;
+  }
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const int k = c0 + 4 * g;
+    const float* R = mr + 4 * g;
+    const float* I = mi + 4 * g;
+    put_granule(Bhi, Blo, sw_off(r, k, kBRows), R[0], R[1], R[2], R[3]);
+    put_granule(Bhi, Blo, sw_off(r, 32 + k, kBRows), -I[0], -I[1], -I[2], -I[3]);
+    put_granule(Bhi, Blo, sw_off(32 + r, k, kBRows), I[0], I[1], I[2], I[3]);
+    put_granule(Bhi, Blo, sw_off(32 + r, 32 + k, kBRows), R[0], R[1], R[2], R[3]);
   }
 }
 
@@ -254,6 +276,13 @@ struct Sync {
   uint32_t bar_b[2], bar_x, bar_step;
   int uses_b[2], nx, nstep;
   int* sh_bad;
+  // a bounded wait without a barrier: a give-up is recorded for the next barrier to see
+  __device__ void wait_nb(uint32_t bar, int k) {
+    if (!mbar_wait(bar, (uint32_t)((k - 1) & 1))) {
+      atomicExch(&g_tc_solve_err, 1);
+      *sh_bad = 1;
+    }
+  }
   // a CTA-uniform bounded wait for the k-th completion (k >= 1) of bar
   __device__ bool wait(uint32_t bar, int k) {
     bool ok = mbar_wait(bar, (uint32_t)((k - 1) & 1));
@@ -317,17 +346,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   // B buffer `cur` <- tile (after the MMA that last read it), then the tile's MMA group into TMEM
   // column d; returns false if a wait gave up
-  auto issue_tile = [&](const TileRegs& tr, bool ct, float s, uint32_t d, bool accumulate, bool commit_x,
+  auto issue_tile = [&](const TileRegs& tr, float s, uint32_t d, bool accumulate, bool commit_x,
                         bool commit_step) -> bool {
     const int b = cur;
-    if (sy.uses_b[b] > 0 && !sy.wait(sy.bar_b[b], sy.uses_b[b])) return false;
-    if (ct)
-      write_b<true>(Bhi[b], Blo[b], tr, s);
-    else
-      write_b<false>(Bhi[b], Blo[b], tr, s);
+    // the MMA that last read this buffer (two groups ago) is normally long done; a wait that
+    // gives up is seen by every thread after the barrier below
+    if (sy.uses_b[b] > 0) sy.wait_nb(sy.bar_b[b], sy.uses_b[b]);
+    write_b(Bhi[b], Blo[b], tr, s);
     proxy_fence();
     tc_fence_before();
     __syncthreads();
+    if (sh_bad) return false;
     if (t == 0) {
       tc_fence_after();
       mma_group(tbase + d, ahi, alo, smem_u32(Bhi[b]), smem_u32(Blo[b]), accumulate);
@@ -376,7 +405,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
         tc_fence_after();
         for (int r = t; r < P; r += kTcThreads) perm[r] = f.perm[(int64_t)K * Pmax + r];
-        tile_fetch(tr, f.inv + (int64_t)(2 * K) * g.tile_elems);
+        tile_fetch<false>(tr, f.inv + (int64_t)(2 * K) * g.tile_elems);
         const uint32_t top = (uint32_t)(64 * (K % ringw));
         blk_from_tm(v, tb + top);
 #pragma unroll
@@ -416,23 +445,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tm_wait_st();
         // x_K = Linv_K g (A's previous readers, the last step's updates, finished with bar_step)
         write_a(v);
-        if (!issue_tile(tr, false, 1.f, scratch, false, true, nbb == 0)) { alive = false; break; }
-        if (nbb >= 1) tile_fetch(tr, tile_of(K + 1, K));
+        if (!issue_tile(tr, 1.f, scratch, false, true, nbb == 0)) { alive = false; break; }
+        if (nbb >= 1) tile_fetch<false>(tr, tile_of(K + 1, K));
         if (!sy.wait(sy.bar_x, sy.nx)) { alive = false; break; }
         tc_fence_after();
         blk_from_tm(x, tb + scratch);
-        blk_to_global(x, X, n, (int64_t)K * kTile, valid);
         write_a(x);
         for (int q = 1; q <= nbb; ++q) {
           const TileRegs cur_t = tr;
-          if (q < nbb) tile_fetch(tr, tile_of(K + q + 1, K));
-          if (!issue_tile(cur_t, false, -1.f, (uint32_t)(64 * ((K + q) % ringw)), true, false, q == nbb)) {
+          if (q < nbb) tile_fetch<false>(tr, tile_of(K + q + 1, K));
+          if (!issue_tile(cur_t, -1.f, (uint32_t)(64 * ((K + q) % ringw)), true, false, q == nbb)) {
             alive = false;
             break;
           }
+          if (q == 1) blk_to_global(x, X, n, (int64_t)K * kTile, valid);  // while the first update runs
         }
         if (!alive) break;
-        if (K + bt + 1 < Nb) {  // block K+bt+1 of Y enters the slot block K leaves
+        if (nbb == 0) blk_to_global(x, X, n, (int64_t)K * kTile, valid);
+        if (K + bt + 1 < Nb) {  // block K+bt+1 of Y enters the slot block K leaves (no update writes it)
           blk_from_global(v, Y, n, (int64_t)(K + bt + 1) * kTile, valid);
           blk_to_tm(v, tb + top);
         }
@@ -450,28 +480,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t sk = (uint32_t)(64 * (K % rings));
         if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
         tc_fence_after();
-        tile_fetch(tr, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
+        tile_fetch<false>(tr, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
         blk_from_tm(v, tb + sk);  // acc_K is complete
         write_a(v);
-        if (!issue_tile(tr, false, 1.f, sk, false, true, nq == 0)) { alive = false; break; }
-        if (nq >= 1) tile_fetch(tr, tile_of(K - 1, K));
+        if (!issue_tile(tr, 1.f, sk, false, true, nq == 0)) { alive = false; break; }
+        if (nq >= 1) tile_fetch<false>(tr, tile_of(K - 1, K));
         if (!sy.wait(sy.bar_x, sy.nx)) { alive = false; break; }
         tc_fence_after();
         blk_from_tm(x, tb + sk);
-        blk_to_global(x, X, n, (int64_t)K * kTile, valid);
         write_a(x);
-        if (K - rings >= 0) {  // block K-2bt enters the pending ring in the slot block K leaves
-          blk_from_global(v, X, n, (int64_t)(K - rings) * kTile, valid);
-          blk_to_tm(v, tb + sk);
-        }
         for (int q = 1; q <= nq; ++q) {
           const TileRegs cur_t = tr;
-          if (q < nq) tile_fetch(tr, tile_of(K - q - 1, K));
-          if (!issue_tile(cur_t, false, -1.f, (uint32_t)(64 * ((K - q) % rings)), true, false, q == nq)) {
+          if (q < nq) tile_fetch<false>(tr, tile_of(K - q - 1, K));
+          if (!issue_tile(cur_t, -1.f, (uint32_t)(64 * ((K - q) % rings)), true, false, q == nq)) {
             alive = false;
             break;
           }
+          if (q == 1) {  // while the first update runs: x_K out, and block K-2bt enters the slot K leaves
+            blk_to_global(x, X, n, (int64_t)K * kTile, valid);
+            if (K - rings >= 0) {
+              blk_from_global(v, X, n, (int64_t)(K - rings) * kTile, valid);
+              blk_to_tm(v, tb + sk);
+            }
+          }
         }
+        if (nq == 0) blk_to_global(x, X, n, (int64_t)K * kTile, valid);
       }
     } else {
       // ======================= adjoint forward: U^H =======================
@@ -484,28 +517,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t sk = (uint32_t)(64 * (K % rings));
         if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
         tc_fence_after();
-        tile_fetch(tr, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
+        tile_fetch<true>(tr, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
         blk_from_tm(v, tb + sk);
         write_a(v);
-        if (!issue_tile(tr, true, 1.f, sk, false, true, nq == 0)) { alive = false; break; }
-        if (nq >= 1) tile_fetch(tr, tile_of(K, K + 1));
+        if (!issue_tile(tr, 1.f, sk, false, true, nq == 0)) { alive = false; break; }
+        if (nq >= 1) tile_fetch<true>(tr, tile_of(K, K + 1));
         if (!sy.wait(sy.bar_x, sy.nx)) { alive = false; break; }
         tc_fence_after();
         blk_from_tm(x, tb + sk);
-        blk_to_global(x, X, n, (int64_t)K * kTile, valid);
         write_a(x);
-        if (K + rings < Nb) {  // block K+2bt enters the pending ring in the slot block K leaves
-          blk_from_global(v, Y, n, (int64_t)(K + rings) * kTile, valid);
-          blk_to_tm(v, tb + sk);
-        }
         for (int q = 1; q <= nq; ++q) {
           const TileRegs cur_t = tr;
-          if (q < nq) tile_fetch(tr, tile_of(K, K + q + 1));
-          if (!issue_tile(cur_t, true, -1.f, (uint32_t)(64 * ((K + q) % rings)), true, false, q == nq)) {
+          if (q < nq) tile_fetch<true>(tr, tile_of(K, K + q + 1));
+          if (!issue_tile(cur_t, -1.f, (uint32_t)(64 * ((K + q) % rings)), true, false, q == nq)) {
             alive = false;
             break;
           }
+          if (q == 1) {  // while the first update runs: w_K out, and block K+2bt enters the slot K leaves
+            blk_to_global(x, X, n, (int64_t)K * kTile, valid);
+            if (K + rings < Nb) {
+              blk_from_global(v, Y, n, (int64_t)(K + rings) * kTile, valid);
+              blk_to_tm(v, tb + sk);
+            }
+          }
         }
+        if (nq == 0) blk_to_global(x, X, n, (int64_t)K * kTile, valid);
       }
     }
     if (!alive) break;
