@@ -207,6 +207,18 @@ __device__ __forceinline__ void write_b(unsigned char* Bhi, unsigned char* Blo, 
   }
 }
 
+// L2 prefetch of `lines` 128-byte lines from p, spread over the CTA's threads (offset by `slot`)
+__device__ __forceinline__ void l2_prefetch(const void* p, int lines, int slot) {
+  for (int l = (threadIdx.x + slot * 37) % kTcThreads; l < lines; l += kTcThreads)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)p + 128 * l));
+}
+// this thread's right-hand side, rows row0..row0+31 (two lines)
+__device__ __forceinline__ void l2_prefetch_rows(const float2* X, int64_t n, int64_t row0, bool valid) {
+  if (!valid || row0 >= n) return;
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(X + row0));
+  if (row0 + 16 < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(X + row0 + 16));
+}
+
 // the 3xTF32 product of one tile: 8 K-steps of 8, three MMAs each
 __device__ __forceinline__ void mma_group(uint32_t d, uint32_t ahi, uint32_t alo, uint32_t bhi, uint32_t blo,
                                           bool accumulate) {
@@ -405,6 +417,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
         tc_fence_after();
         for (int r = t; r < P; r += kTcThreads) perm[r] = f.perm[(int64_t)K * Pmax + r];
+        if (K + 1 < Nb) {  // the next step's tiles, permutation and entering block toward L2
+          const int nb1 = min(bt, Nb - 2 - K);
+          l2_prefetch(f.inv + (int64_t)(2 * (K + 1)) * g.tile_elems, 64, 0);
+          for (int q = 1; q <= nb1; ++q) l2_prefetch(tile_of(K + 1 + q, K + 1), 64, q);
+          l2_prefetch(f.perm + (int64_t)(K + 1) * Pmax, (Pmax * 2 + 127) / 128, 7);
+          l2_prefetch_rows(Y, n, (int64_t)(K + bt + 2) * kTile, valid);
+        }
         tile_fetch<false>(tr, f.inv + (int64_t)(2 * K) * g.tile_elems);
         const uint32_t top = (uint32_t)(64 * (K % ringw));
         blk_from_tm(v, tb + top);
@@ -481,6 +500,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
         tc_fence_after();
         tile_fetch<false>(tr, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
+        if (K >= 1) {  // the next step's tiles and entering block toward L2
+          const int nq1 = min(rings, K - 1);
+          l2_prefetch(f.inv + (int64_t)(2 * (K - 1) + 1) * g.tile_elems, 64, 0);
+          for (int q = 1; q <= nq1; ++q) l2_prefetch(tile_of(K - 1 - q, K - 1), 64, q);
+          if (K - 1 - rings >= 0) l2_prefetch_rows(X, n, (int64_t)(K - 1 - rings) * kTile, valid);
+        }
         blk_from_tm(v, tb + sk);  // acc_K is complete
         write_a(v);
         if (!issue_tile(tr, 1.f, sk, false, true, nq == 0)) { alive = false; break; }
@@ -518,6 +543,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
         tc_fence_after();
         tile_fetch<true>(tr, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
+        if (K + 1 < Nb) {  // the next step's tiles and entering block toward L2
+          const int nq1 = min(rings, Nb - 2 - K);
+          l2_prefetch(f.inv + (int64_t)(2 * (K + 1) + 1) * g.tile_elems, 64, 0);
+          for (int q = 1; q <= nq1; ++q) l2_prefetch(tile_of(K + 1, K + 1 + q), 64, q);
+          if (K + 1 + rings < Nb) l2_prefetch_rows(Y, n, (int64_t)(K + 1 + rings) * kTile, valid);
+        }
         blk_from_tm(v, tb + sk);
         write_a(v);
         if (!issue_tile(tr, 1.f, sk, false, true, nq == 0)) { alive = false; break; }
