@@ -187,8 +187,22 @@ __device__ __forceinline__ void put_granule(unsigned char* Bhi, unsigned char* B
 }
 // B (TF32 high and low parts) of the embedded tile: B[n][k] = s [[Mr, -Mi], [Mi, Mr]],
 // n = output row (re 0..31, im 32..63), k = input (re 0..31, im 32..63); 16-byte granules
-__device__ __forceinline__ void write_b(unsigned char* Bhi, unsigned char* Blo, const TileRegs& t, float s) {
-  const int r = threadIdx.x & 31, c0 = 8 * (threadIdx.x >> 5);
+struct BOffsets {  // this thread's 8 granule offsets in a B part (constant per thread)
+  uint32_t o[8];
+  __device__ void init() {
+    const int r = threadIdx.x & 31, c0 = 8 * (threadIdx.x >> 5);
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int k = c0 + 4 * g;
+      o[4 * g + 0] = sw_off(r, k, kBRows);
+      o[4 * g + 1] = sw_off(r, 32 + k, kBRows);
+      o[4 * g + 2] = sw_off(32 + r, k, kBRows);
+      o[4 * g + 3] = sw_off(32 + r, 32 + k, kBRows);
+    }
+  }
+};
+__device__ __forceinline__ void write_b(unsigned char* Bhi, unsigned char* Blo, const TileRegs& t, float s,
+                                        const BOffsets& bo) {
   float mr[8], mi[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -197,13 +211,12 @@ __device__ __forceinline__ void write_b(unsigned char* Bhi, unsigned char* Blo, 
   }
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
-    const int k = c0 + 4 * g;
     const float* R = mr + 4 * g;
     const float* I = mi + 4 * g;
-    put_granule(Bhi, Blo, sw_off(r, k, kBRows), R[0], R[1], R[2], R[3]);
-    put_granule(Bhi, Blo, sw_off(r, 32 + k, kBRows), -I[0], -I[1], -I[2], -I[3]);
-    put_granule(Bhi, Blo, sw_off(32 + r, k, kBRows), I[0], I[1], I[2], I[3]);
-    put_granule(Bhi, Blo, sw_off(32 + r, 32 + k, kBRows), R[0], R[1], R[2], R[3]);
+    put_granule(Bhi, Blo, bo.o[4 * g + 0], R[0], R[1], R[2], R[3]);
+    put_granule(Bhi, Blo, bo.o[4 * g + 1], -I[0], -I[1], -I[2], -I[3]);
+    put_granule(Bhi, Blo, bo.o[4 * g + 2], I[0], I[1], I[2], I[3]);
+    put_granule(Bhi, Blo, bo.o[4 * g + 3], R[0], R[1], R[2], R[3]);
   }
 }
 
@@ -219,16 +232,18 @@ __device__ __forceinline__ void l2_prefetch_rows(const float2* X, int64_t n, int
   if (row0 + 16 < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(X + row0 + 16));
 }
 
-// the 3xTF32 product of one tile: 8 K-steps of 8, three MMAs each
-__device__ __forceinline__ void mma_group(uint32_t d, uint32_t ahi, uint32_t alo, uint32_t bhi, uint32_t blo,
+// the 3xTF32 product of one tile: 8 K-steps of 8, three MMAs each.  The descriptor of K-step s is
+// the base descriptor plus the step's byte offset / 16 (the start-address field; no carry out of
+// it below 256 KiB of shared memory).
+__device__ __forceinline__ void mma_group(uint32_t d, uint64_t dahi, uint64_t dalo, uint64_t dbhi, uint64_t dblo,
                                           bool accumulate) {
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
-    const uint32_t ka = (uint32_t)((s >> 1) * (kARows * 64) + (s & 1) * 32);
-    const uint32_t kb = (uint32_t)((s >> 1) * (kBRows * 64) + (s & 1) * 32);
-    mma_tf32(d, sw64_desc(ahi + ka), sw64_desc(bhi + kb), (accumulate || s > 0) ? 1u : 0u);
-    mma_tf32(d, sw64_desc(ahi + ka), sw64_desc(blo + kb), 1u);
-    mma_tf32(d, sw64_desc(alo + ka), sw64_desc(bhi + kb), 1u);
+    const uint64_t ka = (uint64_t)(((s >> 1) * (kARows * 64) + (s & 1) * 32) >> 4);
+    const uint64_t kb = (uint64_t)(((s >> 1) * (kBRows * 64) + (s & 1) * 32) >> 4);
+    mma_tf32(d, dahi + ka, dbhi + kb, (accumulate || s > 0) ? 1u : 0u);
+    mma_tf32(d, dahi + ka, dblo + kb, 1u);
+    mma_tf32(d, dalo + ka, dbhi + kb, 1u);
   }
 }
 
@@ -347,13 +362,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tbase = tslot;                          // lane 0, column 0 (MMA destinations)
   const uint32_t tb = tslot + ((uint32_t)(32 * warp) << 16);  // this thread's lane quadrant
-  const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
+  const uint64_t da_hi = sw64_desc(smem_u32(Ahi)), da_lo = sw64_desc(smem_u32(Alo));
+  const uint64_t db_hi[2] = {sw64_desc(smem_u32(Bhi[0])), sw64_desc(smem_u32(Bhi[1]))};
+  const uint64_t db_lo[2] = {sw64_desc(smem_u32(Blo[0])), sw64_desc(smem_u32(Blo[1]))};
   float* myo = orow + t * kSRow;
   const int bt = g.bt, Nb = g.Nb;
   const int64_t n = g.n;
   const int ringw = bt + 1, rings = 2 * bt;
   const uint32_t scratch = (uint32_t)(64 * ringw);       // forward: x_K's TMEM block after the window
   int cur = 0;                                           // B buffer for the next tile
+  BOffsets boff;
+  boff.init();
   bool alive = true;
 
   // B buffer `cur` <- tile (after the MMA that last read it), then the tile's MMA group into TMEM
@@ -364,14 +383,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // the MMA that last read this buffer (two groups ago) is normally long done; a wait that
     // gives up is seen by every thread after the barrier below
     if (sy.uses_b[b] > 0) sy.wait_nb(sy.bar_b[b], sy.uses_b[b]);
-    write_b(Bhi[b], Blo[b], tr, s);
+    write_b(Bhi[b], Blo[b], tr, s, boff);
     proxy_fence();
     tc_fence_before();
     __syncthreads();
     if (sh_bad) return false;
     if (t == 0) {
       tc_fence_after();
-      mma_group(tbase + d, ahi, alo, smem_u32(Bhi[b]), smem_u32(Blo[b]), accumulate);
+      mma_group(tbase + d, da_hi, da_lo, db_hi[b], db_lo[b], accumulate);
       tc_commit(sy.bar_b[b]);
       if (commit_x) tc_commit(sy.bar_x);
       if (commit_step) tc_commit(sy.bar_step);
