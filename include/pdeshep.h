@@ -359,6 +359,20 @@ int pdeshep_restart_plan(int64_t nprev, const double* h_prev_vals, int32_t K, co
                          const int32_t* h_m0, int32_t mode, int64_t* h_src);
 
 /* ------------------------------------------------------------------------ */
+/* The start block of a re-sliced call from a restart plan (the device side  */
+/* of pdeshep_restart_plan, Section 3.1): column j of d_dst (n x ncols,       */
+/* column-major, the band's type) is column h_src[j] of d_prev (n x nprev)    */
+/* when h_src[j] >= 0, else column col0 + j of the library's start-vector    */
+/* stream with this seed (pdeshep_random_start's columns: the random vectors */
+/* interlaced with the previous ones).  h_src[j] < nprev (else -6).          */
+/* d_work: pdeshep_gather_columns_workspace_size(ncols) bytes.  Asynchronous. */
+/* ------------------------------------------------------------------------ */
+size_t pdeshep_gather_columns_workspace_size(int32_t ncols);
+int pdeshep_gather_columns(int64_t n, int32_t is_complex, const void* d_prev, int64_t nprev, int32_t ncols,
+                           const int64_t* h_src, uint64_t seed, int64_t col0, void* d_dst, void* d_work,
+                           size_t work_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Outer bounds of the wanted eigenvalues i0 .. i0+nev-1 of the band from the */
 /* previous matrix's eigenvalues h_prev[nprev] (ascending) (Section 3.2,      */
 /* Algorithm 4 and the lower-bound search described beside it): bK starts at  */

@@ -58,7 +58,7 @@ EXPORTED = [
     "pdeshep_band_matmul_tc_workspace_size", "pdeshep_band_matmul_tc",
     "pdeshep_partition", "pdeshep_outer_bounds_workspace_size", "pdeshep_outer_bounds",
     "pdeshep_restart_plan", "pdeshep_random_start", "pdeshep_equal_count_targets_workspace_size",
-    "pdeshep_equal_count_targets",
+    "pdeshep_equal_count_targets", "pdeshep_gather_columns_workspace_size", "pdeshep_gather_columns",
 ]
 
 
@@ -153,6 +153,8 @@ def load(path: str = LIB_PATH):
         "pdeshep_restart_plan": (C.c_int, [i64, P, i32, P, P, i32, P]),
         "pdeshep_random_start": (C.c_int, [i64, i32, i64, i32, C.c_uint64, P, P]),
         "pdeshep_alu_peak": (C.c_int, [i32, i64, P, P, P]),
+        "pdeshep_gather_columns_workspace_size": (sz, [i32]),
+        "pdeshep_gather_columns": (C.c_int, [i64, i32, P, i64, i32, P, C.c_uint64, i64, P, P, sz, P]),
         "pdeshep_equal_count_targets_workspace_size": (sz, [i64, i32, i32, i32, i32]),
         "pdeshep_equal_count_targets": (C.c_int, [i64, i32, i32, P, i64, i32, dbl, i32, P, P, sz, P]),
         "pdeshep_outer_bounds_workspace_size": (sz, [i64, i32, i32]),
@@ -381,6 +383,22 @@ def restart_plan(prev_vals, bounds, m0, mode=0):
     st = lib.pdeshep_restart_plan(v.size, _np_ptr(v), m.size, _np_ptr(bd), _np_ptr(m), int(mode), _np_ptr(src))
     _check("pdeshep_restart_plan", st)
     return np.split(src, np.cumsum(m)[:-1])
+
+
+def gather_columns(prev, src, n=None, seed=0, col0=0, stream=None):
+    """The start block (ncols, n) of a re-sliced call: row j is row src[j] of ``prev`` (a (nprev, n)
+    tensor of previous eigenvectors) or, for src[j] < 0, column col0 + j of the library's start-vector
+    stream (the device side of ``restart_plan``)."""
+    torch = _torch()
+    lib = load()
+    src = np.ascontiguousarray(np.asarray(src, dtype=np.int64).reshape(-1))
+    nprev, nn = prev.shape
+    out = torch.empty((src.size, nn), dtype=prev.dtype, device=prev.device)
+    ws = _workspace(lib.pdeshep_gather_columns_workspace_size(src.size), prev.device)
+    st = lib.pdeshep_gather_columns(nn, int(prev.is_complex()), _ptr(prev), nprev, src.size, _np_ptr(src),
+                                    C.c_uint64(seed), int(col0), _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
+    _check("pdeshep_gather_columns", st)
+    return out
 
 
 def outer_bounds(band, prev, i0, nev, alpha=1e-3, m_hat=6.0, max_it=64, b=None, stream=None):

@@ -27,6 +27,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -245,4 +246,66 @@ extern "C" int pdeshep_outer_bounds(int64_t n, int32_t b, int32_t is_complex, co
   // a search that used its max_it counts without reaching its target leaves bounds
   // that do not enclose the wanted eigenvalues
   return hi_ok && lo_ok ? 0 : PDESHEP_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// The start block of a re-sliced call from a restart plan, on the device:
+// column j of d_dst is column h_src[j] of d_prev, or (h_src[j] < 0) column
+// col0 + j of the library's start-vector stream (the random vectors that
+// interlace the previous ones, Section 3.1).
+// ---------------------------------------------------------------------------
+namespace pdeshep {
+namespace {
+template <typename S>
+__global__ void gather_columns_kernel(int64_t n, int ncols, const int64_t* __restrict__ src, const S* __restrict__ prev,
+                                      int64_t col0, uint64_t seed, S* __restrict__ dst) {
+  const int64_t total = n * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / n, i = e % n;
+    const int64_t sc = src[c];
+    if (sc >= 0) {
+      dst[e] = prev[i + sc * n];
+    } else {
+      const uint64_t k = (uint64_t)((col0 + c) * n + i);
+      if constexpr (std::is_same<S, double>::value)
+        dst[e] = uniform_pm1(splitmix64(seed + k));
+      else
+        dst[e] = make_double2(uniform_pm1(splitmix64(seed + 2 * k)), uniform_pm1(splitmix64(seed + 2 * k + 1)));
+    }
+  }
+}
+}  // namespace
+}  // namespace pdeshep
+
+extern "C" size_t pdeshep_gather_columns_workspace_size(int32_t ncols) {
+  return ncols > 0 ? (((size_t)ncols * sizeof(int64_t) + 255) & ~size_t(255)) : 0;
+}
+
+extern "C" int pdeshep_gather_columns(int64_t n, int32_t is_complex, const void* d_prev, int64_t nprev, int32_t ncols,
+                                      const int64_t* h_src, uint64_t seed, int64_t col0, void* d_dst, void* d_work,
+                                      size_t work_bytes, void* stream) {
+  if (n <= 0) return -1;
+  if (nprev < 0 || (nprev > 0 && !d_prev)) return -4;
+  if (ncols < 0) return -5;
+  if (ncols > 0 && !h_src) return -6;
+  for (int j = 0; j < ncols; ++j)
+    if (h_src[j] >= nprev) return -6;
+  if (col0 < 0) return -8;
+  if (ncols > 0 && !d_dst) return -9;
+  if (ncols == 0) return 0;
+  if (!d_work || work_bytes < pdeshep_gather_columns_workspace_size(ncols)) return -10;
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t* d_src = (int64_t*)d_work;
+  PD_CK(cudaMemcpyAsync(d_src, h_src, sizeof(int64_t) * ncols, cudaMemcpyHostToDevice, st));
+  const int64_t total = n * ncols;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  if (is_complex)
+    gather_columns_kernel<double2><<<blocks, 256, 0, st>>>(n, ncols, d_src, (const double2*)d_prev, col0, seed,
+                                                           (double2*)d_dst);
+  else
+    gather_columns_kernel<double><<<blocks, 256, 0, st>>>(n, ncols, d_src, (const double*)d_prev, col0, seed,
+                                                          (double*)d_dst);
+  PD_CK_LAUNCH();
+  return 0;
 }

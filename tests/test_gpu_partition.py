@@ -65,3 +65,26 @@ def test_outer_bounds_capped_search_reports_not_converged(device):
     ob0, obK, oit_lo, oit_hi, ook = po.outer_bounds(ab, prev, 30, 50, alpha=1e-3, m_hat=6, max_it=3)
     assert (b0, bK, its, ok) == (ob0, obK, (oit_lo, oit_hi), ook)
     assert not ok and its[1] == 3
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_restart_plan_device_gather(device, cplx):
+    """The device side of the restart plan: previous columns copied bit for bit, the random
+    columns equal to the oracle's start-vector stream at their output column."""
+    import torch
+    import paper_2012_00506_gb300 as pk
+    n, nprev = 300, 40
+    g = np.random.default_rng(5)
+    vals = np.sort(g.uniform(0, 1, nprev))
+    prev = synth.random_subspace(n, nprev, 6, cplx)
+    bounds = [0.0, 0.25, 0.5, 0.8, 1.0]
+    m0 = [14, 9, 30, 12]
+    plan = pk.restart_plan(vals, bounds, m0, mode=0)
+    src = np.concatenate(plan)
+    assert np.any(src < 0) and np.any(src >= 0)
+    X = pk.gather_columns(torch.from_numpy(np.ascontiguousarray(prev.T)).to(device), src, seed=77, col0=11)
+    got = X.cpu().numpy().T
+    rnd = oracle.random_start(n, src.size, cplx, seed=77, col0=11)
+    for j, sj in enumerate(src):
+        ref = prev[:, sj] if sj >= 0 else rnd[:, j]
+        assert np.array_equal(got[:, j], ref), j
