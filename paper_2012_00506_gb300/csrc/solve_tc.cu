@@ -1,8 +1,11 @@
 // solve_tc.cu -- complex64 band solves of eq. (10) with the tile products on
 // the tcgen05 tensor cores (3xTF32: FP32-class accuracy).
 //
-// A CTA of 128 threads takes 128 right-hand sides of one system; thread m owns
-// right-hand side m and TMEM lane m.  Every tile product of a sweep step is
+// A CTA takes 128 right-hand sides of one system: four compute warps, thread m
+// owning right-hand side m and TMEM lane m, and a fifth warp that only issues
+// the MMAs (warp-specialised: operands are handed over through full/empty
+// mbarriers, so preparing the next tile overlaps the running products and no
+// CTA-wide barrier is taken inside a sweep).  Every tile product of a step is
 // one MMA group D(128 x 64) (+)= A(128 x 64) B(64 x 64)^T in real arithmetic:
 //   A = [Re x | Im x] of the 128 right-hand sides (the vector of the step),
 //   B = the factor tile T (or its conjugate transpose) embedded as
@@ -11,9 +14,10 @@
 //   D = a block of 32 complex rows in TMEM as [Re | Im] (FP32 accumulator),
 // and A, B split into TF32 high and low parts, D += A_hi B_hi + A_hi B_lo +
 // A_lo B_hi (the low-by-low term is below FP32 rounding).  Operands are written
-// by the threads into shared memory in the K-major 64-byte-swizzle layout and
-// issued by one thread; completion is tracked by mbarriers whose waits are
-// bounded (a give-up sets the error word and the CTA stops).
+// by the compute threads into shared memory in the K-major 64-byte-swizzle
+// layout; the factor tiles reach shared memory by cp.async one step ahead, each
+// warp copying exactly the part it reads.  Every mbarrier wait is bounded (a
+// give-up sets the error word and the CTA stops at its next item).
 //
 // Sweeps (all right-looking, so that every update is a product into TMEM):
 //   trans 0, forward:  P_K on the window (blocks K..K+bt), x_K = Linv_K g_K,
@@ -31,11 +35,11 @@
 namespace pdeshep {
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcCompute = 128;             // compute warps 0..3
+constexpr int kTcThreads = kTcCompute + 32;  // + the MMA warp
 constexpr int kARows = 128, kBRows = 64, kK = 64;
 constexpr int kABytes = kARows * kK * 4;   // one TF32 part of A: 32 KiB
 constexpr int kBBytes = kBRows * kK * 4;   // one TF32 part of B: 16 KiB
-constexpr int kSRow = 65;
 // instruction descriptor: D FP32, A and B TF32, both K-major, N = 64, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBRows >> 3) << 17) |
                             ((uint32_t)(kARows >> 4) << 24);
@@ -89,20 +93,6 @@ __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
-// bounded wait for the phase of the given parity; false if it never completed
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kPollLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (it > 32) __nanosleep(64);
-  }
-  return false;
-}
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -153,22 +143,65 @@ __device__ __forceinline__ void write_a_row(unsigned char* Ahi, unsigned char* A
   }
 }
 
-// Register prefetch of one factor tile as M = T (CT = false) or M = T^H (CT = true): thread t holds
-// M(r, c0..c0+7) with r = t % 32, c0 = 8 (t / 32) (for M = T the 32 lanes read 32 consecutive rows
-// of a column: coalesced).
+// One factor tile's 8 elements per thread: M = T (CT = false) or M = T^H (CT = true), thread t holds
+// M(r, c0..c0+7) with r = t % 32, c0 = 8 (t / 32).
 struct TileRegs {
   float2 v[8];
 };
+
+// Factor tiles are staged into shared memory by cp.async one sweep step ahead.  Staged layout of a
+// column-major 32 x 32 complex64 tile: column c (256 bytes) at 256 c, its 16-byte chunk k (rows 2k,
+// 2k+1) at chunk position k ^ (c & 15), so that reading along a row or along a column both spread
+// over the banks.
+constexpr int kSlotBytes = kTile * kTile * 8;
+__device__ __forceinline__ uint32_t slot_off(int r, int c) {
+  return (uint32_t)(c * 256 + (((r >> 1) ^ (c & 15)) << 4) + ((r & 1) << 3));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// the part of one tile (16-byte aligned in global memory) that compute warp w later reads, into the
+// slot at shared address dst: columns 8w..8w+7 (CT = false) or rows 8w..8w+7 (CT = true); 4 chunks
+// per lane
 template <bool CT>
-__device__ __forceinline__ void tile_fetch(TileRegs& r, const float2* __restrict__ T) {
+__device__ __forceinline__ void stage_tile_warp(uint32_t dst, const float2* __restrict__ T, int w, int lane) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = lane + 32 * j;
+    const int c = CT ? (i >> 2) : 8 * w + (i >> 4);
+    const int k = CT ? 4 * w + (i & 3) : (i & 15);
+    cp_async16(dst + (uint32_t)(c * 256 + ((k ^ (c & 15)) << 4)), T + c * 32 + 2 * k);
+  }
+}
+// `bytes` (a multiple of 16, at most 512) from p to the shared address dst, by one warp
+__device__ __forceinline__ void stage_bytes_warp(uint32_t dst, const void* p, int bytes, int lane) {
+  if (16 * lane < bytes) cp_async16(dst + (uint32_t)(16 * lane), (const char*)p + 16 * lane);
+}
+// wait until at most n of this thread's most recent cp.async groups are still in flight
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+    case 7: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
+    case 8: asm volatile("cp.async.wait_group 8;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+  }
+}
+template <bool CT>
+__device__ __forceinline__ void tile_from_slot(TileRegs& r, const unsigned char* slot) {
   const int i = threadIdx.x & 31, c0 = 8 * (threadIdx.x >> 5);
 #pragma unroll
   for (int jj = 0; jj < 8; ++jj) {
-    if (CT) {
-      const float2 v = T[(c0 + jj) + 32 * i];
+    if (CT) {  // M(i, c) = conj T(c, i)
+      const float2 v = *(const float2*)(slot + slot_off(c0 + jj, i));
       r.v[jj] = make_float2(v.x, -v.y);
     } else {
-      r.v[jj] = T[i + 32 * (c0 + jj)];
+      r.v[jj] = *(const float2*)(slot + slot_off(i, c0 + jj));
     }
   }
 }
@@ -220,10 +253,9 @@ __device__ __forceinline__ void write_b(unsigned char* Bhi, unsigned char* Blo, 
   }
 }
 
-// L2 prefetch of `lines` 128-byte lines from p, spread over the CTA's threads (offset by `slot`)
-__device__ __forceinline__ void l2_prefetch(const void* p, int lines, int slot) {
-  for (int l = (threadIdx.x + slot * 37) % kTcThreads; l < lines; l += kTcThreads)
-    asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)p + 128 * l));
+// L2 prefetch of compute warp w's quarter of one 8 KiB tile
+__device__ __forceinline__ void l2_prefetch_tile(const void* p, int w, int lane) {
+  if (lane < 16) asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)p + 128 * (16 * w + lane)));
 }
 // this thread's right-hand side, rows row0..row0+31 (two lines)
 __device__ __forceinline__ void l2_prefetch_rows(const float2* X, int64_t n, int64_t row0, bool valid) {
@@ -277,49 +309,79 @@ __device__ __forceinline__ void blk_to_tm(const float (&b)[64], uint32_t a) {
   }
   tm_wait_st();
 }
-// global rows row0..row0+31 of this thread's right-hand side <-> [re | im] registers
+// global rows row0..row0+31 of this thread's right-hand side <-> [re | im] registers; 16-byte
+// accesses where the column is 16-byte aligned and the block is whole
 __device__ __forceinline__ void blk_from_global(float (&b)[64], const float2* __restrict__ Y, int64_t n, int64_t row0,
                                                 bool valid) {
+  const float2* p = Y + row0;
+  if (valid && row0 + 32 <= n && ((uintptr_t)p & 15) == 0) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float4 q = *(const float4*)(p + 2 * k);
+      b[2 * k] = q.x;
+      b[32 + 2 * k] = q.y;
+      b[2 * k + 1] = q.z;
+      b[33 + 2 * k] = q.w;
+    }
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < 32; ++r) {
     float2 v = make_float2(0.f, 0.f);
-    if (valid && row0 + r < n) v = Y[row0 + r];
+    if (valid && row0 + r < n) v = p[r];
     b[r] = v.x;
     b[32 + r] = v.y;
   }
 }
+// the row pairs (2k, 2k+1), k0 <= k < k1, of the block
 __device__ __forceinline__ void blk_to_global(const float (&b)[64], float2* __restrict__ X, int64_t n, int64_t row0,
-                                              bool valid) {
+                                              bool valid, int k0, int k1) {
   if (!valid) return;
+  float2* p = X + row0;
+  const bool vec = row0 + 32 <= n && ((uintptr_t)p & 15) == 0;
 #pragma unroll
-  for (int r = 0; r < 32; ++r)
-    if (row0 + r < n) X[row0 + r] = make_float2(b[r], b[32 + r]);
+  for (int k = 0; k < 16; ++k) {
+    if (k < k0 || k >= k1) continue;
+    if (vec) {
+      *(float4*)(p + 2 * k) = make_float4(b[2 * k], b[32 + 2 * k], b[2 * k + 1], b[33 + 2 * k]);
+    } else {
+      if (row0 + 2 * k < n) p[2 * k] = make_float2(b[2 * k], b[32 + 2 * k]);
+      if (row0 + 2 * k + 1 < n) p[2 * k + 1] = make_float2(b[2 * k + 1], b[33 + 2 * k]);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-struct Sync {
-  uint32_t bar_b[2], bar_x, bar_step;
-  int uses_b[2], nx, nstep;
-  int* sh_bad;
-  // a bounded wait without a barrier: a give-up is recorded for the next barrier to see
-  __device__ void wait_nb(uint32_t bar, int k) {
-    if (!mbar_wait(bar, (uint32_t)((k - 1) & 1))) {
-      atomicExch(&g_tc_solve_err, 1);
-      *sh_bad = 1;
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// bounded wait for the k-th completion (k >= 1) of bar; gives up early once another warp has
+// recorded a failure (unless `early` is false).  A give-up sets the error word and the CTA's
+// failure flag.
+__device__ __forceinline__ bool wait_k(uint32_t bar, int k, volatile int* bad, bool early = true) {
+  const uint32_t parity = (uint32_t)((k - 1) & 1);
+  for (int it = 0; it < kPollLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it > 32) {
+      if (early && (it & 255) == 0 && *bad) break;
+      __nanosleep(64);
     }
   }
-  // a CTA-uniform bounded wait for the k-th completion (k >= 1) of bar
-  __device__ bool wait(uint32_t bar, int k) {
-    bool ok = mbar_wait(bar, (uint32_t)((k - 1) & 1));
-    if (!ok) {
-      atomicExch(&g_tc_solve_err, 1);
-      *sh_bad = 1;
-    }
-    return __syncthreads_or(!ok) == 0;
-  }
-};
+  atomicExch(&g_tc_solve_err, 1);
+  *bad = 1;
+  return false;
+}
+
+// mbarriers of the CTA
+enum { kBarFull0 = 0, kBarFull1, kBarEmpty0, kBarEmpty1, kBarAFull, kBarX, kBarStep, kBarDrain, kNumBars };
 
 template <int TRANS>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -329,25 +391,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   unsigned char* Ahi = sm;
   unsigned char* Alo = Ahi + kABytes;
-  unsigned char* Bhi[2] = {Alo + kABytes, Alo + kABytes + 2 * kBBytes};
-  unsigned char* Blo[2] = {Bhi[0] + kBBytes, Bhi[1] + kBBytes};
-  float* orow = (float*)(Bhi[1] + 2 * kBBytes);             // kTcThreads x kSRow
+  unsigned char* Bbuf = Alo + kABytes;                        // B buffer b: high part, then low part
+  auto Bhi = [&](int b) { return Bbuf + (size_t)b * 2 * kBBytes; };
+  unsigned char* slots = Bbuf + 4 * kBBytes;                  // 2 bt + 1 staged factor tiles
   const int Pmax = (g.bt + 1) * kTile;
-  int16_t* perm = (int16_t*)(orow + kTcThreads * kSRow);     // Pmax
-  uint64_t* bars = (uint64_t*)(((uintptr_t)(perm + Pmax) + 7) & ~(uintptr_t)7);
+  int16_t* perm_base = (int16_t*)(slots + (size_t)(2 * g.bt + 1) * kSlotBytes);  // [warp][2][Pmax]
+  uint64_t* bars = (uint64_t*)(((uintptr_t)(perm_base + 8 * Pmax) + 7) & ~(uintptr_t)7);
   __shared__ uint32_t tslot;
-  __shared__ int sh_item, sh_bad;
+  __shared__ int sh_item;
+  __shared__ volatile int sh_bad;
 
-  const int t = threadIdx.x, warp = t >> 5;
-  Sync sy;
-  sy.bar_b[0] = smem_u32(bars);
-  sy.bar_b[1] = smem_u32(bars + 1);
-  sy.bar_x = smem_u32(bars + 2);
-  sy.bar_step = smem_u32(bars + 3);
-  sy.uses_b[0] = sy.uses_b[1] = sy.nx = sy.nstep = 0;
-  sy.sh_bad = &sh_bad;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  auto bar = [&](int i) { return smem_u32(bars + i); };
+  // a warp-uniform bounded wait (a give-up by any lane fails the whole warp; the warp reconverges)
+  auto wwait = [&](uint32_t b, int k) -> bool { return __all_sync(~0u, wait_k(b, k, &sh_bad)) != 0; };
   if (t == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(bars + i), 1);
+    for (int i = 0; i < kNumBars; ++i)
+      mbar_init(bar(i), (i == kBarFull0 || i == kBarFull1 || i == kBarAFull) ? 4u : 1u);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh_bad = 0;
   }
@@ -360,249 +420,370 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tbase = tslot;                          // lane 0, column 0 (MMA destinations)
-  const uint32_t tb = tslot + ((uint32_t)(32 * warp) << 16);  // this thread's lane quadrant
-  const uint64_t da_hi = sw64_desc(smem_u32(Ahi)), da_lo = sw64_desc(smem_u32(Alo));
-  const uint64_t db_hi[2] = {sw64_desc(smem_u32(Bhi[0])), sw64_desc(smem_u32(Bhi[1]))};
-  const uint64_t db_lo[2] = {sw64_desc(smem_u32(Blo[0])), sw64_desc(smem_u32(Blo[1]))};
-  float* myo = orow + t * kSRow;
+  const uint32_t tbase = tslot;                               // lane 0, column 0 (MMA destinations)
+  const uint32_t tb = tslot + ((uint32_t)(32 * (warp & 3)) << 16);  // a compute warp's lane quadrant
   const int bt = g.bt, Nb = g.Nb;
-  const int64_t n = g.n;
+  const int64_t n = g.n, te = g.tile_elems;
   const int ringw = bt + 1, rings = 2 * bt;
-  const uint32_t scratch = (uint32_t)(64 * ringw);       // forward: x_K's TMEM block after the window
-  int cur = 0;                                           // B buffer for the next tile
-  BOffsets boff;
-  boff.init();
-  bool alive = true;
-
-  // B buffer `cur` <- tile (after the MMA that last read it), then the tile's MMA group into TMEM
-  // column d; returns false if a wait gave up
-  auto issue_tile = [&](const TileRegs& tr, float s, uint32_t d, bool accumulate, bool commit_x,
-                        bool commit_step) -> bool {
-    const int b = cur;
-    // the MMA that last read this buffer (two groups ago) is normally long done; a wait that
-    // gives up is seen by every thread after the barrier below
-    if (sy.uses_b[b] > 0) sy.wait_nb(sy.bar_b[b], sy.uses_b[b]);
-    write_b(Bhi[b], Blo[b], tr, s, boff);
-    proxy_fence();
-    tc_fence_before();
-    __syncthreads();
-    if (sh_bad) return false;
-    if (t == 0) {
-      tc_fence_after();
-      mma_group(tbase + d, da_hi, da_lo, db_hi[b], db_lo[b], accumulate);
-      tc_commit(sy.bar_b[b]);
-      if (commit_x) tc_commit(sy.bar_x);
-      if (commit_step) tc_commit(sy.bar_step);
-    }
-    sy.uses_b[b] += 1;
-    if (commit_x) sy.nx += 1;
-    if (commit_step) sy.nstep += 1;
-    cur ^= 1;
-    return true;
-  };
-  // A <- this thread's 64 values (after the MMAs that read the previous A)
-  auto write_a = [&](const float (&a)[64]) {
-    write_a_row(Ahi, Alo, t, a);
-    proxy_fence();
-  };
+  const uint32_t scratch = (uint32_t)(64 * ringw);            // forward: x_K's TMEM block after the window
+  // completion counts, kept identically by every thread that waits on the barrier
+  int uses[2] = {0, 0};  // groups issued on B buffer b (= completions of its empty barrier)
+  int cur = 0;           // B buffer of the next tile
+  int nx = 0, nstep = 0, na = 0;
 
   for (;;) {
     if (t == 0) sh_item = atomicAdd(counter, 1);
     __syncthreads();
     const int item = sh_item;
-    if (item >= nitems || !alive) break;
+    if (item >= nitems || sh_bad) break;
     const int2 w = items[item];
     const SysDesc d = sys[w.x];
     const FactorPtr<float2> f = factor_ptr<float2>(g, (char*)arena + d.factor_off);
-    const int col = w.y + t;
-    const bool valid = col < d.ncols;
-    const float2* Y = rhs + d.rhs_off + (int64_t)(valid ? col : 0) * n;
-    float2* X = out + (TRANS == 0 ? d.out_off : d.out2_off) + (int64_t)(valid ? col : 0) * n;
-    auto tile_of = [&](int I, int J) { return f.tiles + g.tile_index(I, J) * g.tile_elems; };
-    float v[64], x[64];
-    TileRegs tr;
 
-    if (TRANS == 0) {
-      // ======================= forward: P, L =======================
-      for (int q = 0; q <= min(bt, Nb - 1); ++q) {
-        blk_from_global(v, Y, n, (int64_t)q * kTile, valid);
-        blk_to_tm(v, tb + (uint32_t)(64 * (q % ringw)));
-      }
-      for (int K = 0; K < Nb && alive; ++K) {
-        const int nbb = min(bt, Nb - 1 - K);
-        const int P = (nbb + 1) * kTile;
-        // the window's updates of the previous step are complete
-        if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
+    if (warp == 4) {
+      // ================= the MMA warp: the step sequence of the sweeps, products only =================
+      const uint64_t da_hi = sw64_desc(smem_u32(Ahi)), da_lo = sw64_desc(smem_u32(Alo));
+      // the next tile's group into TMEM column dcol once its operands are in place
+      auto group = [&](uint32_t dcol, bool accumulate, bool wait_a, bool commit_x, bool commit_step) -> bool {
+        if (wait_a && !wwait(bar(kBarAFull), ++na)) return false;
+        const int b = cur;
+        if (!wwait(bar(kBarFull0 + b), uses[b] + 1)) return false;
         tc_fence_after();
-        for (int r = t; r < P; r += kTcThreads) perm[r] = f.perm[(int64_t)K * Pmax + r];
-        if (K + 1 < Nb) {  // the next step's tiles, permutation and entering block toward L2
-          const int nb1 = min(bt, Nb - 2 - K);
-          l2_prefetch(f.inv + (int64_t)(2 * (K + 1)) * g.tile_elems, 64, 0);
-          for (int q = 1; q <= nb1; ++q) l2_prefetch(tile_of(K + 1 + q, K + 1), 64, q);
-          l2_prefetch(f.perm + (int64_t)(K + 1) * Pmax, (Pmax * 2 + 127) / 128, 7);
-          l2_prefetch_rows(Y, n, (int64_t)(K + bt + 2) * kTile, valid);
+        if (lane == 0) {
+          mma_group(tbase + dcol, da_hi, da_lo, sw64_desc(smem_u32(Bhi(b))), sw64_desc(smem_u32(Bhi(b) + kBBytes)),
+                    accumulate);
+          tc_commit(bar(kBarEmpty0 + b));
+          if (commit_x) tc_commit(bar(kBarX));
+          if (commit_step) tc_commit(bar(kBarStep));
         }
-        tile_fetch<false>(tr, f.inv + (int64_t)(2 * K) * g.tile_elems);
-        const uint32_t top = (uint32_t)(64 * (K % ringw));
-        blk_from_tm(v, tb + top);
-#pragma unroll
-        for (int r = 0; r < 64; ++r) myo[r] = v[r];
-        __syncthreads();  // perm is complete
-        // new row r = old row perm[r]: the top rows gather, the old top rows that move down
-        uint32_t ur[32], ui[32];
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-          const int s = perm[r];
-          ur[r] = ui[r] = 0u;
-          if (s >= 32) {
-            const uint32_t a = tb + (uint32_t)(64 * ((K + s / 32) % ringw) + s % 32);
-            ur[r] = tm_ld1(a);
-            ui[r] = tm_ld1(a + 32);
+        __syncwarp();
+        uses[b] += 1;
+        cur ^= 1;
+        return true;
+      };
+      bool ok = true;
+      if (TRANS == 0) {
+        for (int K = 0; K < Nb && ok; ++K) {  // forward: x_K into the scratch block, then block K+q
+          const int nbb = min(bt, Nb - 1 - K), kmod = K % ringw;
+          ok = group(scratch, false, true, true, nbb == 0);
+          for (int q = 1; q <= nbb && ok; ++q) {
+            const int sl = kmod + q;
+            ok = group((uint32_t)(64 * (sl >= ringw ? sl - ringw : sl)), true, q == 1, false, q == nbb);
           }
         }
-        tm_wait_ld();
-        reg_fence16(*(uint32_t(*)[16])&ur[0]);
-        reg_fence16(*(uint32_t(*)[16])&ur[16]);
-        reg_fence16(*(uint32_t(*)[16])&ui[0]);
-        reg_fence16(*(uint32_t(*)[16])&ui[16]);
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-          const int s = perm[r];
-          v[r] = s < 32 ? myo[s] : __uint_as_float(ur[r]);
-          v[32 + r] = s < 32 ? myo[32 + s] : __uint_as_float(ui[r]);
+        for (int K = Nb - 1; K >= 0 && ok; --K) {  // backward: x_K in place, then block K-q
+          const int nq = min(rings, K);
+          ok = group((uint32_t)(64 * (K % rings)), false, true, true, nq == 0);
+          for (int q = 1; q <= nq && ok; ++q)
+            ok = group((uint32_t)(64 * ((K - q) % rings)), true, q == 1, false, q == nq);
         }
-        for (int rho = 32; rho < P; ++rho) {
-          const int s = perm[rho];
-          if (s < 32) {
-            const uint32_t a = tb + (uint32_t)(64 * ((K + rho / 32) % ringw) + rho % 32);
-            tm_st1(a, __float_as_uint(myo[s]));
-            tm_st1(a + 32, __float_as_uint(myo[32 + s]));
-          }
+      } else {
+        for (int K = 0; K < Nb && ok; ++K) {  // adjoint forward: w_K in place, then block K+q
+          const int nq = min(rings, Nb - 1 - K);
+          ok = group((uint32_t)(64 * (K % rings)), false, true, true, nq == 0);
+          for (int q = 1; q <= nq && ok; ++q)
+            ok = group((uint32_t)(64 * ((K + q) % rings)), true, q == 1, false, q == nq);
         }
-        tm_wait_st();
-        // x_K = Linv_K g (A's previous readers, the last step's updates, finished with bar_step)
-        write_a(v);
-        if (!issue_tile(tr, 1.f, scratch, false, true, nbb == 0)) { alive = false; break; }
-        if (nbb >= 1) tile_fetch<false>(tr, tile_of(K + 1, K));
-        if (!sy.wait(sy.bar_x, sy.nx)) { alive = false; break; }
-        tc_fence_after();
-        blk_from_tm(x, tb + scratch);
-        write_a(x);
-        for (int q = 1; q <= nbb; ++q) {
-          const TileRegs cur_t = tr;
-          if (q < nbb) tile_fetch<false>(tr, tile_of(K + q + 1, K));
-          if (!issue_tile(cur_t, -1.f, (uint32_t)(64 * ((K + q) % ringw)), true, false, q == nbb)) {
-            alive = false;
-            break;
-          }
-          if (q == 1) blk_to_global(x, X, n, (int64_t)K * kTile, valid);  // while the first update runs
-        }
-        if (!alive) break;
-        if (nbb == 0) blk_to_global(x, X, n, (int64_t)K * kTile, valid);
-        if (K + bt + 1 < Nb) {  // block K+bt+1 of Y enters the slot block K leaves (no update writes it)
-          blk_from_global(v, Y, n, (int64_t)(K + bt + 1) * kTile, valid);
-          blk_to_tm(v, tb + top);
-        }
-      }
-      if (!alive) break;
-      // ======================= backward: U =======================
-      if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
-      tc_fence_after();
-      for (int J = Nb - 1; J >= max(0, Nb - rings); --J) {  // pending blocks start as the forward result
-        blk_from_global(v, X, n, (int64_t)J * kTile, valid);
-        blk_to_tm(v, tb + (uint32_t)(64 * (J % rings)));
-      }
-      for (int K = Nb - 1; K >= 0 && alive; --K) {
-        const int nq = min(rings, K);
-        const uint32_t sk = (uint32_t)(64 * (K % rings));
-        if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
-        tc_fence_after();
-        tile_fetch<false>(tr, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
-        if (K >= 1) {  // the next step's tiles and entering block toward L2
-          const int nq1 = min(rings, K - 1);
-          l2_prefetch(f.inv + (int64_t)(2 * (K - 1) + 1) * g.tile_elems, 64, 0);
-          for (int q = 1; q <= nq1; ++q) l2_prefetch(tile_of(K - 1 - q, K - 1), 64, q);
-          if (K - 1 - rings >= 0) l2_prefetch_rows(X, n, (int64_t)(K - 1 - rings) * kTile, valid);
-        }
-        blk_from_tm(v, tb + sk);  // acc_K is complete
-        write_a(v);
-        if (!issue_tile(tr, 1.f, sk, false, true, nq == 0)) { alive = false; break; }
-        if (nq >= 1) tile_fetch<false>(tr, tile_of(K - 1, K));
-        if (!sy.wait(sy.bar_x, sy.nx)) { alive = false; break; }
-        tc_fence_after();
-        blk_from_tm(x, tb + sk);
-        write_a(x);
-        for (int q = 1; q <= nq; ++q) {
-          const TileRegs cur_t = tr;
-          if (q < nq) tile_fetch<false>(tr, tile_of(K - q - 1, K));
-          if (!issue_tile(cur_t, -1.f, (uint32_t)(64 * ((K - q) % rings)), true, false, q == nq)) {
-            alive = false;
-            break;
-          }
-          if (q == 1) {  // while the first update runs: x_K out, and block K-2bt enters the slot K leaves
-            blk_to_global(x, X, n, (int64_t)K * kTile, valid);
-            if (K - rings >= 0) {
-              blk_from_global(v, X, n, (int64_t)(K - rings) * kTile, valid);
-              blk_to_tm(v, tb + sk);
-            }
-          }
-        }
-        if (nq == 0) blk_to_global(x, X, n, (int64_t)K * kTile, valid);
       }
     } else {
-      // ======================= adjoint forward: U^H =======================
-      for (int J = 0; J < min(rings, Nb); ++J) {  // pending blocks start as y
-        blk_from_global(v, Y, n, (int64_t)J * kTile, valid);
-        blk_to_tm(v, tb + (uint32_t)(64 * (J % rings)));
-      }
-      for (int K = 0; K < Nb && alive; ++K) {
-        const int nq = min(rings, Nb - 1 - K);
-        const uint32_t sk = (uint32_t)(64 * (K % rings));
-        if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
-        tc_fence_after();
-        tile_fetch<true>(tr, f.inv + (int64_t)(2 * K + 1) * g.tile_elems);
-        if (K + 1 < Nb) {  // the next step's tiles and entering block toward L2
-          const int nq1 = min(rings, Nb - 2 - K);
-          l2_prefetch(f.inv + (int64_t)(2 * (K + 1) + 1) * g.tile_elems, 64, 0);
-          for (int q = 1; q <= nq1; ++q) l2_prefetch(tile_of(K + 1, K + 1 + q), 64, q);
-          if (K + 1 + rings < Nb) l2_prefetch_rows(Y, n, (int64_t)(K + 1 + rings) * kTile, valid);
+      // ================= compute warps =================
+      const int col = w.y + t;
+      const bool valid = col < d.ncols;
+      const float2* Y = rhs + d.rhs_off + (int64_t)(valid ? col : 0) * n;
+      float2* X = out + (TRANS == 0 ? d.out_off : d.out2_off) + (int64_t)(valid ? col : 0) * n;
+      auto tile_of = [&](int I, int J) { return f.tiles + g.tile_index(I, J) * te; };
+      auto slot = [&](int q) { return slots + (size_t)q * kSlotBytes; };
+      auto permbuf = [&](int K) { return perm_base + (size_t)(2 * warp + (K & 1)) * Pmax; };
+      BOffsets boff;
+      boff.init();
+      float v[64], x[64];
+      bool ok = true;
+      // this warp's part of tile T into slot q, as one cp.async group (with P_K if given)
+      auto stage = [&](int q, const float2* T, int Kperm) {
+        stage_tile_warp<TRANS == 1>(smem_u32(slot(q)), T, warp, lane);
+        if (Kperm >= 0) stage_bytes_warp(smem_u32(permbuf(Kperm)), f.perm + (int64_t)Kperm * Pmax, 2 * Pmax, lane);
+        cp_async_commit();
+      };
+      // B buffer `cur` <- staged tile q (scaled by s) once the tile has landed and the buffer's last
+      // group is done; then the slot's refill for the next step goes out.  `later` = groups of the
+      // previous step staged after tile q, `cnt` = groups this step has staged so far.
+      auto put_tile = [&](int q, int later, int& cnt, float s, const float2* refill, int Kperm) -> bool {
+        cp_async_wait_pending(later - q + cnt);
+        __syncwarp();
+        const int b = cur;
+        if (uses[b] > 0 && !wwait(bar(kBarEmpty0 + b), uses[b])) return false;
+        TileRegs tr;
+        tile_from_slot<TRANS == 1>(tr, slot(q));
+        write_b(Bhi(b), Bhi(b) + kBBytes, tr, s, boff);
+        proxy_fence();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(kBarFull0 + b));
+        uses[b] += 1;
+        cur ^= 1;
+        if (refill) {
+          stage(q, refill, Kperm);
+          ++cnt;
         }
-        blk_from_tm(v, tb + sk);
-        write_a(v);
-        if (!issue_tile(tr, 1.f, sk, false, true, nq == 0)) { alive = false; break; }
-        if (nq >= 1) tile_fetch<true>(tr, tile_of(K, K + 1));
-        if (!sy.wait(sy.bar_x, sy.nx)) { alive = false; break; }
+        return true;
+      };
+      // A <- this thread's 64 values, then handed to the MMA warp (with every TMEM access before it)
+      auto put_a = [&](const float (&a)[64]) {
+        write_a_row(Ahi, Alo, t, a);
+        proxy_fence();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(kBarAFull));
+      };
+      auto wait_step = [&]() -> bool {
+        if (nstep > 0 && !wwait(bar(kBarStep), nstep)) return false;
         tc_fence_after();
-        blk_from_tm(x, tb + sk);
-        write_a(x);
-        for (int q = 1; q <= nq; ++q) {
-          const TileRegs cur_t = tr;
-          if (q < nq) tile_fetch<true>(tr, tile_of(K, K + q + 1));
-          if (!issue_tile(cur_t, -1.f, (uint32_t)(64 * ((K + q) % rings)), true, false, q == nq)) {
-            alive = false;
+        return true;
+      };
+      auto wait_x = [&]() -> bool {
+        if (!wwait(bar(kBarX), ++nx)) return false;
+        tc_fence_after();
+        return true;
+      };
+
+      if (TRANS == 0) {
+        // ======================= forward: P, L =======================
+        const int n0 = min(bt, Nb - 1);
+        stage(0, f.inv, 0);  // step 0: Linv_0 with P_0, then L(q, 0), one group each
+        for (int q = 1; q <= n0; ++q) stage(q, tile_of(q, 0), -1);
+        for (int q = 0; q <= n0; ++q) {
+          blk_from_global(v, Y, n, (int64_t)q * kTile, valid);
+          blk_to_tm(v, tb + (uint32_t)(64 * (q % ringw)));
+        }
+        for (int K = 0; K < Nb && ok; ++K) {
+          const int nbb = min(bt, Nb - 1 - K);
+          const int nb1 = K + 1 < Nb ? min(bt, Nb - 2 - K) : -1;  // the next step's update count
+          const int kmod = K % ringw;
+          auto bcol = [&](int j) -> uint32_t {  // TMEM column of window block j (0 <= j <= bt)
+            const int sl = kmod + j;
+            return (uint32_t)(64 * (sl >= ringw ? sl - ringw : sl));
+          };
+          const uint32_t top = (uint32_t)(64 * kmod);
+          int cnt = 0;
+          // Linv_K into B while the previous step's last products run (with P_K; refilled with
+          // Linv_{K+1} and P_{K+1})
+          if (!put_tile(0, nbb, cnt, 1.f, nb1 >= 0 ? f.inv + (int64_t)(2 * (K + 1)) * te : nullptr, K + 1)) {
+            ok = false;
             break;
           }
-          if (q == 1) {  // while the first update runs: w_K out, and block K+2bt enters the slot K leaves
-            blk_to_global(x, X, n, (int64_t)K * kTile, valid);
-            if (K + rings < Nb) {
-              blk_from_global(v, Y, n, (int64_t)(K + rings) * kTile, valid);
-              blk_to_tm(v, tb + sk);
+          if (K + 2 < Nb) {  // step K+2's tiles and permutation, step K+1's entering block toward L2
+            l2_prefetch_tile(f.inv + (int64_t)(2 * (K + 2)) * te, warp, lane);
+            for (int q = 1; q <= min(bt, Nb - 3 - K); ++q) l2_prefetch_tile(tile_of(K + 2 + q, K + 2), warp, lane);
+            if (warp == 0 && 128 * lane < 2 * Pmax)
+              asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)(f.perm + (int64_t)(K + 2) * Pmax) + 128 * lane));
+            l2_prefetch_rows(Y, n, (int64_t)(K + bt + 2) * kTile, valid);
+          }
+          if (!wait_step()) { ok = false; break; }
+          // P_K on the window, in TMEM: new row r = old row perm[r].  The top rows gather (lane r
+          // holds perm[r]); a row below the top changes only by receiving an old top row.
+          const int16_t* pm = permbuf(K);
+          const int pl = pm[lane];
+          const unsigned moved = __ballot_sync(~0u, pl != lane);
+          blk_from_tm(v, tb + top);
+          if (moved) {
+            uint32_t ur[32], ui[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+              const int sr = __shfl_sync(~0u, pl, r);
+              ur[r] = ui[r] = 0u;
+              if ((moved >> r) & 1u) {
+                const uint32_t a = tb + bcol(sr >> 5) + (uint32_t)(sr & 31);
+                ur[r] = tm_ld1(a);
+                ui[r] = tm_ld1(a + 32);
+              }
+            }
+            tm_wait_ld();
+            reg_fence16(*(uint32_t(*)[16])&ur[0]);
+            reg_fence16(*(uint32_t(*)[16])&ur[16]);
+            reg_fence16(*(uint32_t(*)[16])&ui[0]);
+            reg_fence16(*(uint32_t(*)[16])&ui[16]);
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+              if ((moved >> r) & 1u) {
+                v[r] = __uint_as_float(ur[r]);
+                v[32 + r] = __uint_as_float(ui[r]);
+              }
+          }
+          for (int j = 1; j <= nbb; ++j) {  // rows 32 j + l that receive old top row perm[32 j + l]
+            const int pj = pm[32 * j + lane];
+            unsigned m = __ballot_sync(~0u, pj < 32);
+            const uint32_t dcol = tb + bcol(j);
+            while (m) {  // up to 8 rows per batch (m is warp-uniform)
+              uint32_t va[16];
+              int dl[8], nb = 0;
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                va[u] = va[8 + u] = 0u;
+                dl[u] = 0;
+                if (m) {
+                  const int l = __ffs(m) - 1;
+                  m &= m - 1;
+                  const int sr = __shfl_sync(~0u, pj, l);
+                  dl[u] = l;
+                  va[u] = tm_ld1(tb + top + (uint32_t)sr);
+                  va[8 + u] = tm_ld1(tb + top + 32u + (uint32_t)sr);
+                  nb = u + 1;
+                }
+              }
+              tm_wait_ld();
+              reg_fence16(va);
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                if (u < nb) {
+                  tm_st1(dcol + (uint32_t)dl[u], va[u]);
+                  tm_st1(dcol + 32u + (uint32_t)dl[u], va[8 + u]);
+                }
             }
           }
+          tm_wait_st();
+          put_a(v);  // g = P_K rows of the top block; x_K = Linv_K g goes to the scratch block
+          if (nbb >= 1 && !put_tile(1, nbb, cnt, -1.f, 1 <= nb1 ? tile_of(K + 2, K + 1) : nullptr, -1)) {
+            ok = false;
+            break;
+          }
+          // block K+bt+1 of Y enters the slot block K leaves (no product of this step writes it); its
+          // loads are in flight during the products
+          const bool enter = K + bt + 1 < Nb;
+          if (enter) blk_from_global(v, Y, n, (int64_t)(K + bt + 1) * kTile, valid);
+          if (!wait_x()) { ok = false; break; }
+          blk_from_tm(x, tb + scratch);
+          if (nbb >= 1) put_a(x);
+          const int parts = nbb - 1;
+          for (int q = 2; q <= nbb; ++q) {
+            if (!put_tile(q, nbb, cnt, -1.f, q <= nb1 ? tile_of(K + 1 + q, K + 1) : nullptr, -1)) {
+              ok = false;
+              break;
+            }
+            blk_to_global(x, X, n, (int64_t)K * kTile, valid, 16 * (q - 2) / parts, 16 * (q - 1) / parts);
+          }
+          if (!ok) break;
+          if (parts <= 0) blk_to_global(x, X, n, (int64_t)K * kTile, valid, 0, 16);
+          if (enter) blk_to_tm(v, tb + top);
+          ++nstep;
         }
-        if (nq == 0) blk_to_global(x, X, n, (int64_t)K * kTile, valid);
+        if (ok) {
+          // ======================= backward: U =======================
+          const int n0b = min(rings, Nb - 1);
+          if (!wait_step()) ok = false;
+          if (ok) {
+            stage(0, f.inv + (int64_t)(2 * (Nb - 1) + 1) * te, -1);  // step Nb-1: Uinv, U(Nb-1-q, Nb-1)
+            for (int q = 1; q <= n0b; ++q) stage(q, tile_of(Nb - 1 - q, Nb - 1), -1);
+            for (int J = Nb - 1; J >= max(0, Nb - rings); --J) {  // pending blocks start as the forward result
+              blk_from_global(v, X, n, (int64_t)J * kTile, valid);
+              blk_to_tm(v, tb + (uint32_t)(64 * (J % rings)));
+            }
+          }
+          for (int K = Nb - 1; K >= 0 && ok; --K) {
+            const int nq = min(rings, K);
+            const int nq1 = K >= 1 ? min(rings, K - 1) : -1;
+            const uint32_t sk = (uint32_t)(64 * (K % rings));
+            int cnt = 0;
+            if (!put_tile(0, nq, cnt, 1.f, nq1 >= 0 ? f.inv + (int64_t)(2 * (K - 1) + 1) * te : nullptr, -1)) {
+              ok = false;
+              break;
+            }
+            if (K >= 2) {  // step K-2's tiles, step K-1's entering block toward L2
+              l2_prefetch_tile(f.inv + (int64_t)(2 * (K - 2) + 1) * te, warp, lane);
+              for (int q = 1; q <= min(rings, K - 2); ++q) l2_prefetch_tile(tile_of(K - 2 - q, K - 2), warp, lane);
+              if (K - 1 - rings >= 0) l2_prefetch_rows(X, n, (int64_t)(K - 1 - rings) * kTile, valid);
+            }
+            if (!wait_step()) { ok = false; break; }
+            blk_from_tm(v, tb + sk);  // acc_K is complete
+            put_a(v);
+            if (nq >= 1 && !put_tile(1, nq, cnt, -1.f, 1 <= nq1 ? tile_of(K - 2, K - 1) : nullptr, -1)) {
+              ok = false;
+              break;
+            }
+            // block K-2bt enters the slot K leaves; the last update (q = 2bt) accumulates into it
+            const bool enter = K - rings >= 0;
+            if (enter) blk_from_global(v, X, n, (int64_t)(K - rings) * kTile, valid);
+            if (!wait_x()) { ok = false; break; }
+            blk_from_tm(x, tb + sk);
+            if (nq >= 1) put_a(x);
+            const int parts = nq - 1;
+            for (int q = 2; q <= nq; ++q) {
+              if (enter && q == nq) blk_to_tm(v, tb + sk);
+              if (!put_tile(q, nq, cnt, -1.f, q <= nq1 ? tile_of(K - 1 - q, K - 1) : nullptr, -1)) {
+                ok = false;
+                break;
+              }
+              blk_to_global(x, X, n, (int64_t)K * kTile, valid, 16 * (q - 2) / parts, 16 * (q - 1) / parts);
+            }
+            if (!ok) break;
+            if (parts <= 0) blk_to_global(x, X, n, (int64_t)K * kTile, valid, 0, 16);
+            ++nstep;
+          }
+        }
+      } else {
+        // ======================= adjoint forward: U^H =======================
+        const int n0 = min(rings, Nb - 1);
+        stage(0, f.inv + te, -1);  // step 0: Uinv_0^H, then U(0, q)^H
+        for (int q = 1; q <= n0; ++q) stage(q, tile_of(0, q), -1);
+        for (int J = 0; J < min(rings, Nb); ++J) {  // pending blocks start as y
+          blk_from_global(v, Y, n, (int64_t)J * kTile, valid);
+          blk_to_tm(v, tb + (uint32_t)(64 * (J % rings)));
+        }
+        for (int K = 0; K < Nb && ok; ++K) {
+          const int nq = min(rings, Nb - 1 - K);
+          const int nq1 = K + 1 < Nb ? min(rings, Nb - 2 - K) : -1;
+          const uint32_t sk = (uint32_t)(64 * (K % rings));
+          int cnt = 0;
+          if (!put_tile(0, nq, cnt, 1.f, nq1 >= 0 ? f.inv + (int64_t)(2 * (K + 1) + 1) * te : nullptr, -1)) {
+            ok = false;
+            break;
+          }
+          if (K + 2 < Nb) {  // step K+2's tiles, step K+1's entering block toward L2
+            l2_prefetch_tile(f.inv + (int64_t)(2 * (K + 2) + 1) * te, warp, lane);
+            for (int q = 1; q <= min(rings, Nb - 3 - K); ++q) l2_prefetch_tile(tile_of(K + 2, K + 2 + q), warp, lane);
+            if (K + 1 + rings < Nb) l2_prefetch_rows(Y, n, (int64_t)(K + 1 + rings) * kTile, valid);
+          }
+          if (!wait_step()) { ok = false; break; }
+          blk_from_tm(v, tb + sk);
+          put_a(v);
+          if (nq >= 1 && !put_tile(1, nq, cnt, -1.f, 1 <= nq1 ? tile_of(K + 1, K + 2) : nullptr, -1)) {
+            ok = false;
+            break;
+          }
+          // block K+2bt enters the slot K leaves; the last update (q = 2bt) accumulates into it
+          const bool enter = K + rings < Nb;
+          if (enter) blk_from_global(v, Y, n, (int64_t)(K + rings) * kTile, valid);
+          if (!wait_x()) { ok = false; break; }
+          blk_from_tm(x, tb + sk);
+          if (nq >= 1) put_a(x);
+          const int parts = nq - 1;
+          for (int q = 2; q <= nq; ++q) {
+            if (enter && q == nq) blk_to_tm(v, tb + sk);
+            if (!put_tile(q, nq, cnt, -1.f, q <= nq1 ? tile_of(K + 1, K + 1 + q) : nullptr, -1)) {
+              ok = false;
+              break;
+            }
+            blk_to_global(x, X, n, (int64_t)K * kTile, valid, 16 * (q - 2) / parts, 16 * (q - 1) / parts);
+          }
+          if (!ok) break;
+          if (parts <= 0) blk_to_global(x, X, n, (int64_t)K * kTile, valid, 0, 16);
+          ++nstep;
+        }
       }
+      // the item's last products are complete before the next item reuses TMEM
+      if (ok && !wait_step()) ok = false;
+      cp_async_wait_pending(0);
     }
-    if (!alive) break;
-    // the item's last products are complete before the next item reuses TMEM
-    if (sy.nstep > 0 && !sy.wait(sy.bar_step, sy.nstep)) { alive = false; break; }
-    tc_fence_after();
+    // item end: every warp, successful or not, meets here (a failure is in sh_bad)
     __syncthreads();
   }
-  // drain: wait (bounded) for every committed group before TMEM is released
-  for (int b = 0; b < 2; ++b)
-    if (sy.uses_b[b] > 0) mbar_wait(sy.bar_b[b], (uint32_t)((sy.uses_b[b] - 1) & 1));
+  // drain: every product issued is complete (bounded wait) before TMEM is released
+  if (warp == 4) {
+    if (lane == 0) tc_commit(bar(kBarDrain));
+    __syncwarp();
+    wait_k(bar(kBarDrain), 1, &sh_bad, false);
+    __syncwarp();
+  }
+  cp_async_wait_pending(0);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tslot), "r"(512u));
@@ -610,12 +791,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 }  // namespace
 
-bool solve_tc_supported(const FactorGeom& g) { return g.bt >= 1 && 64 * 2 * g.bt <= 512 && 64 * (g.bt + 2) <= 512; }
-
 size_t solve_tc_smem_bytes(const FactorGeom& g) {
   const int Pmax = (g.bt + 1) * kTile;
-  return 1024 + 2 * (size_t)kABytes + 4 * (size_t)kBBytes + (size_t)kTcThreads * kSRow * sizeof(float) +
-         (size_t)Pmax * sizeof(int16_t) + 64;
+  return 1024 + 2 * (size_t)kABytes + 4 * (size_t)kBBytes + (size_t)(2 * g.bt + 1) * kSlotBytes +
+         8 * (size_t)Pmax * sizeof(int16_t) + 8 * kNumBars + 8;
+}
+
+bool solve_tc_supported(const FactorGeom& g) {
+  return g.bt >= 1 && 64 * 2 * g.bt <= 512 && 64 * (g.bt + 2) <= 512 && solve_tc_smem_bytes(g) <= 227 * 1024;
 }
 
 int solve_tc_error(int* h_err, int clear, cudaStream_t st) {
@@ -634,6 +817,10 @@ int launch_solve_tc(const FactorGeom& g, int trans, int nitems, const SysDesc* d
   if (!nitems) return 0;
   if (!solve_tc_supported(g)) {
     set_last_error_msg("band too wide for the tensor-core solve window");
+    return PDESHEP_CUDA_ERROR;
+  }
+  if (((uintptr_t)factor_arena & 15) != 0) {  // the staged tile copies are 16-byte cp.async
+    set_last_error_msg("factor workspace not 16-byte aligned");
     return PDESHEP_CUDA_ERROR;
   }
   const size_t smem = solve_tc_smem_bytes(g);
