@@ -1,5 +1,5 @@
 // solve_tc.cu -- complex64 band solves of eq. (10) with the tile products on
-// the tcgen05 tensor cores (3xTF32: FP32-class accuracy).
+// the tcgen05 tensor cores (bf16x6 products: FP32-level accuracy).
 //
 // A CTA takes 128 right-hand sides of one system: four compute warps, thread m
 // owning right-hand side m and TMEM lane m, and a fifth warp that only issues
@@ -12,8 +12,10 @@
 //       [[s Tr, -s Ti], [s Ti, s Tr]] (rows: real parts then imaginary parts
 //       of the 32 output rows; columns: Re x then Im x), s = +1 or -1,
 //   D = a block of 32 complex rows in TMEM as [Re | Im] (FP32 accumulator),
-// and A, B split into TF32 high and low parts, D += A_hi B_hi + A_hi B_lo +
-// A_lo B_hi (the low-by-low term is below FP32 rounding).  Operands are written
+// and A, B each split into three bf16 parts (a = a0 + a1 + a2, each part the
+// round-to-nearest bf16 of the remainder: 24 significant bits, an FP32 value
+// up to rounding at its last bit), D += a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 +
+// a2 b0 (the dropped terms are below 2^-24 of the product).  Operands are written
 // by the compute threads into shared memory in the K-major 64-byte-swizzle
 // layout; the factor tiles reach shared memory by cp.async one step ahead, each
 // warp copying exactly the part it reads.  Every mbarrier wait is bounded (a
@@ -38,10 +40,10 @@ namespace {
 constexpr int kTcCompute = 128;             // compute warps 0..3
 constexpr int kTcThreads = kTcCompute + 32;  // + the MMA warp
 constexpr int kARows = 128, kBRows = 64, kK = 64;
-constexpr int kABytes = kARows * kK * 4;   // one TF32 part of A: 32 KiB
-constexpr int kBBytes = kBRows * kK * 4;   // one TF32 part of B: 16 KiB
-// instruction descriptor: D FP32, A and B TF32, both K-major, N = 64, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBRows >> 3) << 17) |
+constexpr int kABytes = kARows * kK * 2;   // one bf16 part of A: 16 KiB
+constexpr int kBBytes = kBRows * kK * 2;   // one bf16 part of B: 8 KiB
+// instruction descriptor (kind::f16): D FP32, A and B BF16, both K-major, N = 64, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBRows >> 3) << 17) |
                             ((uint32_t)(kARows >> 4) << 24);
 constexpr int kPollLimit = 1 << 22;
 
@@ -101,45 +103,57 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
       "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
       : "memory");
 }
 
-// byte offset of element (row, k) of an operand of R rows x 64 TF32 in the K-major
-// 64-byte-swizzle layout: 4 regions of 16 K-elements, each R rows x 64 bytes in groups of
-// 8 rows (512 bytes); 16-byte granule g of row r sits at granule g ^ ((r >> 1) & 3)
+// byte offset of bf16 element (row, k) of an operand of R rows x 64 in the K-major 64-byte-swizzle
+// layout: 2 regions of 32 K-elements, each R rows x 64 bytes in groups of 8 rows (512 bytes);
+// 16-byte granule g (8 elements) of row r sits at granule g ^ ((r >> 1) & 3)
 __device__ __forceinline__ uint32_t sw_off(int row, int k, int R) {
-  const int kin = k & 15, g = kin >> 2, r8 = row & 7;
-  return (uint32_t)((k >> 4) * (R * 64) + (row >> 3) * 512 + r8 * 64 + ((g ^ ((r8 >> 1) & 3)) << 4) + ((kin & 3) << 2));
+  const int kin = k & 31, g = kin >> 3, r8 = row & 7;
+  return (uint32_t)((k >> 5) * (R * 64) + (row >> 3) * 512 + r8 * 64 + ((g ^ ((r8 >> 1) & 3)) << 4) + ((kin & 7) << 1));
 }
 
-__device__ __forceinline__ uint32_t tf32_hi(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return r;
+// (lo, hi) -> packed bf16x2, round to nearest (lo in the low half: the lower address)
+__device__ __forceinline__ uint32_t bf2_rn(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// two values -> three packed bf16x2 words with e = p0 + p1 + p2 (each remainder is exact in FP32)
+__device__ __forceinline__ void split3(float e0, float e1, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
+  w0 = bf2_rn(e0, e1);
+  const float r0 = e0 - __uint_as_float(w0 << 16), r1 = e1 - __uint_as_float(w0 & 0xffff0000u);
+  w1 = bf2_rn(r0, r1);
+  w2 = bf2_rn(r0 - __uint_as_float(w1 << 16), r1 - __uint_as_float(w1 & 0xffff0000u));
+}
+// eight values -> the three parts' 16-byte granules
+struct Granule3 {
+  uint4 p[3];
+};
+__device__ __forceinline__ Granule3 split3x8(const float* v) {
+  uint32_t w[3][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) split3(v[2 * e], v[2 * e + 1], w[0][e], w[1][e], w[2][e]);
+  Granule3 g;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) g.p[q] = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+  return g;
 }
 
-// A row m: values a[0..63] (re 0..31, im 32..63) -> TF32 high and low parts
-__device__ __forceinline__ void write_a_row(unsigned char* Ahi, unsigned char* Alo, int m, const float (&a)[64]) {
+// A row m: values a[0..63] (re 0..31, im 32..63) -> the three bf16 parts (kABytes apart)
+__device__ __forceinline__ void write_a_row(unsigned char* A, int m, const float (&a)[64]) {
 #pragma unroll
-  for (int g = 0; g < 16; ++g) {
-    uint4 h, l;
-    uint32_t hv[4], lv[4];
+  for (int g = 0; g < 8; ++g) {
+    const Granule3 q = split3x8(a + 8 * g);
+    const uint32_t off = sw_off(m, 8 * g, kARows);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float v = a[4 * g + e];
-      hv[e] = tf32_hi(v);
-      lv[e] = tf32_hi(v - __uint_as_float(hv[e]));
-    }
-    h = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-    l = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-    const uint32_t off = sw_off(m, 4 * g, kARows);
-    *(uint4*)(Ahi + off) = h;
-    *(uint4*)(Alo + off) = l;
+    for (int p = 0; p < 3; ++p) *(uint4*)(A + p * kABytes + off) = q.p[p];
   }
 }
 
@@ -205,51 +219,36 @@ __device__ __forceinline__ void tile_from_slot(TileRegs& r, const unsigned char*
     }
   }
 }
-// four values -> TF32 high and low granules at byte offset off
-__device__ __forceinline__ void put_granule(unsigned char* Bhi, unsigned char* Blo, uint32_t off, float a, float b,
-                                            float c, float d) {
-  const float v[4] = {a, b, c, d};
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    h[e] = tf32_hi(v[e]);
-    l[e] = tf32_hi(v[e] - __uint_as_float(h[e]));
-  }
-  *(uint4*)(Bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-  *(uint4*)(Blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-}
-// B (TF32 high and low parts) of the embedded tile: B[n][k] = s [[Mr, -Mi], [Mi, Mr]],
-// n = output row (re 0..31, im 32..63), k = input (re 0..31, im 32..63); 16-byte granules
-struct BOffsets {  // this thread's 8 granule offsets in a B part (constant per thread)
-  uint32_t o[8];
+// B (three bf16 parts, kBBytes apart) of the embedded tile: B[n][k] = s [[Mr, -Mi], [Mi, Mr]],
+// n = output row (re 0..31, im 32..63), k = input (re 0..31, im 32..63).  Thread (r, c0) writes the
+// four granules of rows r and 32 + r at k = c0..c0+7 and 32+c0..32+c0+7.
+struct BOffsets {  // this thread's 4 granule offsets in a B part (constant per thread)
+  uint32_t o[4];
   __device__ void init() {
     const int r = threadIdx.x & 31, c0 = 8 * (threadIdx.x >> 5);
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      const int k = c0 + 4 * g;
-      o[4 * g + 0] = sw_off(r, k, kBRows);
-      o[4 * g + 1] = sw_off(r, 32 + k, kBRows);
-      o[4 * g + 2] = sw_off(32 + r, k, kBRows);
-      o[4 * g + 3] = sw_off(32 + r, 32 + k, kBRows);
-    }
+    o[0] = sw_off(r, c0, kBRows);
+    o[1] = sw_off(r, 32 + c0, kBRows);
+    o[2] = sw_off(32 + r, c0, kBRows);
+    o[3] = sw_off(32 + r, 32 + c0, kBRows);
   }
 };
-__device__ __forceinline__ void write_b(unsigned char* Bhi, unsigned char* Blo, const TileRegs& t, float s,
-                                        const BOffsets& bo) {
+__device__ __forceinline__ void write_b(unsigned char* B, const TileRegs& t, float s, const BOffsets& bo) {
   float mr[8], mi[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     mr[j] = s * t.v[j].x;
     mi[j] = s * t.v[j].y;
   }
+  const Granule3 R = split3x8(mr), I = split3x8(mi);
 #pragma unroll
-  for (int g = 0; g < 2; ++g) {
-    const float* R = mr + 4 * g;
-    const float* I = mi + 4 * g;
-    put_granule(Bhi, Blo, bo.o[4 * g + 0], R[0], R[1], R[2], R[3]);
-    put_granule(Bhi, Blo, bo.o[4 * g + 1], -I[0], -I[1], -I[2], -I[3]);
-    put_granule(Bhi, Blo, bo.o[4 * g + 2], I[0], I[1], I[2], I[3]);
-    put_granule(Bhi, Blo, bo.o[4 * g + 3], R[0], R[1], R[2], R[3]);
+  for (int p = 0; p < 3; ++p) {
+    unsigned char* Bp = B + p * kBBytes;
+    const uint4 ni = make_uint4(I.p[p].x ^ 0x80008000u, I.p[p].y ^ 0x80008000u, I.p[p].z ^ 0x80008000u,
+                                I.p[p].w ^ 0x80008000u);  // -Mi: the parts of -v are the negated parts of v
+    *(uint4*)(Bp + bo.o[0]) = R.p[p];
+    *(uint4*)(Bp + bo.o[1]) = ni;
+    *(uint4*)(Bp + bo.o[2]) = I.p[p];
+    *(uint4*)(Bp + bo.o[3]) = R.p[p];
   }
 }
 
@@ -264,18 +263,21 @@ __device__ __forceinline__ void l2_prefetch_rows(const float2* X, int64_t n, int
   if (row0 + 16 < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(X + row0 + 16));
 }
 
-// the 3xTF32 product of one tile: 8 K-steps of 8, three MMAs each.  The descriptor of K-step s is
+// the bf16x6 product of one tile: 4 K-steps of 16, six MMAs each.  The descriptor of K-step s is
 // the base descriptor plus the step's byte offset / 16 (the start-address field; no carry out of
-// it below 256 KiB of shared memory).
-__device__ __forceinline__ void mma_group(uint32_t d, uint64_t dahi, uint64_t dalo, uint64_t dbhi, uint64_t dblo,
+// it below 256 KiB of shared memory).  da, db: descriptors of the three parts.
+__device__ __forceinline__ void mma_group(uint32_t d, const uint64_t (&da)[3], const uint64_t (&db)[3],
                                           bool accumulate) {
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
+  for (int s = 0; s < 4; ++s) {
     const uint64_t ka = (uint64_t)(((s >> 1) * (kARows * 64) + (s & 1) * 32) >> 4);
     const uint64_t kb = (uint64_t)(((s >> 1) * (kBRows * 64) + (s & 1) * 32) >> 4);
-    mma_tf32(d, dahi + ka, dbhi + kb, (accumulate || s > 0) ? 1u : 0u);
-    mma_tf32(d, dahi + ka, dblo + kb, 1u);
-    mma_tf32(d, dalo + ka, dbhi + kb, 1u);
+    mma_bf16(d, da[0] + ka, db[0] + kb, (accumulate || s > 0) ? 1u : 0u);
+    mma_bf16(d, da[0] + ka, db[1] + kb, 1u);
+    mma_bf16(d, da[1] + ka, db[0] + kb, 1u);
+    mma_bf16(d, da[0] + ka, db[2] + kb, 1u);
+    mma_bf16(d, da[1] + ka, db[1] + kb, 1u);
+    mma_bf16(d, da[2] + ka, db[0] + kb, 1u);
   }
 }
 
@@ -389,11 +391,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const int2* items, int nitems, int* counter) {
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  unsigned char* Ahi = sm;
-  unsigned char* Alo = Ahi + kABytes;
-  unsigned char* Bbuf = Alo + kABytes;                        // B buffer b: high part, then low part
-  auto Bhi = [&](int b) { return Bbuf + (size_t)b * 2 * kBBytes; };
-  unsigned char* slots = Bbuf + 4 * kBBytes;                  // 2 bt + 1 staged factor tiles
+  unsigned char* Abuf = sm;                                   // A: three bf16 parts
+  unsigned char* Bbuf = Abuf + 3 * kABytes;                   // B buffer b: three bf16 parts
+  auto Bof = [&](int b) { return Bbuf + (size_t)b * 3 * kBBytes; };
+  unsigned char* slots = Bbuf + 6 * kBBytes;                  // 2 bt + 1 staged factor tiles
   const int Pmax = (g.bt + 1) * kTile;
   int16_t* perm_base = (int16_t*)(slots + (size_t)(2 * g.bt + 1) * kSlotBytes);  // [warp][2][Pmax]
   uint64_t* bars = (uint64_t*)(((uintptr_t)(perm_base + 8 * Pmax) + 7) & ~(uintptr_t)7);
@@ -442,7 +443,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     if (warp == 4) {
       // ================= the MMA warp: the step sequence of the sweeps, products only =================
-      const uint64_t da_hi = sw64_desc(smem_u32(Ahi)), da_lo = sw64_desc(smem_u32(Alo));
+      uint64_t da[3];
+      for (int p = 0; p < 3; ++p) da[p] = sw64_desc(smem_u32(Abuf + p * kABytes));
       // the next tile's group into TMEM column dcol once its operands are in place
       auto group = [&](uint32_t dcol, bool accumulate, bool wait_a, bool commit_x, bool commit_step) -> bool {
         if (wait_a && !wwait(bar(kBarAFull), ++na)) return false;
@@ -450,8 +452,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!wwait(bar(kBarFull0 + b), uses[b] + 1)) return false;
         tc_fence_after();
         if (lane == 0) {
-          mma_group(tbase + dcol, da_hi, da_lo, sw64_desc(smem_u32(Bhi(b))), sw64_desc(smem_u32(Bhi(b) + kBBytes)),
-                    accumulate);
+          uint64_t db[3];
+          for (int p = 0; p < 3; ++p) db[p] = sw64_desc(smem_u32(Bof(b) + p * kBBytes));
+          mma_group(tbase + dcol, da, db, accumulate);
           tc_commit(bar(kBarEmpty0 + b));
           if (commit_x) tc_commit(bar(kBarX));
           if (commit_step) tc_commit(bar(kBarStep));
@@ -514,7 +517,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (uses[b] > 0 && !wwait(bar(kBarEmpty0 + b), uses[b])) return false;
         TileRegs tr;
         tile_from_slot<TRANS == 1>(tr, slot(q));
-        write_b(Bhi(b), Bhi(b) + kBBytes, tr, s, boff);
+        write_b(Bof(b), tr, s, boff);
         proxy_fence();
         tc_fence_before();
         __syncwarp();
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       };
       // A <- this thread's 64 values, then handed to the MMA warp (with every TMEM access before it)
       auto put_a = [&](const float (&a)[64]) {
-        write_a_row(Ahi, Alo, t, a);
+        write_a_row(Abuf, t, a);
         proxy_fence();
         tc_fence_before();
         __syncwarp();
@@ -793,7 +796,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 size_t solve_tc_smem_bytes(const FactorGeom& g) {
   const int Pmax = (g.bt + 1) * kTile;
-  return 1024 + 2 * (size_t)kABytes + 4 * (size_t)kBBytes + (size_t)(2 * g.bt + 1) * kSlotBytes +
+  return 1024 + 3 * (size_t)kABytes + 6 * (size_t)kBBytes + (size_t)(2 * g.bt + 1) * kSlotBytes +
          8 * (size_t)Pmax * sizeof(int16_t) + 8 * kNumBars + 8;
 }
 
