@@ -93,7 +93,7 @@ class Stats(C.Structure):
         ("eig_fallback_unconverged", C.c_int32), ("eig_fallback_wide", C.c_int32),
         ("rhs_chunk_used", C.c_int32), ("gram_splits_used", C.c_int32), ("tuned", C.c_int32),
         ("graph_launches", C.c_int32), ("cholqr_shifted", C.c_int32), ("gram_fp64", C.c_int32),
-        ("rr_fp64_from", C.c_int32),
+        ("rr_fp64_from", C.c_int32), ("rhs_chunk_early", C.c_int32),
     ]
 
     def as_dict(self):

@@ -606,8 +606,17 @@ struct Feast {
   bool rr_fp64_now = false;
   static constexpr int kFFIterations = 3;
 
-  // autotuned choices (see tune.cu)
-  int rhs_chunk = 32;
+  // autotuned choices (see tune.cu).  Solve width of a filter pass: chunk_early (the tensor-core
+  // solve, when it is available and was measured faster) for the first kTcIterations passes, then
+  // chunk_late (the fastest FP32-FMA solve).  The tensor core truncates its FP32 accumulator at
+  // every MMA, which leaves its solves 2-3x less accurate; the refined iteration contracts with the
+  // solve error, so its converging passes take the round-to-nearest kernels.  An explicit
+  // rhs_chunk serves every pass.
+  int rhs_chunk = 32;  // width of the current pass
+  int chunk_late = 32, chunk_early = 0;
+  int iter_now = 1;
+  static constexpr int kTcIterations = 2;
+  int pass_chunk() const { return (chunk_early && iter_now <= kTcIterations) ? chunk_early : chunk_late; }
   int gram_splits = 0;  // 0: heuristic
   bool tune_solve = false, tune_gram = false;
 
@@ -616,15 +625,26 @@ struct Feast {
     return (o->precision == PDESHEP_MIXED && solve_tm_supported(g)) ? kTmChunk : 32;
   }
   void setup_tuning() {
-    rhs_chunk = o->rhs_chunk > 0 ? o->rhs_chunk : default_chunk();
+    if (o->rhs_chunk > 0) {
+      chunk_late = o->rhs_chunk;
+      chunk_early = 0;
+    } else {
+      chunk_late = default_chunk();
+      chunk_early = (o->precision == PDESHEP_MIXED && solve_tc_supported(g)) ? kTcChunk : 0;
+    }
+    rhs_chunk = pass_chunk();
     if (o->autotune <= 0) return;
     int v = 0;
     if (o->rhs_chunk <= 0) {
+      // the stored choice: chunk_late + 1000 if the tensor-core solve serves the first passes
       const std::string k = tune_key("solve", n, b, cplx, o->precision, K * ne, max_m0);
-      if (o->autotune == 1 && tune_lookup(o->tune_cache, k, &v))
-        rhs_chunk = v;
-      else
+      if (o->autotune == 1 && tune_lookup(o->tune_cache, k, &v)) {
+        chunk_late = v % 1000;
+        chunk_early = v >= 1000 ? kTcChunk : 0;
+        rhs_chunk = pass_chunk();
+      } else {
         tune_solve = true;
+      }
     }
     if (tc()) return;  // the tensor-core products choose their own split
     const std::string kg = tune_key("gram", n, b, cplx, o->precision * 2 + ff(), K, max_m0);
@@ -1023,7 +1043,7 @@ struct FeastRun : Feast<S, C> {
       cudaEvent_t t0, t1;
       PD_CK(cudaEventCreate(&t0));
       PD_CK(cudaEventCreate(&t1));
-      float best = 1e30f;
+      float best = 1e30f, t_tc = 1e30f;
       int best_cw = this->default_chunk();
       for (int cw : {16, 32, 64, kTmChunk, kTcChunk}) {
         if (cw == kTmChunk   ? !(sizeof(C) == sizeof(float2) && solve_tm_supported(g))
@@ -1037,19 +1057,25 @@ struct FeastRun : Feast<S, C> {
         PD_CK(cudaEventSynchronize(t1));
         float ms = 0;
         PD_CK(cudaEventElapsedTime(&ms, t0, t1));
-        if (ms < best) {
+        if (cw == kTcChunk) {
+          t_tc = ms;
+        } else if (ms < best) {
           best = ms;
           best_cw = cw;
         }
       }
       cudaEventDestroy(t0);
       cudaEventDestroy(t1);
-      this->rhs_chunk = best_cw;
+      this->chunk_late = best_cw;
+      this->chunk_early = t_tc < best ? kTcChunk : 0;
+      this->rhs_chunk = this->pass_chunk();
       this->tune_solve = false;
       stats.tuned += 1;
-      tune_store(o->tune_cache, tune_key("solve", n, b, cplx, o->precision, K * ne, max_m0), best_cw);
+      tune_store(o->tune_cache, tune_key("solve", n, b, cplx, o->precision, K * ne, max_m0),
+                 this->chunk_late + (this->chunk_early ? 1000 : 0));
     }
     const int chunk = this->rhs_chunk;
+    stats.rhs_chunk_early = this->chunk_early;
     stats.rhs_chunk_used = chunk;
     PD_TRY(launch_solve<C>(g, 0, ns, sd.data(), p.d_sys, p.wave_base, (const C*)p.Yc, (C*)p.wave_base, chunk,
                            p.solve_queue, st));
@@ -1090,7 +1116,7 @@ struct FeastRun : Feast<S, C> {
   // CUDA graphs of the filter pass, one per (active slices, mode)
   struct FilterGraph {
     std::vector<int> active;
-    int mode;
+    int mode, chunk;
     cudaGraphExec_t exec;
     long long kernels;
   };
@@ -1139,7 +1165,7 @@ struct FeastRun : Feast<S, C> {
     PD_TRY(upload_solve_items((int)sd.size(), sd.data(), this->rhs_chunk, p.solve_queue, st, &nitems));
     FilterGraph* fg = nullptr;
     for (auto& f : fgraphs)
-      if (f.mode == mode && f.active == active) fg = &f;
+      if (f.mode == mode && f.active == active && f.chunk == this->rhs_chunk) fg = &f;
     if (!fg) {
       const unsigned long long l0 = launches_so_far();
       cudaGraph_t graph;
@@ -1151,6 +1177,7 @@ struct FeastRun : Feast<S, C> {
       FilterGraph f;
       f.active = active;
       f.mode = mode;
+      f.chunk = this->rhs_chunk;
       f.kernels = (long long)(launches_so_far() - l0);
       count_launches(-f.kernels);  // counted when they run
       const cudaError_t ei = cudaGraphInstantiate(&f.exec, graph, 0);
@@ -1168,6 +1195,7 @@ struct FeastRun : Feast<S, C> {
     for (auto& d : sd) stats.rhs_sweeps += ceil_div(d.ncols, this->rhs_chunk) * (cplx ? 2 : 1);
     stats.rhs_columns += (int64_t)cols * (cplx ? 2 : 1);
     stats.rhs_chunk_used = this->rhs_chunk;
+    stats.rhs_chunk_early = this->chunk_early;
     stats.graph_launches += 1;
     return 0;
   }
@@ -1176,6 +1204,7 @@ struct FeastRun : Feast<S, C> {
   int filter() {
     const int na = (int)active.size();
     if (!na) return 0;
+    if (!this->tune_solve) this->rhs_chunk = this->pass_chunk();
     if (graph_ready()) return filter_graph();
     PD_TRY(upload_active());
     const int mm = act_max_m0();
@@ -1464,6 +1493,7 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
   int it = 1;
   for (; it <= o->max_iter && !F.active.empty(); ++it) {
     F.mode = (refine && it > 1) ? 1 : 0;
+    F.iter_now = it;
     if (it > F.kFFIterations && F.ff()) {
       F.rr_fp64_now = true;
       F.eig.ff = 0;
@@ -1594,6 +1624,7 @@ void merge_stats(pdeshep_stats& t, const pdeshep_stats& g) {
   t.eig_fallback_unconverged += g.eig_fallback_unconverged;
   t.eig_fallback_wide += g.eig_fallback_wide;
   t.rhs_chunk_used = g.rhs_chunk_used;
+  t.rhs_chunk_early = std::max(t.rhs_chunk_early, g.rhs_chunk_early);
   t.gram_splits_used = g.gram_splits_used;
   t.tuned += g.tuned;
   t.graph_launches += g.graph_launches;
