@@ -365,7 +365,7 @@ def run_sequence(pk, torch, seq, W, K, stream, clocks=None, dist=None, dev=None)
     kg_ms = {gname: 0.0 for gname in pk.KERNEL_GROUPS}
     kg_fl = {gname: 0.0 for gname in pk.KERNEL_GROUPS}
     kg_n = {gname: 0 for gname in pk.KERNEL_GROUPS}
-    iters, statuses, eig_rep, tuned = [], [], [], {}
+    iters, statuses, eig_rep, tuned, step_ms, warm = [], [], [], {}, [], []
     for _ in range(K):
         k, g, x0, bounds = walk.inputs()
         inputs.append((k, g, x0, bounds))
@@ -373,6 +373,8 @@ def run_sequence(pk, torch, seq, W, K, stream, clocks=None, dist=None, dev=None)
         statuses.append(r.status)
         pairs += good_pairs(r)
         iters.append(r.stats["iterations"])
+        step_ms.append(round(r.stats["ms_total"], 1))
+        warm.append(x0 is not None)
         eig_rep.append((r.stats["rr_calls"], r.stats["jacobi_sweeps32"], r.stats["eig_refine_steps"],
                         r.stats["eig_fallback_unconverged"] + r.stats["eig_fallback_wide"]))
         tuned = {"rhs_chunk": r.stats["rhs_chunk_used"], "gram_splits": r.stats["gram_splits_used"]}
@@ -389,7 +391,8 @@ def run_sequence(pk, torch, seq, W, K, stream, clocks=None, dist=None, dev=None)
     t_s = e0.elapsed_time(e1) / 1e3
     t_s, pairs = reduce_over_ranks(dist, torch, dev, t_s, pairs)
     return dict(t_s=t_s, pairs=pairs, kg_ms=kg_ms, kg_fl=kg_fl, kg_n=kg_n, iters=iters, statuses=statuses,
-                eig=eig_rep, tuned=tuned, launches=int(launches), clocks=clk, last=r), inputs
+                eig=eig_rep, tuned=tuned, launches=int(launches), clocks=clk, last=r, step_ms=step_ms,
+                warm=warm), inputs
 
 
 def roofline(meas, bounds_tbl, traffic_key):
@@ -459,7 +462,8 @@ def run_gpu(args):
                       "l2": "inputs larger than L2 (factors of one step exceed 1 GB)",
                       "bnorm": "||B_k||_2 by bisection on inertia before timing (%.0f ms per matrix)" % seq.bnorm_ms,
                       "parallelism": "replicas" if world > 1 else "single GPU"},
-           "iterations_per_step": meas["iters"], "status_per_step": meas["statuses"],
+           "iterations_per_step": meas["iters"], "call_ms_per_step": meas["step_ms"],
+           "warm_start_per_step": meas["warm"], "status_per_step": meas["statuses"],
            "eigensolver_rr_sweeps32_refine_fallback": meas["eig"], "autotuned": meas["tuned"],
            "kernel_groups": groups, "roofline": roof, "peaks": peaks, "clocks": meas["clocks"],
            "gpu_launches": meas["launches"]}

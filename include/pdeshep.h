@@ -170,9 +170,9 @@ typedef struct {
   int32_t gram_fp64;       /* float-float mode: slices whose Gram matrices were redone in FP64 */
   int32_t rr_fp64_from;    /* float-float mode: iteration from which the Rayleigh-Ritz products ran in
                               FP64 because slices were still unconverged after 3 iterations (0: never) */
-  int32_t rhs_chunk_early; /* solve column block of the first two filter passes when it differs from the
-                              later passes' (256: the tensor-core solve, chosen when measured faster; the
-                              later, converging passes take the round-to-nearest FP32-FMA solves); 0: none */
+  int32_t rhs_chunk_early; /* solve column block of the first four filter passes when it differs from
+                              the later passes' (256: the tensor-core solve, chosen when measured faster;
+                              passes after the fourth take the round-to-nearest FP32-FMA solves); 0: none */
 } pdeshep_stats;
 
 /* Forget every tuned choice held in this process (cache files are kept). */

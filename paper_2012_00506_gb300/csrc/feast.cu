@@ -606,16 +606,19 @@ struct Feast {
   bool rr_fp64_now = false;
   static constexpr int kFFIterations = 3;
 
-  // autotuned choices (see tune.cu).  Solve width of a filter pass: chunk_early (the tensor-core
-  // solve, when it is available and was measured faster) for the first kTcIterations passes, then
-  // chunk_late (the fastest FP32-FMA solve).  The tensor core truncates its FP32 accumulator at
-  // every MMA, which leaves its solves 2-3x less accurate; the refined iteration contracts with the
-  // solve error, so its converging passes take the round-to-nearest kernels.  An explicit
-  // rhs_chunk serves every pass.
+  // autotuned choices (see tune.cu).  Solve width of a filter pass: chunk_early, the tensor-core
+  // solve (when available and measured faster than every FP32-FMA width), for the first
+  // kTcIterations passes, then chunk_late, the fastest FP32-FMA solve.  The tensor core truncates
+  // its FP32 accumulator at every MMA, which leaves its solves 2-3x less accurate; the refined
+  // iteration contracts with the solve error, so a slice still unconverged after kTcIterations
+  // passes finishes with the round-to-nearest kernels (measured on the C5 sequence: tensor-core
+  // solves on every pass and on the first four give the same throughput, but the first lets single
+  // steps run to 7 iterations; two or three passes are slower).  An explicit rhs_chunk serves every
+  // pass.
   int rhs_chunk = 32;  // width of the current pass
   int chunk_late = 32, chunk_early = 0;
   int iter_now = 1;
-  static constexpr int kTcIterations = 2;
+  static constexpr int kTcIterations = 4;
   int pass_chunk() const { return (chunk_early && iter_now <= kTcIterations) ? chunk_early : chunk_late; }
   int gram_splits = 0;  // 0: heuristic
   bool tune_solve = false, tune_gram = false;
