@@ -377,7 +377,8 @@ def run_sequence(pk, torch, seq, W, K, stream, clocks=None, dist=None, dev=None)
         warm.append(x0 is not None)
         eig_rep.append((r.stats["rr_calls"], r.stats["jacobi_sweeps32"], r.stats["eig_refine_steps"],
                         r.stats["eig_fallback_unconverged"] + r.stats["eig_fallback_wide"]))
-        tuned = {"rhs_chunk": r.stats["rhs_chunk_used"], "gram_splits": r.stats["gram_splits_used"]}
+        tuned = {"rhs_chunk": r.stats["rhs_chunk_used"], "rhs_chunk_early": r.stats["rhs_chunk_early"],
+                 "gram_splits": r.stats["gram_splits_used"]}
         for gname in pk.KERNEL_GROUPS:
             kg_ms[gname] += r.stats["kg_ms"][gname]
             kg_fl[gname] += r.stats["kg_flops"][gname]
@@ -395,8 +396,21 @@ def run_sequence(pk, torch, seq, W, K, stream, clocks=None, dist=None, dev=None)
                 warm=warm), inputs
 
 
+def solve_bound(bounds_tbl, tuned):
+    """The solve group's roofline: the tensor-core solve (bf16x6 products, FP32-class) when the
+    autotuner chose it for the early passes, else the FP32 FMA pipe."""
+    tb = dict(bounds_tbl)
+    if tuned.get("rhs_chunk_early") == 256 or tuned.get("rhs_chunk") == 256:
+        tb["solve"] = ("tensor", BF16_SUSTAINED_TFLOPS / 6,
+                       "bf16 tensor cores (sustained, %s) / 6 bf16 products per FP32-class product (bf16x6); "
+                       "the group also holds the round-to-nearest passes after the fourth and the adjoint "
+                       "backward sweeps on the FP32 pipe" % BF16_PEAK_SOURCE)
+    return tb
+
+
 def roofline(meas, bounds_tbl, traffic_key):
     kg_ms, kg_fl, kg_n, t_s = meas["kg_ms"], meas["kg_fl"], meas["kg_n"], meas["t_s"]
+    bounds_tbl = solve_bound(bounds_tbl, meas["tuned"])
     # the inertia counts run on a side stream beside the first filter pass (off the critical path)
     dom = max((gname for gname in kg_ms if gname != "inertia"), key=lambda gname: kg_ms[gname])
     bound, peak, kind = bounds_tbl[dom]
@@ -719,17 +733,21 @@ def traffic_for(group, key):
     return ent.get("dram_bytes_per_launch")
 
 
-GROUP_SOURCES = {"solve": "band_lu.cu", "factor": "band_lu.cu", "gemm": "tcgemm.cu", "small": "dense.cu",
+GROUP_SOURCES = {"solve": ("band_lu.cu", "solve_tc.cu", "solve_tm.cu"), "factor": "band_lu.cu", "gemm": "tcgemm.cu", "small": "dense.cu",
                  "bandmm": "tcgemm.cu", "accum": "feast.cu", "inertia": "inertia.cu", "eig": "dense.cu"}
 
 
 def source_hash(group):
     import hashlib
-    p = os.path.join(ROOT, "paper_2012_00506_gb300", "csrc", GROUP_SOURCES.get(group, "feast.cu"))
+    files = GROUP_SOURCES.get(group, "feast.cu")
+    files = (files,) if isinstance(files, str) else files
+    h = hashlib.sha1()
     try:
-        return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+        for f in files:
+            h.update(open(os.path.join(ROOT, "paper_2012_00506_gb300", "csrc", f), "rb").read())
     except OSError:
         return None
+    return h.hexdigest()[:12]
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
