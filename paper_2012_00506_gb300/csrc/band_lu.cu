@@ -93,6 +93,19 @@ __global__ void __launch_bounds__(kThreads) init_factor_kernel(FactorGeom g, int
   }
 }
 
+// (value, index) of the warp's largest value, the lowest index on ties, in every lane
+template <typename R>
+__device__ __forceinline__ void warp_argmax(R& best, int& idx) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ob > best || (ob == best && oi < idx)) {
+      best = ob;
+      idx = oi;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // factorization: one thread block per system
 // ---------------------------------------------------------------------------
@@ -110,8 +123,9 @@ __global__ void __launch_bounds__(kThreads) factor_kernel(FactorGeom g, const Sy
   C* Li = Cb + (size_t)ldp * T;
   C* Ui = Li + T * T;
   int* perm = (int*)(Ui + T * T);
-  __shared__ int sh_p;
-  __shared__ R sh_best;
+  int* pos = perm + Pmax;  // [2][Pmax]
+  __shared__ R wbest[64];
+  __shared__ int widx[64];
   __shared__ int sh_status;
 
   const int sidx = blockIdx.x;
@@ -131,63 +145,99 @@ __global__ void __launch_bounds__(kThreads) factor_kernel(FactorGeom g, const Sy
       const C* tile = f.tiles + g.tile_index(K + q, K) * g.tile_elems;
       Pan[q * T + r + c * ldp] = tile[w];
     }
-    for (int r = tid; r < P; r += blockDim.x) perm[r] = r;
+    for (int r = tid; r < P; r += blockDim.x) {
+      perm[r] = r;
+      pos[r] = r;
+    }
     __syncthreads();
-    // panel LU with partial pivoting
-    for (int c = 0; c < T; ++c) {
-      if (warp == 0) {
+    // panel LU with partial pivoting, one CTA barrier per column.  Rows are addressed through
+    // pos[] (logical -> physical row), so an interchange moves no data; a thread owns logical rows
+    // tid, tid + blockDim.x, ...: it eliminates them and, in the same phase, takes their part of the
+    // next column's pivot search (warp maxima in wbest/widx; every thread then reduces the warp
+    // maxima itself).  The pivot is the largest |re| + |im| with the lowest row on ties, and every
+    // element sees the same operations in the same order as with physical interchanges.
+    {
+      const int nw = blockDim.x >> 5;
+      // the pivot search of column 0
+      {
         R best = R(-1);
-        int idx = c;
-        for (int r = c + lane; r < P; r += 32) {
-          R v = cabs1(Pan[r + c * ldp]);
+        int idx = 0x7fffffff;
+        for (int r = tid; r < P; r += blockDim.x) {
+          const R v = cabs1(Pan[r]);
           if (v > best) {
             best = v;
             idx = r;
           }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-          R ob = __shfl_down_sync(0xffffffffu, best, o);
-          int oi = __shfl_down_sync(0xffffffffu, idx, o);
-          if (ob > best || (ob == best && oi < idx)) {
+        warp_argmax(best, idx);
+        if (lane == 0) {
+          wbest[warp] = best;
+          widx[warp] = idx;
+        }
+      }
+      __syncthreads();
+      for (int c = 0; c < T; ++c) {
+        const int cur = c & 1;
+        const int* posc = pos + cur * Pmax;
+        int* posn = pos + (cur ^ 1) * Pmax;
+        R best = R(-1);
+        int p = 0x7fffffff;
+        for (int w = 0; w < nw; ++w) {
+          const R ob = wbest[cur * 32 + w];
+          const int oi = widx[cur * 32 + w];
+          if (ob > best || (ob == best && oi < p)) {
             best = ob;
-            idx = oi;
+            p = oi;
           }
         }
-        if (lane == 0) {
-          sh_p = idx;
-          sh_best = best;
-        }
-      }
-      __syncthreads();
-      const int p = sh_p;
-      const R best = sh_best;
-      if (p != c) {
-        for (int j = tid; j < T; j += blockDim.x) {
-          C t = Pan[c + j * ldp];
-          Pan[c + j * ldp] = Pan[p + j * ldp];
-          Pan[p + j * ldp] = t;
-        }
+        const int pp = posc[p], pc = posc[c];  // physical rows of the pivot and of logical row c
         if (tid == 0) {
-          int t = perm[c];
-          perm[c] = perm[p];
-          perm[p] = t;
+          if (p != c) {
+            int tp = perm[c];
+            perm[c] = perm[p];
+            perm[p] = tp;
+          }
+          const int64_t k = (int64_t)K * T + c;
+          if (ipiv && k < g.n) ipiv[(int64_t)sidx * g.n + k] = (int32_t)((int64_t)K * T + p);
+          if (!(best > R(0)) && sh_status == 0) sh_status = (int)(k + 1);
         }
+        const bool ok = best > R(0);
+        const C inv = ok ? crecip(Pan[pp + c * ldp]) : cmk<C>(0, 0);
+        R nb = R(-1);
+        int ni = 0x7fffffff;
+        for (int r = tid; r < P; r += blockDim.x) {
+          const int phys = r == c ? pp : (r == p ? pc : posc[r]);
+          posn[r] = phys;
+          if (r <= c) continue;
+          if (ok) {
+            const C l = cmul(Pan[phys + c * ldp], inv);
+            Pan[phys + c * ldp] = l;
+            for (int j = c + 1; j < T; ++j) cfms(Pan[phys + j * ldp], l, Pan[pp + j * ldp]);
+          }
+          if (c + 1 < T) {
+            const R v = cabs1(Pan[phys + (c + 1) * ldp]);
+            if (v > nb) {
+              nb = v;
+              ni = r;
+            }
+          }
+        }
+        warp_argmax(nb, ni);
+        if (lane == 0) {
+          wbest[(cur ^ 1) * 32 + warp] = nb;
+          widx[(cur ^ 1) * 32 + warp] = ni;
+        }
+        __syncthreads();
       }
-      if (tid == 0) {
-        const int64_t k = (int64_t)K * T + c;
-        if (ipiv && k < g.n) ipiv[(int64_t)sidx * g.n + k] = (int32_t)((int64_t)K * T + p);
-        if (!(best > R(0)) && sh_status == 0) sh_status = (int)(k + 1);
+      // rows back in logical order (pos of column T, an even count: buffer 0)
+      for (int e = tid; e < P * T; e += blockDim.x) {
+        const int r = e % P, cc = e / P;
+        Cb[r + cc * ldp] = Pan[pos[r] + cc * ldp];
       }
       __syncthreads();
-      if (best > R(0)) {
-        const C inv = crecip(Pan[c + c * ldp]);
-        for (int r = c + 1 + tid; r < P; r += blockDim.x) {
-          const C l = cmul(Pan[r + c * ldp], inv);
-          Pan[r + c * ldp] = l;
-          for (int j = c + 1; j < T; ++j) cfms(Pan[r + j * ldp], l, Pan[c + j * ldp]);
-        }
-      }
-      __syncthreads();
+      C* tmp = Pan;
+      Pan = Cb;
+      Cb = tmp;
     }
     // write back the panel (L multipliers and the packed diagonal block)
     for (int e = tid; e < P * T; e += blockDim.x) {
@@ -229,17 +279,22 @@ __global__ void __launch_bounds__(kThreads) factor_kernel(FactorGeom g, const Sy
         ui[e] = Ui[e];
       }
     }
-    // trailing block columns K+1 .. K+nbr
+    // trailing block columns K+1 .. K+nbr: warp w owns columns w, w+8, w+16, w+24 of every block
+    // column through the gather (rows in panel order), U(K, Jc) = Linv Cb[0:T], the rows below
+    // (Cb[T:P] -= L U) and the scatter, so the warps need no barrier between them
     for (int jb = 1; jb <= nbr; ++jb) {
       const int Jc = K + jb;
-      for (int e = tid; e < P * T; e += blockDim.x) {
-        const int r = e % P, c = e / P;
-        const int sr = perm[r];
-        const int q = sr / T, rr = sr % T;
-        const C* tile = f.tiles + g.tile_index(K + q, Jc) * g.tile_elems;
-        Cb[r + c * ldp] = tile[rr + c * T];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int c = warp + 8 * jj;
+        for (int r = lane; r < P; r += 32) {
+          const int sr = perm[r];
+          const int q = sr / T, rr = sr % T;
+          const C* tile = f.tiles + g.tile_index(K + q, Jc) * g.tile_elems;
+          Cb[r + c * ldp] = tile[rr + c * T];
+        }
       }
-      __syncthreads();
+      __syncwarp();
       // top block: U(K, Jc) = Linv * Cb[0:T]
       C acc[4];
 #pragma unroll
@@ -249,10 +304,10 @@ __global__ void __launch_bounds__(kThreads) factor_kernel(FactorGeom g, const Sy
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) cfma(acc[jj], a, Cb[k + (warp + 8 * jj) * ldp]);
       }
-      __syncthreads();
+      __syncwarp();
 #pragma unroll
       for (int jj = 0; jj < 4; ++jj) Cb[lane + (warp + 8 * jj) * ldp] = acc[jj];
-      __syncthreads();
+      __syncwarp();
       // rows below: Cb[T:P] -= L(panel rows T:P) * U(K, Jc)
       for (int q = 1; q <= nbb; ++q) {
         const int r = q * T + lane;
@@ -266,15 +321,19 @@ __global__ void __launch_bounds__(kThreads) factor_kernel(FactorGeom g, const Sy
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) Cb[r + (warp + 8 * jj) * ldp] = acc[jj];
       }
-      __syncthreads();
-      for (int e = tid; e < P * T; e += blockDim.x) {
-        const int r = e % P, c = e / P;
-        const int q = r / T, rr = r % T;
-        C* tile = f.tiles + g.tile_index(K + q, Jc) * g.tile_elems;
-        tile[rr + c * T] = Cb[r + c * ldp];
+      __syncwarp();
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int c = warp + 8 * jj;
+        for (int r = lane; r < P; r += 32) {
+          const int q = r / T, rr = r % T;
+          C* tile = f.tiles + g.tile_index(K + q, Jc) * g.tile_elems;
+          tile[rr + c * T] = Cb[r + c * ldp];
+        }
       }
-      __syncthreads();
+      __syncwarp();
     }
+    __syncthreads();  // block column K+1 (the next panel) and the tiles below are written
   }
   if (tid == 0) status[sidx] = sh_status;
 }
@@ -743,7 +802,7 @@ size_t solve_smem_bytes(const FactorGeom& g, int chunk, size_t es, int trans) {
 static size_t factor_smem_bytes(const FactorGeom& g, size_t es) {
   const int T = kTile;
   const size_t Pmax = (size_t)(g.bt + 1) * T;
-  return es * (2 * (Pmax + 1) * T + 2 * (size_t)T * T) + sizeof(int) * Pmax;
+  return es * (2 * (Pmax + 1) * T + 2 * (size_t)T * T) + sizeof(int) * 3 * Pmax;
 }
 
 template <typename C>

@@ -806,7 +806,7 @@ struct FeastRun : Feast<S, C> {
     double fl = 0.0;
     for (int s : active) fl += this->cw() * (2.0 * b + 1.0) * (double)n * m0[s];
     PD_TRY(this->kt.begin(PDESHEP_KG_BANDMM));
-    if (this->tc() && this->ff()) {  // tensor-core digit products (until the FP64 switch)
+    if (this->tc()) {  // tensor-core digit products (FP64-class, like the tall products: no escalation)
       std::vector<int64_t> xo(K);
       for (int t = 0; t < K; ++t) xo[t] = col_off[t] * n;
       PD_TRY(tc_band_matmul<S>(p.tc, TcShape{n, cplx, m0}, active, xo, X, Y, st));
