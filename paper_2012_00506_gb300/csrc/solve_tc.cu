@@ -28,8 +28,8 @@
 //                      q = 1..2bt (pending blocks start as the forward result)
 //   trans 1, forward (U^H w = y): w_K = Uinv_K^H acc_K,
 //                      block K+q += (-U(K, K+q)^H) w_K          q = 1..2bt
-// The adjoint backward sweep (L^H with the inverse interchanges, whose window
-// rows move between steps) runs on the TMEM kernel of solve_tm.cu.
+//   trans 1, backward (L^H with the inverse interchanges, whose window rows move
+//                      between steps, so it is left-looking): solve_tca_kernel below.
 #include <algorithm>
 
 #include "band_lu.cuh"
@@ -792,6 +792,276 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tslot), "r"(512u));
 }
 
+// ---------------------------------------------------------------------------
+// The adjoint backward sweep (L^H with the inverse interchanges), left-looking:
+//   v_K = w_K + sum_q (-L(K+q, K)^H) w_{K+q}    (q = 1..bt, the window's current blocks)
+//   x_K = Linv_K^H v_K,  then P_K^T on the window (blocks K..K+bt)
+// Every product is a bf16x6 MMA group into a fresh TMEM accumulator (the sum of the step's
+// update products, then x_K), so the window blocks themselves are only written by the compute
+// warps (round-to-nearest add of the sum to w_K).  A and B of each group go together into one of
+// two operand pairs (full/empty mbarriers).  Factor tiles of the next step are staged per warp by
+// cp.async in consumption order (the update tiles, then Linv with the permutation).
+// ---------------------------------------------------------------------------
+constexpr int kPairBytes = 3 * kABytes + 3 * kBBytes;  // A and B, three bf16 parts each: 72 KiB
+enum { kQFull0 = 0, kQFull1, kQEmpty0, kQEmpty1, kQX, kQStep, kQDrain, kQNumBars };
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    solve_tca_kernel(FactorGeom g, const SysDesc* sys, const char* arena, float2* out, const int2* items,
+                     int nitems, int* counter) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  auto pairA = [&](int p) { return sm + (size_t)p * kPairBytes; };
+  auto pairB = [&](int p) { return sm + (size_t)p * kPairBytes + 3 * kABytes; };
+  unsigned char* slots = sm + 2 * (size_t)kPairBytes;        // bt + 1 staged tiles: Linv, L(K+q, K)
+  const int Pmax = (g.bt + 1) * kTile;
+  int16_t* perm_base = (int16_t*)(slots + (size_t)(g.bt + 1) * kSlotBytes);  // [warp][2][Pmax]
+  int16_t* invp_base = perm_base + 8 * Pmax;                                  // [warp][32]
+  uint64_t* bars = (uint64_t*)(((uintptr_t)(invp_base + 4 * 32) + 7) & ~(uintptr_t)7);
+  __shared__ uint32_t tslot;
+  __shared__ int sh_item;
+  __shared__ volatile int sh_bad;
+
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  auto bar = [&](int i) { return smem_u32(bars + i); };
+  auto wwait = [&](uint32_t b, int k) -> bool { return __all_sync(~0u, wait_k(b, k, &sh_bad)) != 0; };
+  if (t == 0) {
+    for (int i = 0; i < kQNumBars; ++i) mbar_init(bar(i), (i == kQFull0 || i == kQFull1) ? 4u : 1u);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sh_bad = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+  const uint32_t tb = tslot + ((uint32_t)(32 * (warp & 3)) << 16);
+  const int bt = g.bt, Nb = g.Nb;
+  const int64_t n = g.n, te = g.tile_elems;
+  const int ringw = bt + 1;
+  const uint32_t scratch = (uint32_t)(64 * ringw);  // the step's accumulator
+  int uses[2] = {0, 0};                              // groups issued on operand pair p
+  int cur = 0;                                       // operand pair of the next group
+  int nx = 0, nstep = 0;
+
+  for (;;) {
+    if (t == 0) sh_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = sh_item;
+    if (item >= nitems || sh_bad) break;
+    const int2 w = items[item];
+    const SysDesc d = sys[w.x];
+    const FactorPtr<float2> f = factor_ptr<float2>(g, (char*)arena + d.factor_off);
+
+    if (warp == 4) {
+      // ================= the MMA warp =================
+      auto group = [&](bool accumulate, bool commit_x, bool commit_step) -> bool {
+        const int p = cur;
+        if (!wwait(bar(kQFull0 + p), uses[p] + 1)) return false;
+        tc_fence_after();
+        if (lane == 0) {
+          uint64_t da[3], db[3];
+          for (int q = 0; q < 3; ++q) {
+            da[q] = sw64_desc(smem_u32(pairA(p) + q * kABytes));
+            db[q] = sw64_desc(smem_u32(pairB(p) + q * kBBytes));
+          }
+          mma_group(tbase + scratch, da, db, accumulate);
+          tc_commit(bar(kQEmpty0 + p));
+          if (commit_x) tc_commit(bar(kQX));
+          if (commit_step) tc_commit(bar(kQStep));
+        }
+        __syncwarp();
+        uses[p] += 1;
+        cur ^= 1;
+        return true;
+      };
+      bool ok = true;
+      for (int K = Nb - 1; K >= 0 && ok; --K) {
+        const int nb = min(bt, Nb - 1 - K);
+        for (int q = 1; q <= nb && ok; ++q) ok = group(q > 1, q == nb, false);
+        if (ok) ok = group(false, false, true);
+      }
+    } else {
+      // ================= compute warps =================
+      const int col = w.y + t;
+      const bool valid = col < d.ncols;
+      float2* X = out + d.out2_off + (int64_t)(valid ? col : 0) * n;
+      auto tile_of = [&](int I, int J) { return f.tiles + g.tile_index(I, J) * te; };
+      auto slot = [&](int q) { return slots + (size_t)q * kSlotBytes; };
+      auto permbuf = [&](int K) { return perm_base + (size_t)(2 * warp + (K & 1)) * Pmax; };
+      int16_t* invp = invp_base + 32 * warp;
+      BOffsets boff;
+      boff.init();
+      float v[64], x[64];
+      bool ok = true;
+      auto scol = [&](int J) { return (uint32_t)(64 * (J % ringw)); };
+      auto stage = [&](int q, const float2* T, int Kperm) {
+        stage_tile_warp<true>(smem_u32(slot(q)), T, warp, lane);
+        if (Kperm >= 0) stage_bytes_warp(smem_u32(permbuf(Kperm)), f.perm + (int64_t)Kperm * Pmax, 2 * Pmax, lane);
+        cp_async_commit();
+      };
+      // operand pair `cur` <- A (this thread's 64 values) and B (staged tile q scaled by s), once
+      // the pair's last group is done; the MMA warp takes it when all four warps arrived
+      auto put_pair = [&](const float (&a)[64], int q, float s) -> bool {
+        const int p = cur;
+        if (uses[p] > 0 && !wwait(bar(kQEmpty0 + p), uses[p])) return false;
+        write_a_row(pairA(p), t, a);
+        TileRegs tr;
+        tile_from_slot<true>(tr, slot(q));
+        write_b(pairB(p), tr, s, boff);
+        proxy_fence();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(kQFull0 + p));
+        uses[p] += 1;
+        cur ^= 1;
+        return true;
+      };
+      // the first step (K = Nb-1, no updates): Linv_{Nb-1} with P_{Nb-1}
+      stage(0, f.inv + (int64_t)(2 * (Nb - 1)) * te, Nb - 1);
+      for (int K = Nb - 1; K >= 0 && ok; --K) {
+        const int nb = min(bt, Nb - 1 - K);
+        const int nbp = K + 1 < Nb ? min(bt, Nb - 2 - K) : 0;  // tiles the previous step consumed
+        const int nbn = K >= 1 ? min(bt, Nb - K) : -1;         // the next step's update count
+        const uint32_t sk = scol(K);
+        int cnt = 0;
+        // the next step's update tile that this step does not use goes out first
+        for (int q = nb + 1; q <= nbn; ++q) {
+          stage(q, tile_of(K - 1 + q, K - 1), -1);
+          ++cnt;
+        }
+        // block K+bt+1 leaves the window (final); w_K enters its slot
+        if (K + bt + 1 < Nb) {
+          blk_from_tm(x, tb + sk);
+          blk_to_global(x, X, n, (int64_t)(K + bt + 1) * kTile, valid, 0, 16);
+        }
+        blk_from_global(v, X, n, (int64_t)K * kTile, valid);
+        // the update products: A = window block K+q, B = -L(K+q, K)^H
+        for (int q = 1; q <= nb && ok; ++q) {
+          cp_async_wait_pending(max(nbp - q, 0) + 1 + cnt);
+          __syncwarp();
+          blk_from_tm(x, tb + scol(K + q));
+          if (!put_pair(x, q, -1.f)) { ok = false; break; }
+          if (q <= nbn) {
+            stage(q, tile_of(K - 1 + q, K - 1), -1);
+            ++cnt;
+          }
+        }
+        if (!ok) break;
+        if (nb >= 1) {  // v_K = w_K + the products' sum (round to nearest)
+          if (!wwait(bar(kQX), ++nx)) { ok = false; break; }
+          tc_fence_after();
+          blk_from_tm(x, tb + scratch);
+#pragma unroll
+          for (int i = 0; i < 64; ++i) v[i] += x[i];
+        }
+        // x_K = Linv_K^H v_K
+        cp_async_wait_pending(cnt);
+        __syncwarp();
+        if (!put_pair(v, 0, 1.f)) { ok = false; break; }
+        if (K >= 1) {
+          stage(0, f.inv + (int64_t)(2 * (K - 1)) * te, K - 1);
+          ++cnt;
+        }
+        if (!wwait(bar(kQStep), ++nstep)) { ok = false; break; }
+        tc_fence_after();
+        blk_from_tm(x, tb + scratch);
+        blk_to_tm(x, tb + sk);
+        // P_K^T on the window (blocks K..K+nb): new row t = old row invp[t]; the rows below that
+        // receive (old top rows perm[r] >= 32) are exactly those whose values move up
+        const int16_t* pm = permbuf(K);
+        const int P = (nb + 1) * kTile;
+        for (int r = lane; r < P; r += 32) {
+          const int dst = pm[r];
+          if (dst < 32) invp[dst] = (int16_t)r;
+        }
+        __syncwarp();
+        const int pl = invp[lane], pr = pm[lane];
+        const unsigned moved = __ballot_sync(~0u, pl != lane);
+        const unsigned down = __ballot_sync(~0u, pr >= 32);
+        auto bcol = [&](int j) { return scol(K + j); };
+        if (moved) {
+          uint32_t ur[32], ui[32];
+#pragma unroll
+          for (int r = 0; r < 32; ++r) {
+            const int sr = __shfl_sync(~0u, pl, r);
+            ur[r] = ui[r] = 0u;
+            if ((moved >> r) & 1u) {
+              const uint32_t a = tb + bcol(sr >> 5) + (uint32_t)(sr & 31);
+              ur[r] = tm_ld1(a);
+              ui[r] = tm_ld1(a + 32);
+            }
+          }
+          tm_wait_ld();
+          reg_fence16(*(uint32_t(*)[16])&ur[0]);
+          reg_fence16(*(uint32_t(*)[16])&ur[16]);
+          reg_fence16(*(uint32_t(*)[16])&ui[0]);
+          reg_fence16(*(uint32_t(*)[16])&ui[16]);
+          // rows below receive old top rows (from x, still in registers as the old top block)
+          unsigned m = down;
+          while (m) {  // up to 8 rows per batch (warp-uniform)
+            uint32_t va[16];
+            int dr[8], nbt = 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              va[u] = va[8 + u] = 0u;
+              dr[u] = 0;
+              if (m) {
+                const int r = __ffs(m) - 1;
+                m &= m - 1;
+                dr[u] = __shfl_sync(~0u, pr, r);
+                va[u] = tm_ld1(tb + sk + (uint32_t)r);
+                va[8 + u] = tm_ld1(tb + sk + 32u + (uint32_t)r);
+                nbt = u + 1;
+              }
+            }
+            tm_wait_ld();
+            reg_fence16(va);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (u < nbt) {
+                const uint32_t a = tb + bcol(dr[u] >> 5) + (uint32_t)(dr[u] & 31);
+                tm_st1(a, va[u]);
+                tm_st1(a + 32, va[8 + u]);
+              }
+          }
+#pragma unroll
+          for (int r = 0; r < 32; ++r)
+            if ((moved >> r) & 1u) {
+              x[r] = __uint_as_float(ur[r]);
+              x[32 + r] = __uint_as_float(ui[r]);
+            }
+          tm_wait_st();
+          blk_to_tm(x, tb + sk);
+        }
+        __syncwarp();
+      }
+      if (ok) {  // the blocks left in the window are final
+        for (int J = 0; J <= min(bt, Nb - 1); ++J) {
+          blk_from_tm(x, tb + scol(J));
+          blk_to_global(x, X, n, (int64_t)J * kTile, valid, 0, 16);
+        }
+      }
+      cp_async_wait_pending(0);
+    }
+    __syncthreads();
+  }
+  if (warp == 4) {
+    if (lane == 0) tc_commit(bar(kQDrain));
+    __syncwarp();
+    wait_k(bar(kQDrain), 1, &sh_bad, false);
+    __syncwarp();
+  }
+  cp_async_wait_pending(0);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tslot), "r"(512u));
+}
+
 }  // namespace
 
 size_t solve_tc_smem_bytes(const FactorGeom& g) {
@@ -800,8 +1070,15 @@ size_t solve_tc_smem_bytes(const FactorGeom& g) {
          8 * (size_t)Pmax * sizeof(int16_t) + 8 * kNumBars + 8;
 }
 
+size_t solve_tca_smem_bytes(const FactorGeom& g) {
+  const int Pmax = (g.bt + 1) * kTile;
+  return 1024 + 2 * (size_t)kPairBytes + (size_t)(g.bt + 1) * kSlotBytes + 8 * (size_t)Pmax * sizeof(int16_t) +
+         4 * 32 * sizeof(int16_t) + 8 * kQNumBars + 8;
+}
+
 bool solve_tc_supported(const FactorGeom& g) {
-  return g.bt >= 1 && 64 * 2 * g.bt <= 512 && 64 * (g.bt + 2) <= 512 && solve_tc_smem_bytes(g) <= 227 * 1024;
+  return g.bt >= 1 && 64 * 2 * g.bt <= 512 && 64 * (g.bt + 2) <= 512 && solve_tc_smem_bytes(g) <= 227 * 1024 &&
+         solve_tca_smem_bytes(g) <= 227 * 1024;
 }
 
 int solve_tc_error(int* h_err, int clear, cudaStream_t st) {
@@ -840,8 +1117,13 @@ int launch_solve_tc(const FactorGeom& g, int trans, int nitems, const SysDesc* d
     solve_tc_kernel<1><<<grid, kTcThreads, smem, st>>>(g, d_sys, factor_arena, rhs_arena, out_arena, d_items, nitems,
                                                        counter);
     PD_CK_LAUNCH();
-    // the adjoint backward sweep (L^H, inverse interchanges) on the TMEM kernel
-    return launch_solve_tm(g, 1, nitems, d_sys, factor_arena, rhs_arena, out_arena, queue, st, 1, 2);
+    // the adjoint backward sweep (L^H with the inverse interchanges), left-looking
+    const size_t smem2 = solve_tca_smem_bytes(g);
+    PD_CK(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    PD_CK(cudaFuncSetAttribute(solve_tca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    solve_tca_kernel<<<grid, kTcThreads, smem2, st>>>(g, d_sys, factor_arena, out_arena, d_items, nitems, counter);
+    PD_CK_LAUNCH();
+    return 0;
   }
   PD_CK(cudaFuncSetAttribute(solve_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   solve_tc_kernel<0><<<grid, kTcThreads, smem, st>>>(g, d_sys, factor_arena, rhs_arena, out_arena, d_items, nitems,
