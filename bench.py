@@ -403,8 +403,8 @@ def solve_bound(bounds_tbl, tuned):
     if tuned.get("rhs_chunk_early") == 256 or tuned.get("rhs_chunk") == 256:
         tb["solve"] = ("tensor", BF16_SUSTAINED_TFLOPS / 6,
                        "bf16 tensor cores (sustained, %s) / 6 bf16 products per FP32-class product (bf16x6); "
-                       "the group also holds the round-to-nearest passes after the fourth and the adjoint "
-                       "backward sweeps on the FP32 pipe" % BF16_PEAK_SOURCE)
+                       "the group also holds the round-to-nearest passes after the fourth on the FP32 pipe"
+                       % BF16_PEAK_SOURCE)
     return tb
 
 

@@ -1366,8 +1366,9 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
     PD_TRY(spectral_norm(n, b, cplx, band, ldab, 1e-6, &F.bnorm, F.p.inertia_ws, F.p.inertia_bytes, st));
   // Exact counts by inertia at every boundary (Section 3.2).  The LDL^T sweeps
   // occupy one SM per boundary, so they run on a side stream next to the first
-  // filter pass and are read back with the first Rayleigh-Ritz results; a slice
-  // whose subspace is smaller than its count is reported after that pass.
+  // two filter passes and are read back with the second Rayleigh-Ritz results (or
+  // the first, when max_iter is 1); a slice whose subspace is smaller than its
+  // count is reported then.
   SideStream side;
   const int64_t* d_neg = nullptr;
   const int* d_bad = nullptr;
@@ -1482,7 +1483,7 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
     std::vector<int> next;
     for (int s : F.active) {
       F.iters[s] = it;
-      if (F.nconv[s] == F.counts[s])
+      if (counts_ready && F.nconv[s] == F.counts[s])
         done[s] = 1;
       else
         next.push_back(s);
@@ -1510,7 +1511,9 @@ int feast_entry(int64_t n, int b, int cplx, const void* band, int64_t ldab, int 
     };
     PD_TRY(first_error(timed(ms_filter, [&]() { return F.filter(); })));
     PD_TRY(first_error(timed(ms_rr, [&]() { return F.rr(); })));
-    PD_TRY(read_counts());
+    // the counts are read (and a slice can be declared converged) from the second iteration on:
+    // the first pass almost never converges, and the inertia sweeps then overlap two passes
+    if (it >= 2 || it >= o->max_iter) PD_TRY(read_counts());
     update_active(it);
   }
   PD_TRY(read_counts());
