@@ -178,6 +178,15 @@ typedef struct {
 /* Forget every tuned choice held in this process (cache files are kept). */
 void pdeshep_tune_reset(void);
 
+/* Testing hook: the number of polls after which a bounded mbarrier wait of the tensor-core kernels */
+/* (tall and band products, complex64 solves) gives up; polls <= 0 restores the defaults (2^24     */
+/* and 2^22 polls with back-off, about a second).  A wait that gives up ends its CTA's work, the   */
+/* call returns PDESHEP_DEVICE_TIMEOUT, and the GPU context stays usable: before a CTA exits it    */
+/* still waits, with the default limit, for every copy and product it issued.  Process-wide for    */
+/* the current device; do not change it while calls are in flight.  Returns 0 or                   */
+/* PDESHEP_CUDA_ERROR.                                                                             */
+int pdeshep_debug_wait_limit(int64_t polls);
+
 /* Fill *o with the defaults listed above. */
 void pdeshep_opts_default(pdeshep_opts* o);
 

@@ -44,7 +44,7 @@ STATUS = {
 
 EXPORTED = [
     "pdeshep_opts_default", "pdeshep_status_string", "pdeshep_last_error", "pdeshep_version",
-    "pdeshep_kernel_launches", "pdeshep_alu_peak",
+    "pdeshep_kernel_launches", "pdeshep_alu_peak", "pdeshep_debug_wait_limit",
     "pdeshep_inertia_workspace_size", "pdeshep_inertia", "pdeshep_inertia_noalloc",
     "pdeshep_bisect_workspace_size",
     "pdeshep_bisect", "pdeshep_gershgorin", "pdeshep_contour_rule", "pdeshep_contour_rule_trapezoid",
@@ -152,6 +152,7 @@ def load(path: str = LIB_PATH):
         "pdeshep_partition": (C.c_int, [i32, i64, P, i32, dbl, dbl, i32, P, P, P, P]),
         "pdeshep_restart_plan": (C.c_int, [i64, P, i32, P, P, i32, P]),
         "pdeshep_random_start": (C.c_int, [i64, i32, i64, i32, C.c_uint64, P, P]),
+        "pdeshep_debug_wait_limit": (C.c_int, [i64]),
         "pdeshep_alu_peak": (C.c_int, [i32, i64, P, P, P]),
         "pdeshep_gather_columns_workspace_size": (sz, [i32]),
         "pdeshep_gather_columns": (C.c_int, [i64, i32, P, i64, i32, P, C.c_uint64, i64, P, P, sz, P]),

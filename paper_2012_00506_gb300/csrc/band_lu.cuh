@@ -119,6 +119,7 @@ int launch_solve_tc(const FactorGeom& g, int trans, int nitems, const SysDesc* d
                     const float2* rhs_arena, float2* out_arena, void* queue, cudaStream_t st);
 // the error word of the tensor-core solve (a bounded wait gave up): read into *h_err (synchronous) and/or clear
 int solve_tc_error(int* h_err, int clear, cudaStream_t st);
+int solve_tc_set_wait_polls(int polls);  // 0: the default
 // sweep0/sweep1: the sweeps [sweep0, sweep1) of each item (0: forward, 1: backward; default both)
 int launch_solve_tm(const FactorGeom& g, int trans, int nitems, const SysDesc* d_sys, const char* factor_arena,
                     const float2* rhs_arena, float2* out_arena, void* queue, cudaStream_t st, int sweep0 = 0,

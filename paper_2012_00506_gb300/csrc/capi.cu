@@ -7,6 +7,7 @@
 
 #include "band_lu.cuh"
 #include "dense.cuh"
+#include "tcgemm.cuh"
 
 namespace pdeshep {
 
@@ -355,6 +356,14 @@ __global__ void __launch_bounds__(256) fma_probe_kernel(int64_t iters, T seed, T
   if (s == (T)-12345.0) out[blockIdx.x * blockDim.x + threadIdx.x] = s;  // never true; keeps the chains
 }
 }  // namespace
+
+extern "C" int pdeshep_debug_wait_limit(int64_t polls) {
+  using namespace pdeshep;
+  const int64_t p = polls > 0 ? std::min<int64_t>(polls, 1 << 22) : 0;
+  PD_TRY(tc_set_wait_polls((unsigned)p));
+  PD_TRY(solve_tc_set_wait_polls((int)p));
+  return 0;
+}
 
 extern "C" int pdeshep_alu_peak(int32_t fp64, int64_t iters, double* h_tflops, void* d_scratch, void* stream) {
   if (fp64 != 0 && fp64 != 1) return -1;

@@ -49,6 +49,9 @@ constexpr int kPollLimit = 1 << 22;
 
 // set when a bounded wait of the kernel gave up (read and cleared by the host)
 __device__ int g_tc_solve_err;
+// polls after which the main waits give up (a testing hook lowers it; the drains before TMEM is
+// released always use kPollLimit)
+__device__ int g_tc_solve_polls = kPollLimit;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -362,9 +365,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // bounded wait for the k-th completion (k >= 1) of bar; gives up early once another warp has
 // recorded a failure (unless `early` is false).  A give-up sets the error word and the CTA's
 // failure flag.
-__device__ __forceinline__ bool wait_k(uint32_t bar, int k, volatile int* bad, bool early = true) {
+__device__ __forceinline__ bool wait_k(uint32_t bar, int k, volatile int* bad, bool early = true,
+                                       int polls = kPollLimit) {
   const uint32_t parity = (uint32_t)((k - 1) & 1);
-  for (int it = 0; it < kPollLimit; ++it) {
+  for (int it = 0; it < polls; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -405,7 +409,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   auto bar = [&](int i) { return smem_u32(bars + i); };
   // a warp-uniform bounded wait (a give-up by any lane fails the whole warp; the warp reconverges)
-  auto wwait = [&](uint32_t b, int k) -> bool { return __all_sync(~0u, wait_k(b, k, &sh_bad)) != 0; };
+  const int polls = g_tc_solve_polls;
+  auto wwait = [&](uint32_t b, int k) -> bool { return __all_sync(~0u, wait_k(b, k, &sh_bad, true, polls)) != 0; };
   if (t == 0) {
     for (int i = 0; i < kNumBars; ++i)
       mbar_init(bar(i), (i == kBarFull0 || i == kBarFull1 || i == kBarAFull) ? 4u : 1u);
@@ -823,7 +828,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   auto bar = [&](int i) { return smem_u32(bars + i); };
-  auto wwait = [&](uint32_t b, int k) -> bool { return __all_sync(~0u, wait_k(b, k, &sh_bad)) != 0; };
+  const int polls = g_tc_solve_polls;
+  auto wwait = [&](uint32_t b, int k) -> bool { return __all_sync(~0u, wait_k(b, k, &sh_bad, true, polls)) != 0; };
   if (t == 0) {
     for (int i = 0; i < kQNumBars; ++i) mbar_init(bar(i), (i == kQFull0 || i == kQFull1) ? 4u : 1u);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1079,6 +1085,12 @@ size_t solve_tca_smem_bytes(const FactorGeom& g) {
 bool solve_tc_supported(const FactorGeom& g) {
   return g.bt >= 1 && 64 * 2 * g.bt <= 512 && 64 * (g.bt + 2) <= 512 && solve_tc_smem_bytes(g) <= 227 * 1024 &&
          solve_tca_smem_bytes(g) <= 227 * 1024;
+}
+
+int solve_tc_set_wait_polls(int polls) {
+  const int v = polls > 0 ? polls : kPollLimit;
+  PD_CK(cudaMemcpyToSymbol(g_tc_solve_polls, &v, sizeof(v)));
+  return 0;
 }
 
 int solve_tc_error(int* h_err, int clear, cudaStream_t st) {

@@ -386,9 +386,14 @@ __device__ inline void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 __device__ inline void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// polls after which the main waits of tc_gemm_kernel give up (a testing hook lowers it; the
+// drains at the end of the kernel always use kDrainPolls)
+constexpr unsigned kDrainPolls = 1u << 24;
+__device__ unsigned g_tc_wait_polls = kDrainPolls;
+
 // bounded wait for the phase of the given parity; false (and *err set) if it never completes
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
-  for (int it = 0; it < (1 << 24); ++it) {
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, int* err, unsigned polls = kDrainPolls) {
+  for (unsigned it = 0; it < polls; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -491,6 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
+  const unsigned lim = g_tc_wait_polls;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -505,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ya = d.a_row0 + it.tm * BM, yb = d.b_row0 + it.tn * BN;
         for (int s = 0; s < nst; ++s) {
           const int G = gs, slot = G % kStages;
-          if (!mbar_wait(empty0 + 8 * slot, ((G / kStages) & 1) ^ 1, err)) { ok = false; break; }
+          if (!mbar_wait(empty0 + 8 * slot, ((G / kStages) & 1) ^ 1, err, lim)) { ok = false; break; }
           mbar_expect_tx(full0 + 8 * slot, kStage);
           const uint32_t sa = smem_u32(sm + slot * kStage);
           const int x = k0 + s * BK;
@@ -577,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nst = stages_of(it, d, k0);
         const int nchunk = (int)cdiv(nst, kChunk);
         if (ni > 0) {
-          if (!mbar_wait(tfree, (ni - 1) & 1, err)) { ok = false; break; }
+          if (!mbar_wait(tfree, (ni - 1) & 1, err, lim)) { ok = false; break; }
           tc_fence_after();
         }
         tail_started = false;
@@ -586,19 +592,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int pre = min(s1 - s0, kStages);  // stages whose tails run ahead of the read-out wait
           for (int s = s0; s < s0 + pre; ++s) {
             const int G = gs + s;
-            if (!mbar_wait(full0 + 8 * (G % kStages), (G / kStages) & 1, err)) { ok = false; break; }
+            if (!mbar_wait(full0 + 8 * (G % kStages), (G / kStages) & 1, err, lim)) { ok = false; break; }
             tc_fence_after();
             tail(G);
           }
           if (!ok) break;
           if (gc > 0) {
-            if (!mbar_wait(acce, (gc - 1) & 1, err)) { ok = false; break; }
+            if (!mbar_wait(acce, (gc - 1) & 1, err, lim)) { ok = false; break; }
             tc_fence_after();
           }
           for (int s = s0; s < s1; ++s) {
             const int G = gs + s;
             if (s >= s0 + pre) {
-              if (!mbar_wait(full0 + 8 * (G % kStages), (G / kStages) & 1, err)) { ok = false; break; }
+              if (!mbar_wait(full0 + 8 * (G % kStages), (G / kStages) & 1, err, lim)) { ok = false; break; }
               tc_fence_after();
               tail(G);
             }
@@ -632,7 +638,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int q = 0; q < 32; ++q) T[q] = 0;
       for (int ch = 0; ch < nchunk; ++ch, ++gc) {
-        if (!mbar_wait(accf, gc & 1, err)) { ok = false; break; }
+        if (!mbar_wait(accf, gc & 1, err, lim)) { ok = false; break; }
         tc_fence_after();
         // level L holds integer multiples of 2^(-8L), below 2^24 of them: exact in FP32 and in int32
 #pragma unroll
@@ -1127,6 +1133,12 @@ int tc_band_matmul(const TcScratch& w, const TcShape& sh, const std::vector<int>
   PD_TRY(make_map(&ma, w.dband, k2, w.pitch_band, kTcDigits * w.rows_band, BM));
   PD_TRY(make_map(&mb, w.db, pitch, pitch, kTcDigits * w.rows_b, BN));
   return launch_products<S>(w, ma, mb, (int)w.rows_band, (int)w.rows_b, hd, hi, w.eband, Y, st);
+}
+
+int tc_set_wait_polls(unsigned polls) {
+  const unsigned v = polls ? polls : kDrainPolls;
+  PD_CK(cudaMemcpyToSymbol(g_tc_wait_polls, &v, sizeof(v)));
+  return 0;
 }
 
 int tc_read_error(const TcScratch& w, cudaStream_t st) {

@@ -116,6 +116,7 @@ size_t tc_band_bytes(int64_t n, int b, int cplx);
 
 // PDESHEP_DEVICE_TIMEOUT if a product kernel's bounded wait gave up since the last clear (synchronises)
 int tc_read_error(const TcScratch& w, cudaStream_t st);
+int tc_set_wait_polls(unsigned polls);  // 0: the default
 int tc_clear_error(const TcScratch& w, cudaStream_t st);
 
 }  // namespace pdeshep
