@@ -68,10 +68,16 @@ typedef struct {
   int32_t precision;       /* PDESHEP_FP64 or PDESHEP_MIXED; default PDESHEP_MIXED */
   int32_t refine_policy;   /* PDESHEP_REFINE_*; default PDESHEP_REFINE_RESIDUAL */
   int32_t rhs_chunk;       /* right-hand sides per solve work item: 16, 32 or 64 (a thread per
-                              row of a 32-row tile, the window in shared memory), or 128 (complex64
+                              row of a 32-row tile, the window in shared memory), 128 (complex64
                               factors only: a thread per right-hand side, the window in tensor
-                              memory, b <= 128); 0 = 128 where it applies, else 32, or the
-                              autotuned width when autotune is on */
+                              memory, b <= 128) or 256 (complex64 factors only: the tile products
+                              on the tensor cores as bf16x6 MMAs into tensor memory, items of 128
+                              right-hand sides, b <= 128; the tensor core truncates its FP32
+                              accumulator, so these solves carry 2-3x the error of the FP32-FMA
+                              ones); a nonzero value serves every filter pass.  0 = the first four
+                              passes on the tensor cores where they apply and are not measured
+                              slower, the later passes on the fastest FP32-FMA width (measured when
+                              autotune is on, else 128 where it applies or 32) */
   double ellipse_ratio;    /* vertical / horizontal semi-axis of the contour; default 0.3 */
   double bnorm;            /* ||B||_2 for the residual; <= 0: computed by the library */
   uint64_t seed;           /* start vectors drawn by the library when d_x0 is NULL (see
@@ -85,8 +91,9 @@ typedef struct {
                               iteration */
   int32_t autotune;        /* 0 off; 1 use the tuned choice for this problem shape, measuring
                               it on first use; 2 measure again.  Tuned: the solve column block
-                              (16/32/64/128, unless rhs_chunk is set) and the split count of the
-                              tall Gram products (2/4/8) */
+                              (16/32/64/128 and whether 256 serves the first passes, unless
+                              rhs_chunk is set) and the split count of the tall Gram products
+                              (2/4/8) */
   int32_t verbose;         /* 0 quiet */
   void* stream;            /* cudaStream_t */
   int32_t rr_arith;        /* PDESHEP_MIXED only: arithmetic of the Rayleigh-Ritz products.

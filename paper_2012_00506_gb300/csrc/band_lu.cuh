@@ -110,7 +110,7 @@ size_t solve_queue_bytes(int nsys, int max_cols);
 constexpr int kTmChunk = 128;
 bool solve_tm_supported(const FactorGeom& g);
 size_t solve_tm_smem_bytes(const FactorGeom& g);
-// complex64 solves with the tile products on the tcgen05 tensor cores (solve_tc.cu; 3xTF32):
+// complex64 solves with the tile products on the tcgen05 tensor cores (solve_tc.cu; bf16x6):
 // work items of kTmChunk columns, selected as the column block kTcChunk; b <= 128.
 constexpr int kTcChunk = 256;
 bool solve_tc_supported(const FactorGeom& g);

@@ -168,7 +168,7 @@ def test_rhs_block_width_does_not_change_results(device, cplx):
     for e, v, nf in outs[1:]:
         assert nf == outs[0][2]
         assert np.array_equal(e, outs[0][0]) and np.array_equal(v, outs[0][1])
-    # the tensor-core solve (3xTF32 products: FP32-class, not the same FMA sequence) refines to the
+    # the tensor-core solve (bf16x6 products: FP32-class, not the same FMA sequence) refines to the
     # same eigenpairs within the FEAST tolerances
     r = pk.band_slice(band, bounds, m0, block_to_dev(X0, device), precision=pk.MIXED,
                       bnorm=oracle.spectral_norm(ab), rhs_chunk=256, max_iter=30)
