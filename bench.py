@@ -76,9 +76,11 @@ C2 = Config("c2", 8192, 64, 8, 8, 8, 0.2, "random", 0, "bisect", synth.config_se
             "lowest 20% (1638 eigenpairs), Ne=8, m0=max(1.3m, m+10), warm start; one step = one matrix")
 CONFIGS = {"c5": C5, "c2": C2}
 
-METRIC = ("eigenpairs/s at residual <= 1e-10 (mixed path: complex64 band LU/solves with FP64 residual refinement, "
-          "tall Rayleigh-Ritz and band products as bf16 digit products on the tensor cores (FP64-class), "
-          "float-float small products, FP64 inertia and eigensolver refinement; plain FP64 reported alongside)")
+METRIC = ("eigenpairs/s at residual <= 1e-10 (mixed path: complex64 band LU and solves with FP64 residual "
+          "refinement, the solve tiles of the first four filter passes as bf16x6 products on the tensor cores "
+          "(FP32-class), tall Rayleigh-Ritz and band products as bf16 digit products on the tensor cores "
+          "(FP64-class), float-float small products, FP64 inertia and eigensolver refinement; plain FP64 reported "
+          "alongside)")
 DTYPE = "c64+bf16x6+ff32x2+f64"
 
 # Tensor-core tall products: 26 bf16 digit products per FP64-class product, so the usable peak is
