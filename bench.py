@@ -723,7 +723,7 @@ def _e2e_run(pk, torch, seq, inputs, stream, overlap):
 def train_proposer(pk, torch, dev, args):
     """The learned slice proposer: trained here on 128 smaller spectra of the mixture family (n =
     1024; half at b = 64, half at b = 128; labels by the library's inertia bisection to 1e-4
-    relative; 1500 Adam steps), then judged on held-out complex mixture bands (n = 16384, b = 64,
+    relative; 1500 Adam steps), then evaluated on held-out complex mixture bands (n = 16384, b = 64,
     64 equal-count slices) against equal widths (the no-network baseline); counts are exact in both."""
     from paper_2012_00506_gb300 import slicer
 

@@ -1,4 +1,4 @@
-"""Host-side logic of bench.py on the CPU: which roofline a kernel group is judged against, the
+"""Host-side logic of bench.py on the CPU: which roofline a kernel group is measured against, the
 dominant group, the traffic lookup keyed by the sources' hash, and the SCF partition targets."""
 import importlib.util
 import json
