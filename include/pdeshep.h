@@ -298,6 +298,19 @@ int pdeshep_contour_rule(int32_t ne, double lo, double hi, double rho, pdeshep_c
 /* pdeshep_band_slice through h_nodes / h_weights.  Host only.                                    */
 int pdeshep_contour_rule_trapezoid(int32_t ne, double lo, double hi, double rho, pdeshep_c128* h_z,
                                    pdeshep_c128* h_w);
+/* The Zolotarev rule (the improved rational filter Section 2.2 cites after eq. (10)): ne nodes   */
+/* on the upper half of the circle with diameter [lo, hi] and weights in the same convention,      */
+/* whose filter 2 Re sum_k w_k/(z_k - x) is within E of the indicator of [lo, hi] at every real x  */
+/* at least gap*(hi - lo) away from both lo and hi, E being the equioscillation error of           */
+/* Zolotarev's best type (2ne-1, 2ne) approximation of sign(x) on [-1,-ell] U [ell,1] with         */
+/* sqrt(ell) = gap/(1 + gap); r(lo) = r(hi) = 1/2 - f_inf with |f_inf| = E/2 (the constant term of */
+/* the rational function, which a rule of nodes and weights cannot carry, is left out).            */
+/* Arguments: 1 <= ne <= 256, finite lo < hi, finite gap > 0; h_z, h_w hold ne entries each        */
+/* (caller-owned host memory); h_err receives E (may be NULL).  Returns 0, or -1 (ne), -2 (lo/hi), */
+/* -4 (gap), -5 (h_z NULL), -6 (h_w NULL).  Host only; pass the rule to pdeshep_band_slice through */
+/* h_nodes / h_weights.                                                                            */
+int pdeshep_contour_rule_zolotarev(int32_t ne, double lo, double hi, double gap, pdeshep_c128* h_z,
+                                   pdeshep_c128* h_w, double* h_err);
 
 /* ------------------------------------------------------------------------ */
 /* Shifted band solves of eq. (10): for each shift z_s, factor z_s I - B by   */

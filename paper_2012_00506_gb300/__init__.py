@@ -48,6 +48,7 @@ EXPORTED = [
     "pdeshep_inertia_workspace_size", "pdeshep_inertia", "pdeshep_inertia_noalloc",
     "pdeshep_bisect_workspace_size",
     "pdeshep_bisect", "pdeshep_gershgorin", "pdeshep_contour_rule", "pdeshep_contour_rule_trapezoid",
+    "pdeshep_contour_rule_zolotarev",
     "pdeshep_shifted_solve_workspace_size", "pdeshep_shifted_solve", "pdeshep_band_matmul",
     "pdeshep_cholqr_workspace_size", "pdeshep_cholqr", "pdeshep_eigh_workspace_size",
     "pdeshep_eigh", "pdeshep_workspace_size", "pdeshep_band_slice",
@@ -139,6 +140,7 @@ def load(path: str = LIB_PATH):
         "pdeshep_gershgorin": (C.c_int, [i64, i32, i32, P, i64, P, P, P, sz, P]),
         "pdeshep_contour_rule": (C.c_int, [i32, dbl, dbl, dbl, P, P]),
         "pdeshep_contour_rule_trapezoid": (C.c_int, [i32, dbl, dbl, dbl, P, P]),
+        "pdeshep_contour_rule_zolotarev": (C.c_int, [i32, dbl, dbl, dbl, P, P, P]),
         "pdeshep_shifted_solve_workspace_size": (sz, [i64, i32, i32, i32, i32]),
         "pdeshep_shifted_solve": (C.c_int, [i64, i32, i32, P, i64, i32, P, i32, P, i32, i32, P, P, P, sz, P]),
         "pdeshep_band_matmul": (C.c_int, [i64, i32, i32, P, i64, i32, P, P, P]),
@@ -301,6 +303,20 @@ def contour_rule(ne, lo, hi, rho=0.3, kind="gauss"):
     fn = {"gauss": "pdeshep_contour_rule", "trapezoid": "pdeshep_contour_rule_trapezoid"}[kind]
     _check(fn, getattr(lib, fn)(int(ne), float(lo), float(hi), float(rho), _np_ptr(z), _np_ptr(w)))
     return z, w
+
+
+def zolotarev_rule(ne, lo, hi, gap):
+    """Zolotarev rule for [lo, hi] (host computation): nodes, weights and the bound E on
+    |filter - indicator| at every real x at least ``gap * (hi - lo)`` from both ends; pass the
+    rule to ``band_slice`` as ``nodes`` / ``weights``."""
+    lib = load()
+    z = np.zeros(ne, dtype=np.complex128)
+    w = np.zeros(ne, dtype=np.complex128)
+    err = C.c_double()
+    _check("pdeshep_contour_rule_zolotarev",
+           lib.pdeshep_contour_rule_zolotarev(int(ne), float(lo), float(hi), float(gap), _np_ptr(z), _np_ptr(w),
+                                              C.byref(err)))
+    return z, w, err.value
 
 
 def shifted_solve(band, shifts, rhs, trans=0, precision=FP64, b=None, return_ipiv=False, stream=None):

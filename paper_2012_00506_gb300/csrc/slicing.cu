@@ -1,9 +1,11 @@
 // slicing.cu -- host-side pieces of the slicing step: the quadrature rule of
 // Section 2.2 (Gauss-Legendre nodes on the upper half of an ellipse around the
-// slice, eqs. (8)-(9)), eigenvalue enclosures by batched bisection on the GPU
+// slice, eqs. (8)-(9); the trapezoid and Zolotarev rules it cites beside them), eigenvalue enclosures by batched bisection on the GPU
 // inertia kernel (slice boundaries with exact counts, Section 3.2), status
 // strings and option defaults.
 #include <math.h>
+
+#include <cmath>
 
 #include <algorithm>
 #include <vector>
@@ -90,6 +92,108 @@ void contour_rule_trapezoid(int ne, double lo, double hi, double rho, pdeshep_c1
     z[k].im = r * rho * st;
     w[k].re = r / (2.0 * ne) * rho * ct;
     w[k].im = r / (2.0 * ne) * st;
+  }
+}
+
+// Zolotarev rule (the improved rational filter Section 2.2 cites after eq. (10)): Zolotarev's
+// best type (2m-1, 2m) approximation of sign(x) on [-1, -ell] U [ell, 1],
+//   s(x) = M x prod_{j<m} (x^2 + c_{2j}) / prod_{j<=m} (x^2 + c_{2j-1}),
+//   c_i = ell^2 sc^2(i K'/(2m); ell'),   c_i c_{2m-i} = ell^2,
+// composed with the Moebius map x = sqrt(ell) (lambda - lo)/(hi - lambda), sqrt(ell) = gap/(1+gap),
+// gives the filter (1 + s)/2, within E/2 of the indicator of [lo, hi] wherever lambda is at least
+// gap (hi - lo) from both ends.  Its poles x = +-i sqrt(c_{2j-1}) lie on the circle with diameter
+// [lo, hi]; the m upper ones are the nodes and w_j = -Res, so the rule's filter is (1 + s)/2 minus
+// its value at infinity (size E/2), within E of the indicator.  Elliptic functions by the AGM
+// scale of Abramowitz & Stegun 16.4 / 17.6, started from the complementary modulus ell itself; the
+// coefficients past c_m come from the reflection c_{2m-i} = ell^2 / c_i, so that no argument
+// exceeds K'/2 (where cn >= sqrt(ell/(1+ell)) keeps sn/cn accurate); products are formed as
+// bounded ratios so that ne up to 256 neither overflows nor underflows.
+namespace {
+
+struct AgmScale {
+  double a[48], c[48];
+  int n;
+};
+
+// a_0 = 1, b_0 = kc, c_0 = k; c_{i+1} = c_i^2 / (4 a_{i+1}) equals (a_i - b_i)/2 without cancellation.
+AgmScale agm_scale(double k, double kc) {
+  AgmScale g;
+  double a = 1.0, b = kc, c = k;
+  g.a[0] = a;
+  g.c[0] = c;
+  g.n = 0;
+  while (fabs(c) > 1e-17 * a && g.n < 47) {
+    const double an = 0.5 * (a + b);
+    const double bn = sqrt(a * b);
+    c = c * c / (4.0 * an);
+    a = an;
+    b = bn;
+    ++g.n;
+    g.a[g.n] = a;
+    g.c[g.n] = c;
+  }
+  return g;
+}
+
+// tan(am(u)) = sn/cn and dn of modulus k (complement kc) by the descending amplitude recursion.
+void jacobi_sc_dn(const AgmScale& g, double k, double kc, double u, double* sc, double* dn) {
+  double phi = ldexp(g.a[g.n] * u, g.n);
+  for (int i = g.n; i > 0; --i) phi = 0.5 * (phi + asin(g.c[i] / g.a[i] * sin(phi)));
+  const double cn = cos(phi);
+  *sc = tan(phi);
+  *dn = sqrt(kc * kc + k * k * cn * cn);
+}
+
+// s(x) / M as a product of bounded ratios: x / (x^2 + c_{2m-1}) prod_{j<m} (x^2 + c_{2j})/(x^2 + c_{2j-1}).
+double zolo_shape(double x, const double* c, int m) {
+  const double x2 = x * x;
+  double v = x / (x2 + c[2 * m - 2]);
+  for (int j = 1; j < m; ++j) v *= (x2 + c[2 * j - 1]) / (x2 + c[2 * j - 2]);
+  return v;
+}
+
+}  // namespace
+
+void contour_rule_zolotarev(int ne, double lo, double hi, double gap, pdeshep_c128* z, pdeshep_c128* w,
+                            double* err) {
+  const int m = ne;
+  const double q = gap / (1.0 + gap);  // sqrt(ell)
+  const double ell = q * q;
+  const double kp = sqrt((1.0 - ell) * (1.0 + ell));
+  const AgmScale g = agm_scale(kp, ell);
+  const double Kp = M_PI / (2.0 * g.a[g.n]);
+  std::vector<double> c(2 * m - 1);  // c[i-1] = c_i
+  double dn1 = q;  // dn(K'/2; ell') = sqrt(ell): the value for m = 1
+  for (int i = 1; i < m; ++i) {
+    double sc, dn;
+    jacobi_sc_dn(g, kp, ell, i * Kp / (2.0 * m), &sc, &dn);
+    c[i - 1] = ell * sc * sc * ell;
+    if (i == 1) dn1 = dn;
+  }
+  c[m - 1] = ell;  // sc^2(K'/2; ell') = 1/ell
+  for (int i = m + 1; i <= 2 * m - 1; ++i) c[i - 1] = ell * ell / c[2 * m - i - 1];
+  // M equalises the error at the first two equioscillation points ell and ell / dn(K'/(2m)).
+  const double s0 = zolo_shape(ell, c.data(), m), s1 = zolo_shape(ell / dn1, c.data(), m);
+  const double M = 2.0 / (s0 + s1);
+  if (err) *err = fabs(1.0 - M * s0);
+  const double span = hi - lo;
+  for (int j = 0; j < m; ++j) {
+    const double cj = c[2 * j];  // c_{2j+1}
+    // Res_x s at i sqrt(cj) = (M/2) prod_{i<m} (c_{2i} - cj) / prod_{k != j} (c_{2k-1} - cj), paired:
+    // even index k+1 against odd index k below j, even index k against odd index k+1 above it.
+    double ratio = 1.0;
+    for (int k = 0; k < j; ++k) ratio *= (c[2 * k + 1] - cj) / (c[2 * k] - cj);
+    for (int k = j + 1; k < m; ++k) ratio *= (c[2 * k - 1] - cj) / (c[2 * k] - cj);
+    const double res = 0.5 * M * ratio;
+    // u = i y, lambda = (lo + hi u)/(1 + u), dlambda/dx = span / (sqrt(ell) (1 + u)^2)
+    const double y = sqrt(cj) / q;
+    const double d = 1.0 + y * y;
+    z[j].re = (lo + hi * y * y) / d;
+    z[j].im = span * y / d;
+    // 1/(1 + i y)^2 = (1 - y^2 - 2 i y) / d^2;  w = -(1/2) res dlambda/dx
+    const double f = -0.5 * res * span / (q * d * d);
+    w[j].re = f * (1.0 - y * y);
+    w[j].im = f * (-2.0 * y);
   }
 }
 
@@ -236,6 +340,17 @@ extern "C" int pdeshep_contour_rule_trapezoid(int32_t ne, double lo, double hi, 
   if (!h_z) return -5;
   if (!h_w) return -6;
   contour_rule_trapezoid(ne, lo, hi, rho, h_z, h_w);
+  return 0;
+}
+
+extern "C" int pdeshep_contour_rule_zolotarev(int32_t ne, double lo, double hi, double gap, pdeshep_c128* h_z,
+                                              pdeshep_c128* h_w, double* h_err) {
+  if (ne < 1 || ne > 256) return -1;
+  if (!(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi)) return -2;
+  if (!(gap > 0.0) || !std::isfinite(gap)) return -4;
+  if (!h_z) return -5;
+  if (!h_w) return -6;
+  contour_rule_zolotarev(ne, lo, hi, gap, h_z, h_w, h_err);
   return 0;
 }
 

@@ -376,6 +376,40 @@ def test_slice_groups_match_one_batch(device):
         off += m
 
 
+def test_zolotarev_rule_through_gpu_feast(device):
+    """The Zolotarev rule (the rational filter Section 2.2 cites after eq. (10)) from the library's
+    host code, passed as the call's nodes and weights: the GPU FEAST matches the oracle's FEAST run
+    with the oracle's own Zolotarev rule."""
+    import paper_2012_00506_gb300 as pk
+    from oracle import rules_oracle
+    n, b = 400, 8
+    ab = synth.random_band(n, b, 503, True)
+    ks = [90, 130, 170]
+    bounds = _bounds(ab, ks)
+    bn = oracle.spectral_norm(ab)
+    m0 = [oracle.m0_rule(40), oracle.m0_rule(40)]
+    rules = [rules_oracle.zolotarev_rule(8, bounds[i], bounds[i + 1], 0.1)[:2] for i in range(2)]
+    lib_rules = [pk.zolotarev_rule(8, bounds[i], bounds[i + 1], 0.1)[:2] for i in range(2)]
+    for (z, w), (zl, wl) in zip(rules, lib_rules):
+        assert np.max(np.abs(z - zl)) <= 1e-12 * bn and np.max(np.abs(w - wl)) <= 1e-12 * np.max(np.abs(w))
+    X0 = synth.random_subspace(n, sum(m0), 504, True)
+    r = pk.band_slice(to_dev(ab, device), bounds, m0, block_to_dev(X0, device), bnorm=bn, max_iter=40,
+                      nodes=np.concatenate([z for z, _ in lib_rules]), weights=np.concatenate([w for _, w in lib_rules]))
+    assert r.status == 0
+    ev, V = r.evals.cpu().numpy(), block_from_dev(r.evecs)
+    off = 0
+    for i in range(2):
+        cnt = ks[i + 1] - ks[i]
+        assert r.counts[i] == r.nfound[i] == cnt
+        o = oracle.feast_slice(ab, bounds[i], bounds[i + 1], X0[:, off:off + m0[i]], tol=1e-10, bnorm=bn,
+                               max_iter=40, count=cnt, rule=rules[i])
+        assert o["status"] == 0 and o["nfound"] == cnt
+        assert np.max(np.abs(ev[off:off + cnt] - o["evals"][:cnt])) <= 1e-10 * bn
+        assert oracle.subspace_sin_angle(V[:, off:off + cnt], o["evecs"][:, :cnt]) <= 1e-8
+        assert oracle.orth_max(V[:, off:off + cnt]) <= orth_tol(n, 2)
+        off += m0[i]
+
+
 def test_trapezoid_rule_through_gpu_feast(device):
     """The midpoint trapezoid rule (Section 2.2 names it beside Gauss quadrature) passed as the
     call's nodes and weights: the GPU FEAST matches the oracle's FEAST run with the same rule."""
