@@ -2,8 +2,8 @@
 re-slicing between steps (Section 3.1): every step partitions the previous step's converged
 eigenvalues (equal counts or the simplified k-means of Algorithm 3), takes the exact counts by
 inertia, sizes m0 by the rule of Section 3.2, and starts every slice from the previous
-eigenvectors chosen by the restart plan (the nearest ones when the slice grew).  Gauss and
-trapezoid rules.  Every slice must converge with its exact count; the iteration counts (a
+eigenvectors chosen by the restart plan (the nearest ones when the slice grew).  Gauss,
+trapezoid and Zolotarev rules.  Every slice must converge with its exact count; the iteration counts (a
 property of the algorithm, not of the hardware) are printed."""
 import numpy as np
 import pytest
@@ -43,7 +43,12 @@ def _sequence(method, rule_kind, n=800, b=8, nev=160, K=8, steps=4, ne=8, seed=5
             Y = np.empty((n, m0[i]), dtype=np.complex128)
             for q, src in enumerate(plan[i]):
                 Y[:, q] = vecs[:, src] if src >= 0 else g.standard_normal(n) + 1j * g.standard_normal(n)
-            rule = ro.trapezoid_rule(ne, bounds[i], bounds[i + 1], 0.3) if rule_kind == "trapezoid" else None
+            if rule_kind == "trapezoid":
+                rule = ro.trapezoid_rule(ne, bounds[i], bounds[i + 1], 0.3)
+            elif rule_kind == "zolotarev":
+                rule = ro.zolotarev_rule(ne, bounds[i], bounds[i + 1], 0.2)[:2]
+            else:
+                rule = None
             o = oracle.feast_slice(B, bounds[i], bounds[i + 1], Y, ne=ne, rho=0.3, tol=1e-10, bnorm=bn,
                                    max_iter=40, count=counts[i], rule=rule)
             assert o["status"] == 0 and o["nfound"] == counts[i]
@@ -63,7 +68,8 @@ def _sequence(method, rule_kind, n=800, b=8, nev=160, K=8, steps=4, ne=8, seed=5
 
 @pytest.mark.slow
 @pytest.mark.parametrize("method,rule,outer", [("equal", "gauss", "dense"), ("kmeans", "gauss", "dense"),
-                                               ("kmeans", "trapezoid", "dense"), ("kmeans", "gauss", "alg4")])
+                                               ("kmeans", "trapezoid", "dense"), ("kmeans", "zolotarev", "dense"),
+                                               ("equal", "zolotarev", "dense"), ("kmeans", "gauss", "alg4")])
 def test_sequence_with_reslicing(method, rule, outer):
     """outer = "alg4": the outer bounds of every warm step come from Algorithm 4 on the current
     matrix instead of the previous matrix's dense spectrum (the loop of the paper's Algorithm 2)."""
