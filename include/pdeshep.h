@@ -305,12 +305,12 @@ int pdeshep_contour_rule_trapezoid(int32_t ne, double lo, double hi, double rho,
 /* Zolotarev's best type (2ne-1, 2ne) approximation of sign(x) on [-1,-ell] U [ell,1] with         */
 /* sqrt(ell) = gap/(1 + gap); r(lo) = r(hi) = 1/2 - f_inf with |f_inf| = E/2 (the constant term of */
 /* the rational function, which a rule of nodes and weights cannot carry, is left out).            */
-/* Arguments: 1 <= ne <= 256, finite lo < hi, finite gap >= 1e-6; h_z, h_w hold ne entries each   */
+/* Arguments: 1 <= ne <= 256, finite lo < hi, finite gap >= 1e-8; h_z, h_w hold ne entries each   */
 /* (caller-owned host memory); h_err receives E (may be NULL).  Returns 0, or -1 (ne), -2 (lo/hi), */
-/* -4 (gap), -5 (h_z NULL), -6 (h_w NULL).  The nodes and weights carry the rounding of the        */
-/* elliptic functions near the quarter period (relative eps K'/sqrt(ell)), amplified with ne: the  */
-/* filter is within E + 1e-10 of the indicator for gap >= 1e-3 (any ne), within about 1e-5 at the  */
-/* smallest gap.  Host only; pass the rule to pdeshep_band_slice through h_nodes / h_weights.      */
+/* -4 (gap), -5 (h_z NULL), -6 (h_w NULL).  Rounding amplified by the partial fractions adds to E: */
+/* the filter is within E + 1e-12 of the indicator for gap >= 1e-4, E + 1e-10 for gap >= 1e-6 and */
+/* E + 1e-9 down to gap = 1e-8 (ne <= 256).  Host only; pass the rule to pdeshep_band_slice        */
+/* through h_nodes / h_weights.                                                                    */
 int pdeshep_contour_rule_zolotarev(int32_t ne, double lo, double hi, double gap, pdeshep_c128* h_z,
                                    pdeshep_c128* h_w, double* h_err);
 

@@ -306,10 +306,10 @@ def contour_rule(ne, lo, hi, rho=0.3, kind="gauss"):
 
 
 def zolotarev_rule(ne, lo, hi, gap):
-    """Zolotarev rule for [lo, hi] (host computation, ``gap >= 1e-6``): nodes, weights and the
+    """Zolotarev rule for [lo, hi] (host computation, ``gap >= 1e-8``): nodes, weights and the
     bound E on |filter - indicator| at every real x at least ``gap * (hi - lo)`` from both ends
-    (plus a rounding floor: 1e-10 for gap >= 1e-3); pass the rule to ``band_slice`` as ``nodes`` /
-    ``weights``."""
+    (plus a rounding floor: 1e-12 for gap >= 1e-4, 1e-9 at the smallest gap); pass the rule to
+    ``band_slice`` as ``nodes`` / ``weights``."""
     lib = load()
     z = np.zeros(ne, dtype=np.complex128)
     w = np.zeros(ne, dtype=np.complex128)

@@ -106,12 +106,14 @@ void contour_rule_trapezoid(int ne, double lo, double hi, double rho, pdeshep_c1
 // its value at infinity (size E/2), within E of the indicator.  Elliptic functions by the AGM
 // scale of Abramowitz & Stegun 16.4 / 17.6, started from the complementary modulus ell itself; the
 // coefficients past c_m come from the reflection c_{2m-i} = ell^2 / c_i, so that no argument
-// exceeds K'/2, where cn >= sqrt(ell/(1+ell)); sn/cn = tan(amplitude) then carries a relative
-// error of about eps K'/sqrt(ell), so gap is held to >= 1e-6 (ell >= 1e-12), and the rule's
-// filter departs from the exact Zolotarev filter by that rounding times a factor that grows with
-// ne (measured: below 1e-10 for gap >= 1e-3 and ne <= 256, about 1e-5 at gap = 1e-6 and
-// ne = 256).  Products are formed as bounded ratios and the nodes as points c + r e^{i theta}
-// of the circle, so that nothing overflows for ne up to 256 or |lo|, |hi| up to 1e307.
+// exceeds K'/2.  There cn >= sqrt(ell/(1+ell)) is small for small ell, and sn/cn = tan(amplitude)
+// would carry a relative error of about eps K'/sqrt(ell); for ell <= 1/2 sn/cn comes from the
+// nome series of the imaginary transformation instead (sc_nome below), accurate to a few ulps
+// for any ell.  Products are formed as bounded ratios and the nodes as points c + r e^{i theta}
+// of the circle, so that nothing overflows for ne up to 256 or |lo|, |hi| up to 1e307.  What is
+// left is rounding amplified by the partial fractions at large ne and tiny ell (measured: the
+// filter within E + 1e-12 for gap >= 1e-4, E + 1e-10 for gap >= 1e-6, E + 1e-9 for gap >= 1e-8,
+// ne <= 256); gap is held to >= 1e-8.
 namespace {
 
 struct AgmScale {
@@ -139,13 +141,31 @@ AgmScale agm_scale(double k, double kc) {
   return g;
 }
 
-// tan(am(u)) = sn/cn and dn of modulus k (complement kc) by the descending amplitude recursion.
-void jacobi_sc_dn(const AgmScale& g, double k, double kc, double u, double* sc, double* dn) {
+// tan(am(u)) = sn/cn of modulus k by the descending amplitude recursion.
+double jacobi_sc(const AgmScale& g, double u) {
   double phi = ldexp(g.a[g.n] * u, g.n);
   for (int i = g.n; i > 0; --i) phi = 0.5 * (phi + asin(g.c[i] / g.a[i] * sin(phi)));
-  const double cn = cos(phi);
-  *sc = tan(phi);
-  *dn = sqrt(kc * kc + k * k * cn * cn);
+  return tan(phi);
+}
+
+// sc(u; ell') for a small complement ell by Jacobi's imaginary transformation (A&S 16.20), sc(u; ell') =
+// -i sn(iu; ell), and the nome (Fourier) series of sn (Abramowitz & Stegun 16.23.1):
+//   sc(u; ell') = (2 pi / (ell K)) sum_{n>=0} q^{n+1/2} sinh((2n+1) w) / (1 - q^{2n+1}),
+// K = K(ell), q = exp(-pi K'/K), w = pi u / (2K).  For 0 <= u <= K'/2 every term is positive and
+// the ratio of consecutive terms is about sqrt(q) ~ ell/4, so the sum is accurate to a few ulps
+// where the amplitude recursion loses eps/cn.  Each term is formed as one exponential
+// e^{(n+1/2)(ln q + 2w)} (1 - e^{-2(2n+1)w})/2 / (1 - q^{2n+1}) with ln q + 2w <= ln q / 2 < 0,
+// so nothing overflows.
+double sc_nome(double u, double K, double lnq, double ell) {
+  const double w = M_PI * u / (2.0 * K);
+  double sum = 0.0;
+  for (int n = 0; n < 200; ++n) {
+    const double a = 2.0 * n + 1.0;
+    const double t = exp((n + 0.5) * (lnq + 2.0 * w)) * (-0.5 * expm1(-2.0 * a * w)) / (-expm1(a * lnq));
+    sum += t;
+    if (t <= 1e-17 * sum) break;
+  }
+  return 2.0 * M_PI / (ell * K) * sum;
 }
 
 // s(x) / M as a product of bounded ratios: x / (x^2 + c_{2m-1}) prod_{j<m} (x^2 + c_{2j})/(x^2 + c_{2j-1}).
@@ -167,12 +187,22 @@ void contour_rule_zolotarev(int ne, double lo, double hi, double gap, pdeshep_c1
   const AgmScale g = agm_scale(kp, ell);
   const double Kp = M_PI / (2.0 * g.a[g.n]);
   std::vector<double> c(2 * m - 1);  // c[i-1] = c_i
+  // sn/cn at i K'/(2m), i < m: the nome series for ell <= 1/2 (there cn at K'/2 is below 0.58 and
+  // shrinks like sqrt(ell)); the amplitude recursion otherwise (its series converges slowly as
+  // ell -> 1, while cn stays large).  dn = sqrt(ell^2 + ell'^2 cn^2) with cn^2 = 1/(1 + sc^2).
+  const bool nome = ell <= 0.5;
+  double K = 0.0, lnq = 0.0;
+  if (nome) {
+    const AgmScale gk = agm_scale(ell, kp);  // K(ell) = pi / (2 AGM(1, ell'))
+    K = M_PI / (2.0 * gk.a[gk.n]);
+    lnq = -M_PI * Kp / K;
+  }
   double dn1 = q;  // dn(K'/2; ell') = sqrt(ell): the value for m = 1
   for (int i = 1; i < m; ++i) {
-    double sc, dn;
-    jacobi_sc_dn(g, kp, ell, i * Kp / (2.0 * m), &sc, &dn);
+    const double u = i * Kp / (2.0 * m);
+    const double sc = nome ? sc_nome(u, K, lnq, ell) : jacobi_sc(g, u);
     c[i - 1] = ell * sc * sc * ell;
-    if (i == 1) dn1 = dn;
+    if (i == 1) dn1 = sqrt(ell * ell + kp * kp / (1.0 + sc * sc));
   }
   c[m - 1] = ell;  // sc^2(K'/2; ell') = 1/ell
   for (int i = m + 1; i <= 2 * m - 1; ++i) c[i - 1] = ell * ell / c[2 * m - i - 1];
@@ -353,7 +383,7 @@ extern "C" int pdeshep_contour_rule_zolotarev(int32_t ne, double lo, double hi, 
                                               pdeshep_c128* h_w, double* h_err) {
   if (ne < 1 || ne > 256) return -1;
   if (!(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi)) return -2;
-  if (!(gap >= 1e-6) || !std::isfinite(gap)) return -4;
+  if (!(gap >= 1e-8) || !std::isfinite(gap)) return -4;
   if (!h_z) return -5;
   if (!h_w) return -6;
   contour_rule_zolotarev(ne, lo, hi, gap, h_z, h_w, h_err);
