@@ -14,6 +14,11 @@ Step (III): backtransform of the band's eigenvectors):
 * ``to_lower_band(D, b)``   LAPACK lower compact band storage (n, b + 1): ab[i, k] =
                             D[i + k, i], the layout of the band FEAST input.
 * ``backtransform(W, Xh)``  X = U^H X_hat = W X_hat (Step (III)).
+* ``generalized_to_standard(A, B)``  the generalized problem A x = lambda B x (A Hermitian, B
+                            Hermitian positive definite) reduced to the standard one by the
+                            Cholesky factor B = L L^H: A~ = L^{-1} A L^{-H} with eigenvectors
+                            x~ = L^H x (Section 2.1); returns A~ and L.
+* ``standard_to_generalized(L, Xt)``  x = L^{-H} x~ for every column.
 """
 from __future__ import annotations
 
@@ -52,3 +57,15 @@ def to_lower_band(D, b):
 
 def backtransform(W, Xh):
     return W @ Xh
+
+
+def generalized_to_standard(A, B):
+    """A~ = L^{-1} A L^{-H}, B = L L^H (lower Cholesky factor), A~ made exactly Hermitian."""
+    L = np.linalg.cholesky(B)
+    Y = np.linalg.solve(L, A)                        # L^{-1} A
+    At = np.linalg.solve(L, Y.conj().T).conj().T     # (L^{-1} (L^{-1} A)^H)^H = L^{-1} A L^{-H}
+    return 0.5 * (At + At.conj().T), L
+
+
+def standard_to_generalized(L, Xt):
+    return np.linalg.solve(L.conj().T, Xt)
